@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: 4-pol W-projection gridding rate on GB300.
+
+A step is one call of the gridding path on one batch of synthetic input:
+index selection, device binning and the gridding kernel (the kernel tables
+are built once per plan, as the thesis generates its GCF table once).
+Workload: 64 antennas in a 5 km disk, 256 times x 16 channels (120-180 MHz)
+= 8,257,536 visibilities x 4 pols; 4096^2 x 4 grid, 32 w-planes, support
+7 -> 63, oversampling 8.  Inputs (vis 264 MB, grid 512 MB) exceed the
+129 MB L2, so no explicit flush is done between steps.
+
+value = grid-point polarisation updates per second (sum over visibilities of
+S_p^2 x npol, divided by the device time of the step), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank grids its own batch (seeded by rank) into its own
+grid; the grids are summed once (NCCL all-reduce) inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gridding rate (grid-point updates/s), 4-pol W-proj; p50/p99 request latency"
+UNIT = "grid-point pol-updates/s"
+FLOP_PER_UPDATE = 8           # complex x complex multiply-accumulate = 4 FFMA
+SM_MAX_MHZ_DEFAULT = 2070.0
+FFMA_PER_SM_PER_CLK = 128
+
+# DRAM traffic of the gridding kernel from one ncu capture, valid only for the
+# kernel source it was taken on (sha256 of gw_grid.cu); null otherwise.
+GRID_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "capture": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-rows", type=int, default=0,
+                    help="rows of the workload in the CPU-baseline sample (0 = 1/8 of rows)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_sha(name="gw_grid.cu"):
+    p = os.path.join(ROOT, "paper_2111_04141_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7],
+                                 swp=f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def cpu_baseline(obs, rows):
+    """The FP64 oracle on a bounded sample of the workload (host cores)."""
+    import numpy as np
+    from oracle.cgrid import Oracle, default_threads
+    from oracle.wkernel import Params, plane_support
+    prm = Params(**obs.plan_kwargs())
+    orc = Oracle(prm)
+    sub = slice(0, rows)
+    idx = orc.index(obs.uvw_m[sub], obs.freq_hz)
+    S = plane_support(prm)
+    taps = int(np.sum(S[idx["plane"]][idx["valid"]] ** 2))
+    th = default_threads()
+    t0 = time.perf_counter()
+    orc.grid(obs.uvw_m[sub], obs.freq_hz, obs.vis[sub], idx=idx, nthreads=th)
+    dt = time.perf_counter() - t0
+    return taps * prm.npol / dt, th, dt, taps
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import synthetic as syn
+    from oracle.cgrid import Oracle, default_threads
+    from oracle.wkernel import Params, plane_support
+    obs = syn.config_wproj()
+    prm = Params(**obs.plan_kwargs())
+    orc = Oracle(prm)
+    rows = obs.nrow // 64
+    S = plane_support(prm)
+    th = default_threads()
+    times, taps_tot = [], 0
+    for step in range(args.warmup + args.steps):
+        r0 = (step * rows) % (obs.nrow - rows)
+        sub = slice(r0, r0 + rows)
+        idx = orc.index(obs.uvw_m[sub], obs.freq_hz)
+        taps = int(np.sum(S[idx["plane"]][idx["valid"]] ** 2))
+        t0 = time.perf_counter()
+        orc.grid(obs.uvw_m[sub], obs.freq_hz, obs.vis[sub], idx=idx, nthreads=th)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            taps_tot += taps
+    value = taps_tot * prm.npol / sum(times)
+    sample = (f"{rows} consecutive rows (1/64 of the workload's rows, all 16 channels) per step, "
+              f"FP64 C oracle, {th} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": obs.name, "rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    import synthetic as syn
+    import paper_2111_04141_gb300 as gw
+    from paper_2111_04141_gb300 import build as gwbuild
+
+    gwbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    obs = syn.config_wproj(seed_offset=rank)
+    plan = gw.Plan.from_observation(obs)
+    uvw = torch.from_numpy(obs.uvw_m).to(dev)
+    freq = torch.from_numpy(obs.freq_hz).to(dev)
+    vis = torch.from_numpy(obs.vis).to(dev)
+    grid = plan.new_grid()
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(3, args.warmup)):
+        plan.grid(uvw, freq, vis, out=grid)
+    torch.cuda.synchronize(dev)
+    plan.timing(True)
+    plan.timing()  # reset counters
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = gw.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.grid(uvw, freq, vis, out=grid)
+    if pg:
+        pg.all_reduce(grid)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = gw.launch_count() - l0
+    t_ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    tm = plan.timing()
+    plan.timing(False)
+    if pg:
+        tt = torch.tensor([t_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_ms = float(tt.item())
+
+    npol = obs.npol
+    taps_step = tm["taps"] / args.steps
+    updates_step = taps_step * npol
+    value = world * updates_step * args.steps / (t_ms * 1e-3)
+    grid_ms = tm["grid_ms"] / max(1, tm["grid_calls"])
+    flop_launch = updates_step * FLOP_PER_UPDATE / max(1, tm["grid_calls"] / args.steps)
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (clocks or {}).get("sm_max_mhz") or SM_MAX_MHZ_DEFAULT
+    peak = num_sms * FFMA_PER_SM_PER_CLK * 2 * sm_max * 1e6 / 1e12
+    achieved = flop_launch / (grid_ms * 1e-3) / 1e12
+    traffic = (GRID_TRAFFIC["bytes_per_launch"]
+               if GRID_TRAFFIC["sha256"] == kernel_sha() else None)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "k_grid (gw_grid.cu)",
+            "peak_basis": f"FP32 FFMA: {num_sms} SMs x {FFMA_PER_SM_PER_CLK} FFMA/clk x 2 FLOP x "
+                          f"{sm_max:.0f} MHz",
+            "frac_at_sampled_clock": (achieved / (num_sms * FFMA_PER_SM_PER_CLK * 2 *
+                                                  clocks["sm_mhz"] * 1e-6)
+                                      if clocks and clocks.get("sm_mhz") else None),
+            "stage_ms_per_step": {k: tm[f"{k}_ms"] / args.steps
+                                  for k in ("index", "bin", "grid")}}
+
+    # ---- end to end through the public API with host buffers --------------
+    pin_uvw = torch.from_numpy(obs.uvw_m).pin_memory()
+    pin_freq = torch.from_numpy(obs.freq_hz).pin_memory()
+    pin_vis = torch.from_numpy(obs.vis).pin_memory()
+    pin_out = torch.empty(grid.shape, dtype=grid.dtype).pin_memory()
+    d_uvw, d_freq, d_vis = torch.empty_like(uvw), torch.empty_like(freq), torch.empty_like(vis)
+    ne = max(1, args.e2e_steps)
+
+    def e2e_step():
+        d_uvw.copy_(pin_uvw, non_blocking=True)
+        d_freq.copy_(pin_freq, non_blocking=True)
+        d_vis.copy_(pin_vis, non_blocking=True)
+        grid.zero_()
+        plan.grid(d_uvw, d_freq, d_vis, out=grid)
+        pin_out.copy_(grid, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(ne):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / ne
+    if pg:
+        tt = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = pin_uvw.numel() * 8 + pin_freq.numel() * 8 + pin_vis.numel() * 8
+    d2h = pin_out.numel() * 8
+    e2e = {"value": world * updates_step / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": e2e_ms}
+
+    # ---- degridding (the adjoint) on the same batch -------------------------
+    out_vis = torch.empty_like(vis)
+    plan.degrid(uvw, freq, grid, out=out_vis)
+    plan.timing(True)
+    plan.timing()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    nd = max(1, min(args.steps, 10))
+    for _ in range(nd):
+        plan.degrid(uvw, freq, grid, out=out_vis)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dg = plan.timing()
+    plan.timing(False)
+    dg_ms = e0.elapsed_time(e1) / nd
+    degrid = {"value": dg["taps"] / nd * npol / (dg_ms * 1e-3), "unit": UNIT,
+              "ms_per_step": dg_ms, "kernel_ms": dg["degrid_ms"] / max(1, dg["degrid_calls"]),
+              "achieved_tflops": dg["taps"] / nd * npol * FLOP_PER_UPDATE /
+                                 (dg["degrid_ms"] / max(1, dg["degrid_calls"]) * 1e-3) / 1e12}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = args.cpu_sample_rows or obs.nrow // 8
+        v, th, dt, taps = cpu_baseline(obs, rows)
+        cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"first {rows} rows (1/{obs.nrow // rows} of the workload, all "
+                         f"{obs.nchan} channels), FP64 C oracle, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": obs.name, "nvis": obs.nvis, "npol": npol,
+                       "grid_n": obs.grid_n, "n_wplanes": obs.n_wplanes,
+                       "support": f"{obs.support_min}->{obs.support_max}",
+                       "oversample": obs.oversample,
+                       "valid_vis": int(tm["valid_vis"] / args.steps),
+                       "mean_S2": taps_step / max(1, tm["valid_vis"] / args.steps),
+                       "vis_per_s": world * tm["valid_vis"] / args.steps * args.steps /
+                                    (t_ms * 1e-3),
+                       "l2": "inputs larger than L2 (vis 264 MB, grid 512 MB); no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "degrid": degrid,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/*
+ * gw.h -- C ABI of the GB300 W-projection gridding / degridding library.
+ *
+ * The library implements the data-parallel hot path of convolutional
+ * gridding with a w-projection gridding convolution function (GCF) as
+ * formulated in "High-Performance Gridding For Radio Interferometric Image
+ * Synthesis" (Muscat, arXiv:2111.04141):
+ *
+ *   uvw -> index selection        Section 3.3.5 (pre-processing), Section 2.3.6
+ *   binning by grid tile          Section 3.3.5 ("SS" ordering mode)
+ *   w-kernel tables               Section 1.7.1 (W-projection), Section 2.3.6
+ *   gridding                      Section 2.4.5, Algorithm convgriddingoversampling
+ *   degridding (the adjoint)      Section 1.6, Eq. (residualcalc), operator G^T
+ *   grid correction               Section 2.4.5, Eq. (hco); Section 3.3.8
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All pointers marked "device" are CUDA device pointers on the device that
+ *   was current when the plan was created; "host" pointers are ordinary host
+ *   memory.  The caller owns every buffer it passes; the plan owns its
+ *   kernel tables and scratch.
+ * - Calls are asynchronous on the CUDA stream passed as `cuda_stream`
+ *   (a cudaStream_t; NULL means the legacy default stream), except where an
+ *   argument asks for a host result (n_dropped), which synchronises that
+ *   stream.  Two calls on the same plan must not run concurrently (they
+ *   share the plan's scratch); serialise them on one stream.
+ * - Errors are returned as gw_status codes; no exception crosses the ABI.
+ *   gw_last_error() gives a human-readable message for the calling thread.
+ * - Complex numbers are interleaved (re, im) float pairs ("c64") unless the
+ *   plan selects a half-precision storage type.
+ * - Visibilities are laid out [nrow][nchan][npol]; uvw is [nrow][3] float64
+ *   metres; frequencies are [nchan] float64 Hz; the grid and images are
+ *   [npol][N][N] c64, row index v (or m), column index u (or l), with the uv
+ *   origin on pixel (N/2, N/2).
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GW_API_VERSION 1
+
+typedef struct gw_plan_s* gw_plan;
+
+typedef enum {
+    GW_OK = 0,
+    GW_EINVAL = -1,        /* invalid argument (null pointer, bad size, bad descriptor) */
+    GW_ENOMEM = -2,        /* a device or host allocation failed */
+    GW_ECUDA = -3,         /* a CUDA runtime call failed (see gw_last_error) */
+    GW_ETIMEDOUT = -4,     /* a bounded device-side wait gave up */
+    GW_EUNSUPPORTED = -5,  /* valid request this build does not implement */
+    GW_EDEVICE = -6        /* called with a different current device than the plan's */
+} gw_status;
+
+typedef enum {
+    GW_C64 = 0,            /* complex float32 pairs */
+    GW_BF16X2 = 1,         /* complex bfloat16 pairs */
+    GW_F16X2 = 2           /* complex float16 pairs */
+} gw_dtype;
+
+/* Plan descriptor.  Defines the imaging problem; see gw_plan_create. */
+typedef struct {
+    int32_t grid_n;          /* N: grid side, even, 8 <= N <= 32768 */
+    double cell_rad;         /* pixel size in direction cosines; L = N * cell_rad */
+    int32_t support_min;     /* odd, >= 1: GCF support of the w = 0 plane (taper support) */
+    int32_t support_max;     /* odd, >= support_min: support of the outermost w-plane */
+    int32_t oversample;      /* beta: even, 2 <= beta <= 256 */
+    int32_t n_wplanes;       /* P >= 1; P == 1 ignores w (2-D gridding) */
+    double w_max_lambda;     /* > 0 when P > 1: |w| (wavelengths) of the outermost plane */
+    int32_t npol;            /* 1 .. 4 polarisations gridded together (Section 3.3.4) */
+    int32_t vis_dtype;       /* gw_dtype of visibilities passed to gw_grid_vis / gw_degrid_vis */
+    int32_t table_dtype;     /* gw_dtype the kernel tables are stored in */
+    int64_t max_vis_per_call;/* scratch sizing: visibilities processed per internal chunk
+                                (0 = 2^23); larger calls are processed in chunks */
+} gw_plan_desc;
+
+/* One visibility's index record (output of the index stage, 16 bytes).
+ * For a valid record: the record sits at pixel (ku + ou/beta, kv + ov/beta)
+ * of the grid; ou, ov in [-beta/2, beta/2); plane in [0, P); flags bit 0 =
+ * valid (Bounded Records Assumption, Section 2.3.1), bit 1 = w < 0 (the
+ * conjugate kernel is used).  Invalid records are all zeros. */
+typedef struct {
+    int32_t ku, kv;
+    int16_t ou, ov;
+    int16_t plane;
+    uint16_t flags;
+} gw_index_rec;
+
+#define GW_FLAG_VALID 1u
+#define GW_FLAG_CONJ 2u
+
+/* Read-only facts about a plan (gw_plan_info). */
+typedef struct {
+    int32_t grid_n, npol, oversample, n_wplanes;
+    int32_t tile;             /* grid tile side used by the binner and gridder */
+    int32_t device;           /* CUDA device ordinal the plan lives on */
+    int64_t table_elems;      /* complex elements in all kernel tables */
+    int64_t chunk_vis;        /* visibilities per internal chunk */
+    double field;             /* L = N * cell_rad */
+    double taper_c;           /* PSWF bandwidth c = pi * support_min / 2 */
+    double table_scale;       /* global kernel scale (w = 0, o = 0 slice sums to 1) */
+} gw_plan_info;
+
+/* ------------------------------------------------------------------------
+ * Plan lifetime
+ * ------------------------------------------------------------------------ */
+
+/* Create a plan on the current CUDA device: validates the descriptor,
+ * computes the per-plane w and support (w_p = w_max (p/(P-1))^2; S_p = the
+ * odd integer nearest S_min + (S_max - S_min) p/(P-1), ties up), builds the
+ * kernel tables on the device in FP64 (prolate spheroidal taper psi_0 with
+ * c = pi S_min / 2 times the w-screen exp(+j 2 pi w_p (n - 1)), Fourier
+ * transformed by Gauss-Legendre quadrature and sampled at offsets
+ * t - o/beta, Section 1.7.1 and Section 2.3.6), stores them as table_dtype,
+ * computes the corrector, and allocates scratch.  Work is issued on
+ * `cuda_stream`; the call synchronises it before returning.
+ * Errors: GW_EINVAL (null arguments or a descriptor outside the ranges
+ * above, or a field of view whose corners reach l^2 + m^2 >= 1 when P > 1),
+ * GW_ENOMEM, GW_ECUDA.  On error *out is set to NULL. */
+gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* out);
+
+/* Free all device memory of the plan.  NULL is accepted.  The caller must
+ * ensure no work using the plan is still in flight. */
+gw_status gw_plan_destroy(gw_plan plan);
+
+gw_status gw_plan_info_get(gw_plan plan, gw_plan_info* out);
+
+/* ------------------------------------------------------------------------
+ * Hot path
+ * ------------------------------------------------------------------------ */
+
+/* Gridding (Section 2.4.5, Algorithm convgriddingoversampling, Gridding Step,
+ * with the w-projection GCF): for every visibility (row r, channel c),
+ *     grid[pol][kv + tv][ku + tu] += K(tv, tu) * vis[r][c][pol] * weight[r][c][pol]
+ * over the S_p x S_p taps of its plane, K the table slice for its offset
+ * (conjugated when w < 0).  The grid is ACCUMULATED (+=), so repeated calls
+ * and chunked inputs add linearly; zero it first for a fresh image.
+ *   uvw_m    device, [nrow][3] float64, metres
+ *   freq_hz  device, [nchan] float64, Hz
+ *   vis      device, [nrow][nchan][npol] complex of the plan's vis_dtype
+ *   weight   device, [nrow][nchan][npol] float32, or NULL for unit weights
+ *   grid     device, [npol][N][N] c64, accumulated
+ *   n_dropped host, optional: receives the number of visibilities dropped by
+ *            the Bounded Records Assumption (Section 2.3.1) or invalid
+ *            coordinates; when non-NULL the call synchronises the stream.
+ * nrow * nchan may be 0 (no work).  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */
+gw_status gw_grid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                      int32_t nchan, const void* vis, const float* weight, void* grid,
+                      int64_t* n_dropped, void* cuda_stream);
+
+/* Degridding, the adjoint of gw_grid_vis with unit weights:
+ *     vis_out[r][c][pol] = sum_{tv,tu} conj(K(tv, tu)) * grid[pol][kv + tv][ku + tu]
+ * vis_out (device, [nrow][nchan][npol] of the plan's vis_dtype) is
+ * OVERWRITTEN; dropped visibilities receive 0.  Other arguments as above. */
+gw_status gw_degrid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                        int32_t nchan, const void* grid, void* vis_out, int64_t* n_dropped,
+                        void* cuda_stream);
+
+/* Grid correction (Correction Step, Section 2.3 / 3.3.8), in place on
+ * image (device, [npol][N][N] c64):
+ *     image[pol][i][j] *= s(i, j) * h(m_i) * h(l_j),
+ *     h(l) = 1 / (chat(l) sinc_beta(l)),  l = (pixel - N/2) / N,
+ * chat the Fourier transform of the truncated, oversampled w = 0 table
+ * (Eq. (hco) of Section 2.4.5 as realised by the table), sinc_beta the
+ * nearest-neighbour factor sin(pi l / beta) / (pi l / beta).
+ *   direction = +1: image side, applied to the unnormalised inverse FFT of
+ *                   a grid prepared with gw_grid_shift; s = (-1)^(i+j)
+ *                   re-centres the image on pixel (N/2, N/2).
+ *   direction = -1: model side, applied before a forward FFT whose output is
+ *                   then passed through gw_grid_shift; s = (-1)^(i+j).
+ *   direction =  0: correction only, s = 1.
+ * The multiplier is real and diagonal, so +1 and -1 apply the same operator
+ * (it is its own adjoint).  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */
+gw_status gw_grid_correct(gw_plan plan, void* image, int32_t direction, void* cuda_stream);
+
+/* Multiply a [npol][N][N] c64 grid in place by (-1)^(kv+ku): moves the uv
+ * origin between pixel (N/2, N/2) and the corner (Section 3.3.6, IFFT Step)
+ * for an FFT library.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */
+gw_status gw_grid_shift(gw_plan plan, void* grid, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Stage access (testing, diagnostics, custom pipelines)
+ * ------------------------------------------------------------------------ */
+
+/* The index stage alone (pre-processing of Section 3.3.5): writes
+ * nrow * nchan records, (row, channel) order, to `out` (device).  Each record
+ * is computed in FP64 with the operation sequence
+ *     u_lambda = (u * f) / c0;  x = u_lambda * L + N/2;
+ *     q = floor(beta * x + 0.5);  k = floor((q + beta/2) / beta);  o = q - k beta
+ * (same for v), plane p = min(floor(sqrt(|w_lambda| / w_max) (P-1) + 0.5), P-1),
+ * every operation rounded to nearest with no fused multiply-add.  n_dropped
+ * as for gw_grid_vis. */
+gw_status gw_index_vis(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                       int32_t nchan, gw_index_rec* out, int64_t* n_dropped, void* cuda_stream);
+
+/* Copy the plan's kernel tables to host memory as interleaved float32
+ * complex, layout [plane][ov + beta/2][ou + beta/2][tv + h][tu + h]
+ * (table_elems complex elements; `out` must hold 2 * table_elems floats).
+ * plane_offsets (host, may be NULL) receives n_wplanes + 1 element offsets;
+ * supports (host, may be NULL) receives n_wplanes supports.  Synchronous. */
+gw_status gw_plan_copy_tables(gw_plan plan, float* out, int64_t* plane_offsets, int32_t* supports);
+
+/* Copy the corrector h(l_i), i = 0..N-1, to host memory (float64).  Synchronous. */
+gw_status gw_plan_copy_corrector(gw_plan plan, double* out);
+
+/* Run index + binning and copy the bins to host memory (tests): tile_offsets
+ * receives ntiles + 1 offsets (ntiles = ceil(N/tile)^2), entries receives
+ * the binned visibility ids, each visibility appearing once in every tile
+ * its footprint touches ("footprint" mode, mode = 0) or once in the tile of
+ * its centre pixel (mode = 1).  Order within a tile is unspecified.
+ * `capacity` is the size of `entries`; GW_EINVAL if too small.  Synchronous. */
+gw_status gw_debug_bins(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                        int32_t nchan, int32_t mode, int64_t* tile_offsets, uint32_t* entries,
+                        int64_t capacity, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Tracing
+ * ------------------------------------------------------------------------ */
+
+/* Per-stage device time and work of the calls made since the last
+ * gw_plan_timing_get (or since timing was enabled). */
+typedef struct {
+    double index_ms, bin_ms, grid_ms, degrid_ms;   /* summed CUDA-event durations */
+    int64_t index_calls, bin_calls, grid_calls, degrid_calls;
+    int64_t valid_vis;    /* visibilities that passed the index stage */
+    int64_t taps;         /* sum over valid visibilities of S_p^2 (per polarisation) */
+} gw_timing;
+
+/* Enable (1) or disable (0) stage timing: when enabled every stage of
+ * gw_grid_vis / gw_degrid_vis is bracketed by CUDA events recorded on the
+ * call's stream.  Work counters (valid_vis, taps) are always kept. */
+gw_status gw_plan_timing_enable(gw_plan plan, int32_t enable);
+
+/* Wait for the recorded events, return the accumulated timings and work,
+ * and reset them.  Synchronous. */
+gw_status gw_plan_timing_get(gw_plan plan, gw_timing* out);
+
+/* ------------------------------------------------------------------------
+ * Misc
+ * ------------------------------------------------------------------------ */
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t gw_launch_count(void);
+
+/* Static description of a status code. */
+const char* gw_strerror(gw_status status);
+
+/* Message describing the last error returned on the calling thread. */
+const char* gw_last_error(void);
+
+int32_t gw_api_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GW_H */

@@ -137,3 +137,57 @@ int oracle_degrid(int N, int npol, int beta, const int32_t* support, const int64
     }
     return 0;
 }
+
+/*
+ * Gridding evaluated only at the lattice points (off + step * a, off + step * b),
+ * a, b = 0 .. m-1, for full-size checks: out[pol][b][a] (row = v) receives the
+ * same sum as the full grid at that point, accumulated in record order.
+ */
+int oracle_grid_lattice(int N, int npol, int beta, const int32_t* support,
+                        const int64_t* plane_off, const double* table, int64_t nvis,
+                        const int32_t* ku, const int32_t* kv, const int32_t* ou,
+                        const int32_t* ov, const int32_t* plane, const uint8_t* flags,
+                        const double* vis, const double* weight, int off, int step, int m,
+                        double* out)
+{
+    (void)N;
+    for (int64_t i = 0; i < nvis; ++i) {
+        if (!(flags[i] & 1)) continue;
+        const int p = plane[i];
+        const int S = support[p];
+        const int h = (S - 1) / 2;
+        const int conj = (flags[i] & 2) != 0;
+        /* lattice indices whose point lies in [k - h, k + h] */
+        int a0 = (ku[i] - h - off + step - 1) / step, a1 = (ku[i] + h - off) / step;
+        int b0 = (kv[i] - h - off + step - 1) / step, b1 = (kv[i] + h - off) / step;
+        if (ku[i] - h - off < 0) a0 = 0;
+        if (kv[i] - h - off < 0) b0 = 0;
+        if (ku[i] + h - off < 0 || kv[i] + h - off < 0) continue;
+        if (a1 > m - 1) a1 = m - 1;
+        if (b1 > m - 1) b1 = m - 1;
+        const double* K = table + 2 * (plane_off[p] +
+            ((int64_t)(ov[i] + beta / 2) * beta + (ou[i] + beta / 2)) * (int64_t)S * S);
+        for (int b = b0; b <= b1; ++b) {
+            const int tv = off + step * b - kv[i];
+            for (int a = a0; a <= a1; ++a) {
+                const int tu = off + step * a - ku[i];
+                const double* k = K + 2 * ((int64_t)(tv + h) * S + (tu + h));
+                const double kr = k[0];
+                const double ki = conj ? -k[1] : k[1];
+                for (int pol = 0; pol < npol; ++pol) {
+                    double vr = vis[2 * (i * npol + pol)];
+                    double vi = vis[2 * (i * npol + pol) + 1];
+                    if (weight) {
+                        const double wt = weight[i * npol + pol];
+                        vr = vr * wt;
+                        vi = vi * wt;
+                    }
+                    double* g = out + 2 * (((int64_t)pol * m + b) * m + a);
+                    g[0] = g[0] + (kr * vr - ki * vi);
+                    g[1] = g[1] + (kr * vi + ki * vr);
+                }
+            }
+        }
+    }
+    return 0;
+}

@@ -37,6 +37,9 @@ def _load():
         p = ctypes.c_void_p
         lib.oracle_grid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, p,
                                     ctypes.c_int64, p, p, p, p, p, p, p, p, p, ctypes.c_int]
+        lib.oracle_grid_lattice.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, p,
+                                            ctypes.c_int64, p, p, p, p, p, p, p, p,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, p]
         lib.oracle_degrid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, p,
                                       ctypes.c_int64, p, p, p, p, p, p, p, p, ctypes.c_int]
         _lib = lib
@@ -104,4 +107,24 @@ class Oracle:
         _load().oracle_degrid(N, npol, prm.oversample, _ptr(self._support), _ptr(self._offs),
                               _ptr(self._table), nvis, *[_ptr(x) for x in a], _ptr(g),
                               _ptr(out), nthreads or default_threads())
+        return out
+
+    def grid_lattice(self, uvw_m, freq_hz, vis, off: int, step: int, m: int, weight=None, idx=None):
+        """The grid at lattice points (off + step*a, off + step*b): [npol, m, m]
+        (row index b = v), the same per-point sums as ``grid``."""
+        prm = self.prm
+        npol = prm.npol
+        if idx is None:
+            idx = self.index(uvw_m, freq_hz)
+        nvis = idx["ku"].shape[0]
+        v = np.ascontiguousarray(np.asarray(vis, dtype=np.complex128).reshape(nvis, npol))
+        wt = None
+        if weight is not None:
+            wt = np.ascontiguousarray(np.asarray(weight, dtype=np.float64).reshape(nvis, npol))
+        out = np.zeros((npol, m, m), dtype=np.complex128)
+        a = self._idx_arrays(idx)
+        _load().oracle_grid_lattice(prm.grid_n, npol, prm.oversample, _ptr(self._support),
+                                    _ptr(self._offs), _ptr(self._table), nvis,
+                                    *[_ptr(x) for x in a], _ptr(v), _ptr(wt), off, step, m,
+                                    _ptr(out))
         return out

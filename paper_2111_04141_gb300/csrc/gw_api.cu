@@ -1,0 +1,552 @@
+// C ABI of libgw: plan lifetime, argument checking, chunking, launches.
+// See include/gw.h for the contract of every entry point.
+#include "gw_internal.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace gw {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+static thread_local std::string t_last_error;
+
+static gw_status fail(gw_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static gw_status fail(gw_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return st;
+}
+
+static gw_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(GW_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+struct gw_plan_s {
+    gw_plan_desc desc{};
+    int device = -1;
+    int num_sms = 0;
+    int side = 0;        // tiles per grid side
+    int ntiles = 0;
+    double field = 0, table_scale = 0;
+    std::vector<int> support;
+    std::vector<double> wplane;
+    std::vector<int64_t> plane_off;
+    int max_tiles_per_vis = 0;
+    int64_t chunk = 0;
+    // device state
+    float2* table = nullptr;
+    int64_t* d_plane_off = nullptr;
+    int* d_support = nullptr;
+    double* d_h = nullptr;
+    float* d_hf = nullptr;
+    Scratch sc;
+    IndexParams ip{};
+    // tracing
+    bool timing = false;
+    struct Ev { int stage; cudaEvent_t a, b; };
+    std::vector<Ev> events;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+void plan_free(gw_plan p) {
+    if (!p) return;
+    for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (auto e : p->pool) cudaEventDestroy(e);
+    cudaFree(p->sc.work);
+    cudaFree(p->table);
+    cudaFree(p->d_plane_off);
+    cudaFree(p->d_support);
+    cudaFree(p->d_h);
+    cudaFree(p->d_hf);
+    cudaFree(p->sc.rec);
+    cudaFree(p->sc.count);
+    cudaFree(p->sc.offsets);
+    cudaFree(p->sc.cursor);
+    cudaFree(p->sc.item_off);
+    cudaFree(p->sc.entries);
+    cudaFree(p->sc.items);
+    cudaFree(p->sc.counters);
+    cudaFree(p->sc.dropped);
+    delete p;
+}
+
+gw_status check_desc(const gw_plan_desc* d) {
+    if (!d) return fail(GW_EINVAL, "null descriptor");
+    if (d->grid_n < 8 || d->grid_n > 32768 || (d->grid_n & 1))
+        return fail(GW_EINVAL, "grid_n must be even and in [8, 32768] (got %d)", d->grid_n);
+    if (!(d->cell_rad > 0.0) || !std::isfinite(d->cell_rad))
+        return fail(GW_EINVAL, "cell_rad must be positive and finite");
+    if (d->support_min < 1 || !(d->support_min & 1) || d->support_max < d->support_min ||
+        !(d->support_max & 1) || d->support_max > 255)
+        return fail(GW_EINVAL, "supports must be odd with 1 <= support_min <= support_max <= 255");
+    if (d->oversample < 2 || d->oversample > 256 || (d->oversample & 1))
+        return fail(GW_EINVAL, "oversample must be even and in [2, 256]");
+    if (d->n_wplanes < 1 || d->n_wplanes > 4096)
+        return fail(GW_EINVAL, "n_wplanes must be in [1, 4096]");
+    if (d->npol < 1 || d->npol > 4) return fail(GW_EINVAL, "npol must be in [1, 4]");
+    if (d->n_wplanes > 1 && !(d->w_max_lambda > 0.0 && std::isfinite(d->w_max_lambda)))
+        return fail(GW_EINVAL, "w_max_lambda must be positive when n_wplanes > 1");
+    const double half = 0.5 * d->grid_n * d->cell_rad;
+    if (d->n_wplanes > 1 && 2.0 * half * half >= 1.0)
+        return fail(GW_EINVAL, "field of view too wide: corners reach l^2 + m^2 >= 1");
+    if (d->vis_dtype != GW_C64 || d->table_dtype != GW_C64)
+        return fail(GW_EUNSUPPORTED, "only GW_C64 visibilities and tables are implemented");
+    if (d->max_vis_per_call < 0) return fail(GW_EINVAL, "max_vis_per_call must be >= 0");
+    return GW_OK;
+}
+
+gw_status check_device(gw_plan p) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device)
+        return fail(GW_EDEVICE, "plan lives on device %d but device %d is current", p->device, dev);
+    return GW_OK;
+}
+
+template <class T>
+cudaError_t dmalloc(T** ptr, size_t n) {
+    return cudaMalloc((void**)ptr, sizeof(T) * (n ? n : 1));
+}
+
+enum Stage { kStIndex = 0, kStBin = 1, kStGrid = 2, kStDegrid = 3 };
+
+cudaEvent_t take_event(gw_plan p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets one stage with CUDA events on the launch stream when timing is on.
+struct StageTimer {
+    gw_plan p;
+    cudaStream_t s;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageTimer(gw_plan p_, int stage_, cudaStream_t s_) : p(p_), s(s_), stage(stage_) {
+        if (p->timing && (a = take_event(p))) cudaEventRecord(a, s);
+    }
+    ~StageTimer() {
+        if (!a) return;
+        cudaEvent_t b = take_event(p);
+        if (!b) { p->pool.push_back(a); return; }
+        cudaEventRecord(b, s);
+        p->events.push_back({stage, a, b});
+    }
+};
+
+// Index + bin one chunk of rows; leaves records and bins in the plan scratch.
+gw_status index_and_bin(gw_plan p, const double* uvw, const double* freq, int64_t nrow, int nchan,
+                        int mode, cudaStream_t s) {
+    {
+        StageTimer t(p, kStIndex, s);
+        launch_index(uvw, freq, nrow, nchan, p->ip, p->sc.rec, p->sc.dropped, s);
+    }
+    {
+        StageTimer t(p, kStBin, s);
+        launch_bin(p->sc.rec, nrow * (int64_t)nchan, mode, p->desc.grid_n, p->desc.n_wplanes,
+                   p->desc.support_min, p->desc.support_max, p->sc, p->side, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "index/bin launch");
+    return GW_OK;
+}
+
+int64_t rows_per_chunk(gw_plan p, int nchan) {
+    int64_t r = p->chunk / (nchan > 0 ? nchan : 1);
+    return r < 1 ? 1 : r;
+}
+
+gw_status finish_dropped(gw_plan p, int64_t* n_dropped, cudaStream_t s) {
+    if (!n_dropped) return GW_OK;
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, p->sc.dropped, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the drop count");
+    *n_dropped = (int64_t)h;
+    return GW_OK;
+}
+
+gw_status common_checks(gw_plan p, const double* uvw, const double* freq, int64_t nrow, int nchan) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    if (nrow < 0 || nchan < 0) return fail(GW_EINVAL, "negative nrow or nchan");
+    if (nrow > 0 && nchan > 0 && (!uvw || !freq)) return fail(GW_EINVAL, "null uvw or freq");
+    if ((int64_t)nchan > p->chunk)
+        return fail(GW_EINVAL, "nchan (%d) exceeds the plan's chunk size", nchan);
+    return GW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t gw_api_version(void) { return GW_API_VERSION; }
+
+uint64_t gw_launch_count(void) { return g_launches.load(); }
+
+const char* gw_strerror(gw_status s) {
+    switch (s) {
+        case GW_OK: return "success";
+        case GW_EINVAL: return "invalid argument";
+        case GW_ENOMEM: return "out of memory";
+        case GW_ECUDA: return "CUDA error";
+        case GW_ETIMEDOUT: return "device wait timed out";
+        case GW_EUNSUPPORTED: return "unsupported";
+        case GW_EDEVICE: return "wrong current device";
+    }
+    return "unknown status";
+}
+
+const char* gw_last_error(void) { return t_last_error.c_str(); }
+
+gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* out) {
+    if (!out) return fail(GW_EINVAL, "null output pointer");
+    *out = nullptr;
+    gw_status st = check_desc(desc);
+    if (st != GW_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    gw_plan p = new (std::nothrow) gw_plan_s;
+    if (!p) return fail(GW_ENOMEM, "host allocation failed");
+    p->desc = *desc;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaGetDevice"); }
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaDeviceGetAttribute"); }
+
+    const int N = desc->grid_n, P = desc->n_wplanes, beta = desc->oversample;
+    p->field = (double)N * desc->cell_rad;
+    p->side = (N + kTile - 1) / kTile;
+    p->ntiles = p->side * p->side;
+    p->support.resize(P);
+    p->wplane.resize(P);
+    p->plane_off.resize(P + 1);
+    p->plane_off[0] = 0;
+    int smax_real = 0;
+    for (int q = 0; q < P; ++q) {
+        p->support[q] = plane_support(q, P, desc->support_min, desc->support_max);
+        const double r = P > 1 ? (double)q / (double)(P - 1) : 0.0;
+        p->wplane[q] = P > 1 ? desc->w_max_lambda * (r * r) : 0.0;
+        p->plane_off[q + 1] = p->plane_off[q] + (int64_t)beta * beta * p->support[q] * p->support[q];
+        smax_real = std::max(smax_real, p->support[q]);
+    }
+    if (p->plane_off[P] >= (int64_t)1 << 31) {
+        plan_free(p);
+        return fail(GW_EINVAL, "kernel tables exceed 2^31 elements");
+    }
+    const int span = (smax_real - 1) / kTile + 2;
+    p->max_tiles_per_vis = span * span;
+    p->chunk = desc->max_vis_per_call > 0 ? desc->max_vis_per_call : ((int64_t)1 << 23);
+    if (p->chunk * p->max_tiles_per_vis >= ((int64_t)1 << 32)) {
+        plan_free(p);
+        return fail(GW_EINVAL, "max_vis_per_call too large for 32-bit bin entries");
+    }
+
+    p->ip.L = p->field;
+    p->ip.halfN = (double)(N / 2);
+    p->ip.beta_d = (double)beta;
+    p->ip.Pm1_d = (double)(P - 1);
+    p->ip.wmax = desc->w_max_lambda;
+    p->ip.N = N;
+    p->ip.beta = beta;
+    p->ip.P = P;
+    p->ip.smin = desc->support_min;
+    p->ip.smax = desc->support_max;
+
+    Scratch& sc = p->sc;
+    sc.entries_cap = p->chunk * p->max_tiles_per_vis;
+    sc.items_cap = sc.entries_cap / kItemMax + p->ntiles + 1;
+#define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { plan_free(p); \
+        return fail(GW_ENOMEM, "device allocation of %s failed", #x); } } while (0)
+    GW_ALLOC(p->table, (size_t)p->plane_off[P]);
+    GW_ALLOC(p->d_plane_off, (size_t)P + 1);
+    GW_ALLOC(p->d_support, (size_t)P);
+    GW_ALLOC(p->d_h, (size_t)N);
+    GW_ALLOC(p->d_hf, (size_t)N);
+    GW_ALLOC(sc.rec, (size_t)p->chunk);
+    GW_ALLOC(sc.count, (size_t)p->ntiles);
+    GW_ALLOC(sc.offsets, (size_t)p->ntiles + 1);
+    GW_ALLOC(sc.cursor, (size_t)p->ntiles);
+    GW_ALLOC(sc.item_off, (size_t)p->ntiles + 1);
+    GW_ALLOC(sc.entries, (size_t)sc.entries_cap);
+    GW_ALLOC(sc.items, (size_t)sc.items_cap);
+    GW_ALLOC(sc.counters, 4);
+    GW_ALLOC(sc.dropped, 1);
+    GW_ALLOC(sc.work, 2);
+#undef GW_ALLOC
+    e = cudaMemsetAsync(sc.work, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaMemsetAsync"); }
+    e = cudaMemcpyAsync(p->d_plane_off, p->plane_off.data(), sizeof(int64_t) * (P + 1),
+                        cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_support, p->support.data(), sizeof(int) * P,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "uploading plane metadata"); }
+
+    TableBuild tb;
+    tb.N = N;
+    tb.beta = beta;
+    tb.P = P;
+    tb.smin = desc->support_min;
+    tb.smax = desc->support_max;
+    tb.field = p->field;
+    tb.wmax = desc->w_max_lambda;
+    tb.support = p->support.data();
+    tb.wplane = p->wplane.data();
+    tb.plane_off = p->plane_off.data();
+    tb.num_sms = p->num_sms;
+    e = build_tables(tb, p->table, p->d_h, p->d_hf, &p->table_scale, s);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "building kernel tables"); }
+    *out = p;
+    return GW_OK;
+}
+
+gw_status gw_plan_destroy(gw_plan plan) {
+    plan_free(plan);
+    return GW_OK;
+}
+
+gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
+    if (!p || !out) return fail(GW_EINVAL, "null argument");
+    out->grid_n = p->desc.grid_n;
+    out->npol = p->desc.npol;
+    out->oversample = p->desc.oversample;
+    out->n_wplanes = p->desc.n_wplanes;
+    out->tile = kTile;
+    out->device = p->device;
+    out->table_elems = p->plane_off.back();
+    out->chunk_vis = p->chunk;
+    out->field = p->field;
+    out->taper_c = M_PI * p->desc.support_min / 2.0;
+    out->table_scale = p->table_scale;
+    return GW_OK;
+}
+
+gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                      int32_t nchan, const void* vis, const float* weight, void* grid,
+                      int64_t* n_dropped, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!grid) return fail(GW_EINVAL, "null grid");
+    if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const int npol = p->desc.npol;
+    const int64_t rpc = rows_per_chunk(p, nchan);
+    for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
+        const int64_t nr = std::min(rpc, nrow - r0);
+        const int64_t v0 = r0 * nchan;
+        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, 0, s);
+        if (st != GW_OK) return st;
+        GridArgs a;
+        a.rec = p->sc.rec;
+        a.vis = reinterpret_cast<const float2*>(vis) + v0 * npol;
+        a.weight = weight ? weight + v0 * npol : nullptr;
+        a.table = p->table;
+        a.plane_off = p->d_plane_off;
+        a.support = p->d_support;
+        a.entries = p->sc.entries;
+        a.items = p->sc.items;
+        a.item_count = p->sc.item_off + p->ntiles;
+        a.queue = p->sc.counters;
+        a.grid = reinterpret_cast<float2*>(grid);
+        a.N = p->desc.grid_n;
+        a.npol = npol;
+        a.beta = p->desc.oversample;
+        a.ntiles_side = p->side;
+        {
+            StageTimer t(p, kStGrid, s);
+            launch_grid(a, p->num_sms, s);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "grid launch");
+    }
+    return finish_dropped(p, n_dropped, s);
+}
+
+gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                        int32_t nchan, const void* grid, void* vis_out, int64_t* n_dropped,
+                        void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!grid) return fail(GW_EINVAL, "null grid");
+    if (nrow > 0 && nchan > 0 && !vis_out) return fail(GW_EINVAL, "null vis_out");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const int npol = p->desc.npol;
+    const int64_t rpc = rows_per_chunk(p, nchan);
+    for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
+        const int64_t nr = std::min(rpc, nrow - r0);
+        const int64_t v0 = r0 * nchan;
+        float2* out = reinterpret_cast<float2*>(vis_out) + v0 * npol;
+        e = cudaMemsetAsync(out, 0, sizeof(float2) * nr * nchan * npol, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, 1, s);
+        if (st != GW_OK) return st;
+        DegridArgs a;
+        a.rec = p->sc.rec;
+        a.grid = reinterpret_cast<const float2*>(grid);
+        a.table = p->table;
+        a.plane_off = p->d_plane_off;
+        a.support = p->d_support;
+        a.entries = p->sc.entries;
+        a.n_entries = p->sc.offsets + p->ntiles;
+        a.vis_out = out;
+        a.N = p->desc.grid_n;
+        a.npol = npol;
+        a.beta = p->desc.oversample;
+        {
+            StageTimer t(p, kStDegrid, s);
+            launch_degrid(a, nr * nchan, p->num_sms, s);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "degrid launch");
+    }
+    return finish_dropped(p, n_dropped, s);
+}
+
+gw_status gw_grid_correct(gw_plan p, void* image, int32_t direction, void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    if (!image) return fail(GW_EINVAL, "null image");
+    if (direction < -1 || direction > 1) return fail(GW_EINVAL, "direction must be -1, 0 or +1");
+    launch_correct(reinterpret_cast<float2*>(image), p->d_hf, p->desc.grid_n, p->desc.npol,
+                   direction, (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "correct launch");
+}
+
+gw_status gw_grid_shift(gw_plan p, void* grid, void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    if (!grid) return fail(GW_EINVAL, "null grid");
+    launch_shift(reinterpret_cast<float2*>(grid), p->desc.grid_n, p->desc.npol,
+                 (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "shift launch");
+}
+
+gw_status gw_index_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                       int32_t nchan, gw_index_rec* out, int64_t* n_dropped, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (nrow > 0 && nchan > 0 && !out) return fail(GW_EINVAL, "null output");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    launch_index(uvw_m, freq_hz, nrow, nchan, p->ip, out, p->sc.dropped, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "index launch");
+    return finish_dropped(p, n_dropped, s);
+}
+
+gw_status gw_plan_copy_tables(gw_plan p, float* out, int64_t* plane_offsets, int32_t* supports) {
+    if (!p || !out) return fail(GW_EINVAL, "null argument");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    cudaError_t e = cudaMemcpy(out, p->table, sizeof(float2) * p->plane_off.back(),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "copying tables");
+    if (plane_offsets)
+        for (size_t i = 0; i < p->plane_off.size(); ++i) plane_offsets[i] = p->plane_off[i];
+    if (supports)
+        for (size_t i = 0; i < p->support.size(); ++i) supports[i] = p->support[i];
+    return GW_OK;
+}
+
+gw_status gw_plan_timing_enable(gw_plan p, int32_t enable) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    p->timing = enable != 0;
+    return GW_OK;
+}
+
+gw_status gw_plan_timing_get(gw_plan p, gw_timing* out) {
+    if (!p || !out) return fail(GW_EINVAL, "null argument");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    std::memset(out, 0, sizeof *out);
+    double* ms[4] = {&out->index_ms, &out->bin_ms, &out->grid_ms, &out->degrid_ms};
+    int64_t* calls[4] = {&out->index_calls, &out->bin_calls, &out->grid_calls, &out->degrid_calls};
+    cudaError_t e = cudaSuccess;
+    for (auto& ev : p->events) {
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev.a, ev.b);
+        *ms[ev.stage] += t;
+        *calls[ev.stage] += 1;
+        p->pool.push_back(ev.a);
+        p->pool.push_back(ev.b);
+    }
+    p->events.clear();
+    if (e != cudaSuccess) return cuda_fail(e, "reading stage events");
+    unsigned long long w[2] = {0, 0};
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(w, p->sc.work, sizeof w, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->sc.work, 0, sizeof w);
+    if (e != cudaSuccess) return cuda_fail(e, "reading work counters");
+    out->valid_vis = (int64_t)w[0];
+    out->taps = (int64_t)w[1];
+    return GW_OK;
+}
+
+gw_status gw_plan_copy_corrector(gw_plan p, double* out) {
+    if (!p || !out) return fail(GW_EINVAL, "null argument");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    cudaError_t e = cudaMemcpy(out, p->d_h, sizeof(double) * p->desc.grid_n, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "copying corrector");
+}
+
+gw_status gw_debug_bins(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                        int32_t nchan, int32_t mode, int64_t* tile_offsets, uint32_t* entries,
+                        int64_t capacity, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!tile_offsets || (mode != 0 && mode != 1)) return fail(GW_EINVAL, "bad arguments");
+    if (nrow * (int64_t)nchan > p->chunk) return fail(GW_EINVAL, "input exceeds one chunk");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    st = index_and_bin(p, uvw_m, freq_hz, nrow, nchan, mode, s);
+    if (st != GW_OK) return st;
+    std::vector<uint32_t> offs(p->ntiles + 1);
+    cudaError_t e = cudaMemcpyAsync(offs.data(), p->sc.offsets, sizeof(uint32_t) * offs.size(),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "copying bin offsets");
+    for (size_t i = 0; i < offs.size(); ++i) tile_offsets[i] = offs[i];
+    const int64_t n = offs.back();
+    if (n > capacity || (n > 0 && !entries)) return fail(GW_EINVAL, "entries capacity too small");
+    if (n > 0) {
+        e = cudaMemcpy(entries, p->sc.entries, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "copying bin entries");
+    }
+    return GW_OK;
+}
+
+}  // extern "C"

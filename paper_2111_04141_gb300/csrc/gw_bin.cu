@@ -1,0 +1,178 @@
+// Device binner: groups visibility ids by grid tile.
+//
+// The thesis orders records by their position on the NN grid ("SS" mode,
+// Section 3.3.5) because record order controls commit traffic.  Here the
+// equivalent is a bin per kTile x kTile grid tile:
+//   footprint mode: a record is listed in every tile its S_p x S_p footprint
+//                   touches (the gridder owns a tile and needs all of them);
+//   centre mode:    a record is listed once, in the tile of its pixel (the
+//                   degridder reads a record's whole footprint).
+// Steps: histogram (atomics) -> exclusive scan -> scatter (atomic cursors),
+// then the footprint bins are cut into work items of at most kItemMax
+// entries.  Order within a bin is unspecified.
+#include "gw_internal.cuh"
+
+namespace gw {
+
+namespace {
+
+struct TileRange {
+    int tu0, tu1, tv0, tv1;
+};
+
+__device__ __forceinline__ TileRange tile_range(const gw_index_rec& r, int mode, int P, int smin,
+                                                int smax) {
+    TileRange t;
+    if (mode == 1) {
+        t.tu0 = t.tu1 = r.ku / kTile;
+        t.tv0 = t.tv1 = r.kv / kTile;
+    } else {
+        const int h = plane_support(r.plane, P, smin, smax) / 2;
+        t.tu0 = (r.ku - h) / kTile;
+        t.tu1 = (r.ku + h) / kTile;
+        t.tv0 = (r.kv - h) / kTile;
+        t.tv1 = (r.kv + h) / kTile;
+    }
+    return t;
+}
+
+__device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, int64_t i) {
+    int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
+    return *reinterpret_cast<gw_index_rec*>(&v);
+}
+
+__global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, int mode, int P,
+                        int smin, int smax, int side, uint32_t* __restrict__ count,
+                        unsigned long long* __restrict__ work) {
+    unsigned long long n_valid = 0, n_taps = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const gw_index_rec r = load_rec(rec, i);
+        if (!(r.flags & GW_FLAG_VALID)) continue;
+        const int S = plane_support(r.plane, P, smin, smax);
+        ++n_valid;
+        n_taps += (unsigned long long)(S * S);
+        const TileRange t = tile_range(r, mode, P, smin, smax);
+        for (int tv = t.tv0; tv <= t.tv1; ++tv)
+            for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(count + tv * side + tu, 1u);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        n_valid += __shfl_down_sync(0xffffffffu, n_valid, d);
+        n_taps += __shfl_down_sync(0xffffffffu, n_taps, d);
+    }
+    if ((threadIdx.x & 31) == 0 && n_valid) {
+        atomicAdd(work, n_valid);
+        atomicAdd(work + 1, n_taps);
+    }
+}
+
+// Exclusive scans of count[] -> offsets[], and of ceil(count / kItemMax) ->
+// item_off[], in one block.  n may exceed the block size; each thread scans
+// a contiguous run, then the run totals are scanned across the block.
+__global__ void k_scan(const uint32_t* __restrict__ count, int n, uint32_t* __restrict__ offsets,
+                       uint32_t* __restrict__ item_off, uint32_t* __restrict__ cursor) {
+    __shared__ uint32_t s_a[1024];
+    __shared__ uint32_t s_b[1024];
+    const int tid = threadIdx.x;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, tid * per), hi = min(n, lo + per);
+    uint32_t sa = 0, sb = 0;
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t c = count[i];
+        sa += c;
+        sb += (c + kItemMax - 1) / kItemMax;
+    }
+    s_a[tid] = sa;
+    s_b[tid] = sb;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the run totals
+    for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+        uint32_t xa = 0, xb = 0;
+        if (tid >= d) {
+            xa = s_a[tid - d];
+            xb = s_b[tid - d];
+        }
+        __syncthreads();
+        s_a[tid] += xa;
+        s_b[tid] += xb;
+        __syncthreads();
+    }
+    uint32_t ra = s_a[tid] - sa, rb = s_b[tid] - sb;
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t c = count[i];
+        offsets[i] = ra;
+        item_off[i] = rb;
+        cursor[i] = 0;
+        ra += c;
+        rb += (c + kItemMax - 1) / kItemMax;
+    }
+    if (tid == blockDim.x - 1) {
+        offsets[n] = s_a[tid];
+        item_off[n] = s_b[tid];
+    }
+}
+
+__global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, int mode, int P,
+                          int smin, int smax, int side, const uint32_t* __restrict__ offsets,
+                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const gw_index_rec r = load_rec(rec, i);
+        if (!(r.flags & GW_FLAG_VALID)) continue;
+        const TileRange t = tile_range(r, mode, P, smin, smax);
+        for (int tv = t.tv0; tv <= t.tv1; ++tv)
+            for (int tu = t.tu0; tu <= t.tu1; ++tu) {
+                const int tile = tv * side + tu;
+                const uint32_t pos = atomicAdd(cursor + tile, 1u);
+                entries[offsets[tile] + pos] = (uint32_t)i;
+            }
+    }
+}
+
+__global__ void k_items(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offsets,
+                        const uint32_t* __restrict__ item_off, int ntiles, Item* __restrict__ items) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        const uint32_t c = count[t];
+        uint32_t o = item_off[t];
+        for (uint32_t s = 0; s < c; s += kItemMax, ++o) {
+            Item it;
+            it.tile = t;
+            it.start = (int32_t)(offsets[t] + s);
+            it.len = (int32_t)min((uint32_t)kItemMax, c - s);
+            it.pad = 0;
+            items[o] = it;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_bin(const gw_index_rec* rec, int64_t nvis, int mode, int N, int P, int smin, int smax,
+                Scratch& sc, int side, cudaStream_t s) {
+    const int ntiles = side * side;
+    cudaMemsetAsync(sc.count, 0, sizeof(uint32_t) * ntiles, s);
+    const int threads = 256;
+    int64_t blocks = (nvis + threads - 1) / threads;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    if (nvis > 0) {
+        k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, mode, P, smin, smax, side, sc.count,
+                                                     sc.work);
+        note_launch();
+    }
+    k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, sc.offsets, sc.item_off, sc.cursor);
+    note_launch();
+    if (nvis > 0) {
+        k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, mode, P, smin, smax, side,
+                                                       sc.offsets, sc.cursor, sc.entries);
+        note_launch();
+    }
+    if (mode == 0) {
+        const int tb = (ntiles + 255) / 256;
+        k_items<<<tb, 256, 0, s>>>(sc.count, sc.offsets, sc.item_off, ntiles, sc.items);
+        note_launch();
+    }
+    (void)N;
+}
+
+}  // namespace gw

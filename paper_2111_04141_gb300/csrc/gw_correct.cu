@@ -1,0 +1,63 @@
+// Correction Step (Section 2.3, Algorithm convgridding; Section 3.3.8) and the
+// centre/corner origin shift used around the FFT (Section 3.3.6).
+//
+//   correct: image[pol][i][j] *= s(i, j) h(m_i) h(l_j), s = (-1)^(i+j) when the
+//            image comes from (or goes to) an FFT of a shifted grid, else 1.
+//   shift:   grid[pol][kv][ku] *= (-1)^(kv+ku).
+// For even N, (-1)^(k) before and (-1)^(i) after an unnormalised FFT turn it
+// into the transform with both origins at pixel N/2.
+#include "gw_internal.cuh"
+
+namespace gw {
+
+namespace {
+
+__global__ void k_correct(float2* __restrict__ img, const float* __restrict__ h, int N, int npol,
+                          int shift) {
+    const int64_t n = (int64_t)N * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
+        float m = __ldg(h + i) * __ldg(h + j);
+        if (shift && ((i + j) & 1)) m = -m;
+        for (int p = 0; p < npol; ++p) {
+            float2 v = img[(int64_t)p * n + e];
+            v.x *= m;
+            v.y *= m;
+            img[(int64_t)p * n + e] = v;
+        }
+    }
+}
+
+__global__ void k_shift(float2* __restrict__ g, int N, int npol) {
+    const int64_t n = (int64_t)N * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
+        if (!((i + j) & 1)) continue;
+        for (int p = 0; p < npol; ++p) {
+            float2 v = g[(int64_t)p * n + e];
+            g[(int64_t)p * n + e] = make_float2(-v.x, -v.y);
+        }
+    }
+}
+
+unsigned blocks_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)std::max<int64_t>(b, 1);
+}
+
+}  // namespace
+
+void launch_correct(float2* image, const float* h, int N, int npol, int mode, cudaStream_t s) {
+    k_correct<<<blocks_for((int64_t)N * N), 256, 0, s>>>(image, h, N, npol, mode != 0);
+    note_launch();
+}
+
+void launch_shift(float2* grid, int N, int npol, cudaStream_t s) {
+    k_shift<<<blocks_for((int64_t)N * N), 256, 0, s>>>(grid, N, npol);
+    note_launch();
+}
+
+}  // namespace gw

@@ -1,0 +1,99 @@
+// Index stage: uvw (metres) x frequency -> pixel, oversampled offset, w-plane.
+//
+// This is the pre-processing the thesis moves out of the gridder
+// (Section 3.3.5): each record's uv coordinate becomes integer indices of
+// the beta-oversampled grid (nearest neighbour, Section 2.3.6), and records
+// whose footprint leaves the grid are dropped (Bounded Records Assumption,
+// Section 2.3.1).  Every floating-point step is an explicitly rounded FP64
+// intrinsic, so no multiply-add is ever fused and the result is bit-exact
+// with any IEEE-754 implementation of the same sequence.
+#include "gw_internal.cuh"
+
+namespace gw {
+
+namespace {
+
+struct AxisIdx {
+    long long k, o;
+    bool ok;
+};
+
+__device__ __forceinline__ AxisIdx axis_index(double coord_m, double f, const IndexParams& p) {
+    // u_lambda = (u * f) / c0 ; x = u_lambda * L + N/2 ; q = floor(beta * x + 0.5)
+    const double lam = __ddiv_rn(__dmul_rn(coord_m, f), kC0);
+    const double x = __dadd_rn(__dmul_rn(lam, p.L), p.halfN);
+    const double q = floor(__dadd_rn(__dmul_rn(p.beta_d, x), 0.5));
+    AxisIdx r;
+    r.ok = isfinite(q) && fabs(q) < kQLimit;
+    const long long qi = r.ok ? (long long)q : 0LL;
+    r.k = floor_div(qi + p.beta / 2, p.beta);
+    r.o = qi - r.k * p.beta;
+    return r;
+}
+
+__global__ void k_index(const double* __restrict__ uvw, const double* __restrict__ freq,
+                        int64_t nrow, int nchan, IndexParams p, gw_index_rec* __restrict__ out,
+                        unsigned long long* __restrict__ dropped) {
+    const int64_t nvis = nrow * (int64_t)nchan;
+    unsigned int my_drops = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / nchan;
+        const int chan = (int)(i - row * nchan);
+        const double f = __ldg(freq + chan);
+        const double u = __ldg(uvw + 3 * row + 0);
+        const double v = __ldg(uvw + 3 * row + 1);
+        const AxisIdx au = axis_index(u, f, p);
+        const AxisIdx av = axis_index(v, f, p);
+        int plane = 0;
+        bool conj = false, okw = true;
+        if (p.P > 1) {
+            const double w = __ldg(uvw + 3 * row + 2);
+            const double wl = __ddiv_rn(__dmul_rn(w, f), kC0);
+            const double s = __dmul_rn(__dsqrt_rn(__ddiv_rn(fabs(wl), p.wmax)), p.Pm1_d);
+            const double pf = floor(__dadd_rn(s, 0.5));
+            okw = isfinite(pf);
+            plane = okw ? (int)fmin(pf, p.Pm1_d) : 0;
+            conj = wl < 0.0;
+        }
+        const int h = plane_support(plane, p.P, p.smin, p.smax) / 2;
+        const bool inside = (au.k - h >= 0) && (au.k + h <= p.N - 1) &&
+                            (av.k - h >= 0) && (av.k + h <= p.N - 1);
+        const bool valid = au.ok && av.ok && okw && inside;
+        gw_index_rec r;
+        if (valid) {
+            r.ku = (int32_t)au.k;
+            r.kv = (int32_t)av.k;
+            r.ou = (int16_t)au.o;
+            r.ov = (int16_t)av.o;
+            r.plane = (int16_t)plane;
+            r.flags = (uint16_t)(GW_FLAG_VALID | (conj ? GW_FLAG_CONJ : 0u));
+        } else {
+            r.ku = r.kv = 0;
+            r.ou = r.ov = 0;
+            r.plane = 0;
+            r.flags = 0;
+            ++my_drops;
+        }
+        reinterpret_cast<int4*>(out)[i] = *reinterpret_cast<const int4*>(&r);
+    }
+    // one atomic per warp
+    for (int d = 16; d > 0; d >>= 1) my_drops += __shfl_down_sync(0xffffffffu, my_drops, d);
+    if ((threadIdx.x & 31) == 0 && my_drops) atomicAdd(dropped, (unsigned long long)my_drops);
+}
+
+}  // namespace
+
+void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan,
+                  const IndexParams& prm, gw_index_rec* out, unsigned long long* dropped,
+                  cudaStream_t s) {
+    const int64_t nvis = nrow * (int64_t)nchan;
+    if (nvis <= 0) return;
+    const int threads = 256;
+    int64_t blocks = (nvis + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_index<<<(unsigned)blocks, threads, 0, s>>>(uvw, freq, nrow, nchan, prm, out, dropped);
+    note_launch();
+}
+
+}  // namespace gw

@@ -1,0 +1,224 @@
+"""Python face of the libgw C ABI: a Plan object over torch CUDA tensors.
+
+Only argument marshalling happens here; every step of gridding,
+degridding, index selection, binning, table generation and correction runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import GwError, PlanDesc, PlanInfo, check
+
+_DTYPES = {"c64": _lib.GW_C64, "bf16": _lib.GW_BF16X2, "f16": _lib.GW_F16X2}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream, device):
+    s = torch.cuda.current_stream(device) if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t: torch.Tensor, name: str, dtype, device, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class Plan:
+    """A gridding/degridding plan on one CUDA device (see include/gw.h)."""
+
+    def __init__(self, grid_n: int, cell_rad: float, support_min: int, support_max: int,
+                 oversample: int = 8, n_wplanes: int = 1, w_max_lambda: float = 0.0,
+                 npol: int = 1, vis_dtype: str = "c64", table_dtype: str = "c64",
+                 max_vis_per_call: int = 0, device=None, stream=None):
+        self._lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        d = PlanDesc(grid_n=int(grid_n), cell_rad=float(cell_rad), support_min=int(support_min),
+                     support_max=int(support_max), oversample=int(oversample),
+                     n_wplanes=int(n_wplanes), w_max_lambda=float(w_max_lambda), npol=int(npol),
+                     vis_dtype=_DTYPES[vis_dtype], table_dtype=_DTYPES[table_dtype],
+                     max_vis_per_call=int(max_vis_per_call))
+        self.desc = d
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_create(ctypes.byref(d), _stream_ptr(stream, self.device),
+                                           ctypes.byref(self._h)), "gw_plan_create")
+        info = PlanInfo()
+        check(self._lib.gw_plan_info_get(self._h, ctypes.byref(info)), "gw_plan_info_get")
+        self.info = info
+        self.grid_n = int(grid_n)
+        self.npol = int(npol)
+
+    @classmethod
+    def from_observation(cls, obs, **kw):
+        args = dict(obs.plan_kwargs())
+        args.update(kw)
+        return cls(**args)
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            with torch.cuda.device(self.device):
+                torch.cuda.synchronize(self.device)
+                self._lib.gw_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def _coords(self, uvw, freq):
+        _need(uvw, "uvw", torch.float64, self.device)
+        _need(freq, "freq", torch.float64, self.device)
+        if uvw.dim() != 2 or uvw.shape[1] != 3:
+            raise ValueError("uvw must be [nrow, 3]")
+        if freq.dim() != 1:
+            raise ValueError("freq must be [nchan]")
+        return int(uvw.shape[0]), int(freq.shape[0])
+
+    def new_grid(self) -> torch.Tensor:
+        return torch.zeros((self.npol, self.grid_n, self.grid_n), dtype=torch.complex64,
+                           device=self.device)
+
+    def grid(self, uvw, freq, vis, weight=None, out=None, stream=None, return_dropped=False):
+        """Accumulate vis [nrow, nchan, npol] onto out (new zero grid if None)."""
+        nrow, nchan = self._coords(uvw, freq)
+        _need(vis, "vis", torch.complex64, self.device, (nrow, nchan, self.npol))
+        if weight is not None:
+            _need(weight, "weight", torch.float32, self.device, (nrow, nchan, self.npol))
+        if out is None:
+            out = self.new_grid()
+        _need(out, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        dropped = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_vis(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(vis),
+                                        _ptr(weight), _ptr(out),
+                                        ctypes.byref(dropped) if return_dropped else None,
+                                        _stream_ptr(stream, self.device)), "gw_grid_vis")
+        return (out, int(dropped.value)) if return_dropped else out
+
+    def degrid(self, uvw, freq, grid, out=None, stream=None, return_dropped=False):
+        """Visibilities [nrow, nchan, npol] from grid [npol, N, N] (overwrites out)."""
+        nrow, nchan = self._coords(uvw, freq)
+        _need(grid, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        if out is None:
+            out = torch.empty((nrow, nchan, self.npol), dtype=torch.complex64, device=self.device)
+        _need(out, "vis_out", torch.complex64, self.device, (nrow, nchan, self.npol))
+        dropped = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_degrid_vis(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(grid),
+                                          _ptr(out),
+                                          ctypes.byref(dropped) if return_dropped else None,
+                                          _stream_ptr(stream, self.device)), "gw_degrid_vis")
+        return (out, int(dropped.value)) if return_dropped else out
+
+    def correct(self, image, direction: int = 1, stream=None):
+        _need(image, "image", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_correct(self._h, _ptr(image), int(direction),
+                                            _stream_ptr(stream, self.device)), "gw_grid_correct")
+        return image
+
+    def shift(self, grid, stream=None):
+        _need(grid, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_shift(self._h, _ptr(grid), _stream_ptr(stream, self.device)),
+                  "gw_grid_shift")
+        return grid
+
+    def index(self, uvw, freq, stream=None):
+        """Raw index records as an int32 tensor [nvis, 4] plus the drop count.
+
+        Column 0 = ku, 1 = kv, 2 = (ou & 0xffff) | (ov << 16), 3 = plane | flags << 16.
+        """
+        nrow, nchan = self._coords(uvw, freq)
+        out = torch.empty((nrow * nchan, 4), dtype=torch.int32, device=self.device)
+        dropped = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_index_vis(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(out),
+                                         ctypes.byref(dropped), _stream_ptr(stream, self.device)),
+                  "gw_index_vis")
+        return out, int(dropped.value)
+
+    @staticmethod
+    def unpack_index(raw: np.ndarray) -> dict:
+        raw = np.ascontiguousarray(raw, dtype=np.int32)
+        h16 = raw[:, 2:4].copy().view(np.int16).reshape(-1, 4)
+        return dict(ku=raw[:, 0].astype(np.int64), kv=raw[:, 1].astype(np.int64),
+                    ou=h16[:, 0].astype(np.int64), ov=h16[:, 1].astype(np.int64),
+                    plane=h16[:, 2].astype(np.int64),
+                    flags=h16[:, 3].astype(np.uint16).astype(np.int64))
+
+    def tables(self):
+        P = self.info.n_wplanes
+        buf = np.empty(2 * self.info.table_elems, dtype=np.float32)
+        offs = np.empty(P + 1, dtype=np.int64)
+        sup = np.empty(P, dtype=np.int32)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_copy_tables(self._h, buf.ctypes.data_as(ctypes.c_void_p),
+                                                offs.ctypes.data_as(ctypes.c_void_p),
+                                                sup.ctypes.data_as(ctypes.c_void_p)),
+                  "gw_plan_copy_tables")
+        return buf.view(np.complex64), offs, sup
+
+    def corrector(self):
+        h = np.empty(self.grid_n, dtype=np.float64)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_copy_corrector(self._h, h.ctypes.data_as(ctypes.c_void_p)),
+                  "gw_plan_copy_corrector")
+        return h
+
+    def timing(self, enable=None):
+        """With ``enable`` set, switch stage timing on/off; otherwise return and
+        reset the accumulated per-stage timings and work counters as a dict."""
+        if enable is not None:
+            check(self._lib.gw_plan_timing_enable(self._h, int(bool(enable))),
+                  "gw_plan_timing_enable")
+            return None
+        t = _lib.Timing()
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_timing_get(self._h, ctypes.byref(t)), "gw_plan_timing_get")
+        return {name: getattr(t, name) for name, _ in t._fields_}
+
+    def debug_bins(self, uvw, freq, mode: int = 0, capacity: Optional[int] = None, stream=None):
+        nrow, nchan = self._coords(uvw, freq)
+        side = (self.grid_n + self.info.tile - 1) // self.info.tile
+        offs = np.empty(side * side + 1, dtype=np.int64)
+        cap = capacity if capacity is not None else max(1, nrow * nchan * 16)
+        ent = np.empty(cap, dtype=np.uint32)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_debug_bins(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, int(mode),
+                                          offs.ctypes.data_as(ctypes.c_void_p),
+                                          ent.ctypes.data_as(ctypes.c_void_p), cap,
+                                          _stream_ptr(stream, self.device)), "gw_debug_bins")
+        return offs, ent[:offs[-1]]
+
+
+def launch_count() -> int:
+    return int(_lib.load().gw_launch_count())

@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: index records, bin counts and bin membership are bit-exact;
+FP32 grids and degridded visibilities within relative L2 1e-5 of the FP64
+oracle; kernel tables within 2e-7 of the table's peak (FP32 storage of FP64
+values); the corrector within 1e-9 relative.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle.cgrid import Oracle
+from oracle.image import centred_idft, correct
+from oracle.index import index_vis
+from oracle.wkernel import C0, KernelTables, Params, corrector, plane_support
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRID = 1e-5
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "index_cases.txt")
+
+
+@pytest.fixture(scope="module")
+def gw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_04141_gb300 import build as b
+    b.build()
+    import paper_2111_04141_gb300 as gw
+    return gw
+
+
+DEV = torch.device("cuda", 0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+_ORACLES = {}
+
+
+def oracle_for(prm):
+    if prm not in _ORACLES:
+        _ORACLES[prm] = Oracle(prm)
+    return _ORACLES[prm]
+
+
+CASES = {
+    "2d": lambda: syn.config_2d(),
+    "small-w": lambda: syn.small_case(n_ant=7, n_times=10, n_chan=3, npol=4, grid_n=128,
+                                      s_min=7, s_max=21, n_w=5, diameter_m=1500.0),
+    "ragged": lambda: syn.small_case(n_ant=5, n_times=7, n_chan=5, npol=3, grid_n=90, s_min=5,
+                                     s_max=13, n_w=3, diameter_m=900.0, beta=4, seed=3),
+    "npol2-beta16": lambda: syn.small_case(n_ant=6, n_times=9, n_chan=2, npol=2, grid_n=160,
+                                           s_min=9, s_max=9, n_w=1, diameter_m=1200.0,
+                                           beta=16, seed=5),
+    "bigS": lambda: syn.small_case(n_ant=6, n_times=12, n_chan=2, npol=1, grid_n=256,
+                                   s_min=15, s_max=63, n_w=6, diameter_m=1500.0, seed=9),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    obs = CASES[request.param]()
+    return request.param, obs, Params(**obs.plan_kwargs())
+
+
+# ---------------------------------------------------------------------------
+# index stage (bit-exact)
+# ---------------------------------------------------------------------------
+
+def _gpu_index(gw, plan, uvw, freq):
+    raw, dropped = plan.index(dev(uvw), dev(freq))
+    return gw.Plan.unpack_index(raw.cpu().numpy()), dropped
+
+
+def test_index_bit_exact(gw, case):
+    name, obs, prm = case
+    with gw.Plan.from_observation(obs) as plan:
+        got, dropped = _gpu_index(gw, plan, obs.uvw_m, obs.freq_hz)
+    ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
+    for key in ("ku", "kv", "ou", "ov", "plane", "flags"):
+        assert np.array_equal(got[key], ref[key]), (name, key)
+    assert dropped == int((~ref["valid"]).sum())
+
+
+def test_index_golden_edges(gw):
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    uvw = np.array([[float(r[0]), float(r[1]), float(r[2])] for r in rows])
+    want = np.array([[int(x) for x in r[3:9]] for r in rows])
+    with gw.Plan(grid_n=16, cell_rad=1.0 / 16, support_min=7, support_max=11, oversample=8,
+                 n_wplanes=3, w_max_lambda=4.0, npol=1) as plan:
+        got, _ = _gpu_index(gw, plan, uvw, np.array([C0]))
+    g = np.stack([got["ku"], got["kv"], got["ou"], got["ov"], got["plane"], got["flags"]], 1)
+    assert np.array_equal(g, want)
+
+
+def test_index_random_ties_and_extremes(gw):
+    """Coordinates on exact fine-grid ties and random magnitudes."""
+    rng = np.random.default_rng(17)
+    prm = Params(grid_n=64, cell_rad=1.0 / 64, support_min=7, support_max=15, oversample=8,
+                 n_wplanes=4, w_max_lambda=9.0, npol=1)
+    n = 5000
+    u = np.concatenate([rng.integers(-300, 300, n) / 16.0, rng.normal(0, 20, n)])
+    v = np.concatenate([rng.integers(-300, 300, n) / 16.0, rng.normal(0, 20, n)])
+    w = np.concatenate([rng.integers(-40, 40, n) / 4.0, rng.normal(0, 6, n)])
+    uvw = np.stack([u, v, w], 1)
+    uvw[::97, 0] = np.inf
+    uvw[::89, 2] = np.nan
+    uvw[::83, 1] = 1e15
+    freq = np.array([C0, 0.75 * C0, 1.5 * C0])
+    with gw.Plan(**prm.__dict__) as plan:
+        got, _ = _gpu_index(gw, plan, uvw, freq)
+    ref = index_vis(uvw, freq, prm)
+    for key in ("ku", "kv", "ou", "ov", "plane", "flags"):
+        assert np.array_equal(got[key], ref[key]), key
+
+
+# ---------------------------------------------------------------------------
+# tables and corrector
+# ---------------------------------------------------------------------------
+
+def test_tables_match_oracle(gw, case):
+    name, obs, prm = case
+    orc = oracle_for(prm)
+    with gw.Plan.from_observation(obs) as plan:
+        tab, offs, sup = plan.tables()
+        h = plan.corrector()
+    assert list(sup) == list(plane_support(prm))
+    flat, roffs = orc.tables.flat()
+    assert list(offs) == list(roffs)
+    peak = np.max(np.abs(flat))
+    assert np.max(np.abs(tab.astype(np.complex128) - flat)) <= 2e-7 * peak
+    href = corrector(prm)
+    assert np.max(np.abs(h - href) / np.abs(href)) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+# binner
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_bins(gw, case, mode):
+    name, obs, prm = case
+    ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
+    tile = 32
+    side = (prm.grid_n + tile - 1) // tile
+    S = plane_support(prm)
+    want = [[] for _ in range(side * side)]
+    for i in np.nonzero(ref["valid"])[0]:
+        h = int(S[ref["plane"][i]]) // 2
+        ku, kv = int(ref["ku"][i]), int(ref["kv"][i])
+        if mode == 1:
+            want[(kv // tile) * side + ku // tile].append(i)
+            continue
+        for tv in range((kv - h) // tile, (kv + h) // tile + 1):
+            for tu in range((ku - h) // tile, (ku + h) // tile + 1):
+                want[tv * side + tu].append(i)
+    with gw.Plan.from_observation(obs) as plan:
+        offs, ent = plan.debug_bins(dev(obs.uvw_m), dev(obs.freq_hz), mode=mode)
+    counts = np.diff(offs)
+    assert list(counts) == [len(w) for w in want]
+    for t in range(side * side):
+        assert sorted(ent[offs[t]:offs[t + 1]].tolist()) == want[t]
+
+
+# ---------------------------------------------------------------------------
+# gridding / degridding
+# ---------------------------------------------------------------------------
+
+def test_grid_matches_oracle(gw, case):
+    name, obs, prm = case
+    orc = oracle_for(prm)
+    ref = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis)
+    with gw.Plan.from_observation(obs) as plan:
+        g, dropped = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis),
+                               return_dropped=True)
+    got = g.cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, ref) <= TOL_GRID, name
+    assert dropped == int((~orc.index(obs.uvw_m, obs.freq_hz)["valid"]).sum())
+
+
+def test_grid_weights_accumulate_and_chunks(gw):
+    obs = CASES["small-w"]()
+    prm = Params(**obs.plan_kwargs())
+    orc = oracle_for(prm)
+    wt = syn.random_weights(obs)
+    ref = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis, weight=wt)
+    # a small chunk size forces several internal chunks with a ragged last one
+    with gw.Plan.from_observation(obs, max_vis_per_call=37 * obs.nchan + 1) as plan:
+        g = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis), weight=dev(wt))
+        got = g.cpu().numpy().astype(np.complex128)
+        assert rel_l2(got, ref) <= TOL_GRID
+        plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis), weight=dev(wt), out=g)
+        assert rel_l2(g.cpu().numpy().astype(np.complex128), 2 * ref) <= TOL_GRID
+
+
+def test_grid_empty_and_all_dropped(gw):
+    obs = CASES["small-w"]()
+    with gw.Plan.from_observation(obs) as plan:
+        e3 = torch.zeros((0, 3), dtype=torch.float64, device=DEV)
+        f = dev(obs.freq_hz)
+        v = torch.zeros((0, obs.nchan, obs.npol), dtype=torch.complex64, device=DEV)
+        g, dropped = plan.grid(e3, f, v, return_dropped=True)
+        assert dropped == 0 and not torch.any(g != 0)
+        far = obs.uvw_m * 1e6
+        g, dropped = plan.grid(dev(far), f, dev(obs.vis), return_dropped=True)
+        assert dropped == obs.nvis and not torch.any(g != 0)
+        vo, dropped = plan.degrid(dev(far), f, plan.new_grid() + 1, return_dropped=True)
+        assert dropped == obs.nvis and not torch.any(vo != 0)
+
+
+def test_degrid_matches_oracle(gw, case):
+    name, obs, prm = case
+    orc = oracle_for(prm)
+    rng = np.random.default_rng(21)
+    N = prm.grid_n
+    grid = (rng.normal(size=(prm.npol, N, N)) + 1j * rng.normal(size=(prm.npol, N, N)))
+    grid = grid.astype(np.complex64)
+    ref = orc.degrid(obs.uvw_m, obs.freq_hz, grid.astype(np.complex128))
+    with gw.Plan.from_observation(obs) as plan:
+        v = plan.degrid(dev(obs.uvw_m), dev(obs.freq_hz), dev(grid))
+    got = v.cpu().numpy().reshape(ref.shape).astype(np.complex128)
+    assert rel_l2(got, ref) <= TOL_GRID, name
+
+
+def test_adjoint_dot_gpu(gw):
+    obs = CASES["small-w"]()
+    rng = np.random.default_rng(3)
+    N = obs.grid_n
+    y = (rng.normal(size=(obs.npol, N, N)) + 1j * rng.normal(size=(obs.npol, N, N)))
+    y = y.astype(np.complex64)
+    with gw.Plan.from_observation(obs) as plan:
+        gx = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)).cpu().numpy()
+        ghy = plan.degrid(dev(obs.uvw_m), dev(obs.freq_hz), dev(y)).cpu().numpy()
+    lhs = np.vdot(y.astype(np.complex128), gx.astype(np.complex128))
+    rhs = np.vdot(ghy.astype(np.complex128), obs.vis.astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+# ---------------------------------------------------------------------------
+# correction + shift
+# ---------------------------------------------------------------------------
+
+def test_correction_pipeline_matches_oracle(gw):
+    obs = CASES["small-w"]()
+    prm = Params(**obs.plan_kwargs())
+    orc = oracle_for(prm)
+    ref_grid = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis)
+    ref_img = correct(centred_idft(ref_grid), corrector(prm))
+    with gw.Plan.from_observation(obs) as plan:
+        g = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis))
+        plan.shift(g)
+        img = torch.fft.ifft2(g, norm="forward")      # unnormalised inverse FFT
+        plan.correct(img, direction=+1)
+        got = img.cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, ref_img) <= 2e-5
+    # direction 0: correction only
+    x = (np.arange(prm.npol * prm.grid_n ** 2).reshape(prm.npol, prm.grid_n, prm.grid_n) % 7
+         + 1j).astype(np.complex64)
+    with gw.Plan.from_observation(obs) as plan:
+        t = dev(x)
+        plan.correct(t, direction=0)
+        h = corrector(prm)
+        assert rel_l2(t.cpu().numpy(), x * (h[:, None] * h[None, :])) <= 1e-6
+
+
+def test_launch_count_increases(gw):
+    obs = CASES["2d"]()
+    before = gw.launch_count()
+    with gw.Plan.from_observation(obs) as plan:
+        plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis))
+    assert gw.launch_count() > before
