@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0,
                     help="rows of the workload in the CPU-baseline sample (0 = 1/8 of rows)")
+    ap.add_argument("--times", type=int, default=256,
+                    help="time steps of the workload (256 = the full workload)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="plan + warm-up + one gridding call, no timing or JSON (for ncu)")
     return ap.parse_args()
 
 
@@ -210,7 +214,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    obs = syn.config_wproj(seed_offset=rank)
+    obs = syn.config_wproj(seed_offset=rank, n_times=args.times)
     plan = gw.Plan.from_observation(obs)
     uvw = torch.from_numpy(obs.uvw_m).to(dev)
     freq = torch.from_numpy(obs.freq_hz).to(dev)
@@ -221,6 +225,11 @@ def main():
     for _ in range(max(3, args.warmup)):
         plan.grid(uvw, freq, vis, out=grid)
     torch.cuda.synchronize(dev)
+    if args.profile_only:
+        plan.grid(uvw, freq, vis, out=grid)
+        torch.cuda.synchronize(dev)
+        plan.close()
+        return
     plan.timing(True)
     plan.timing()  # reset counters
 

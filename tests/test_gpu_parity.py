@@ -3,7 +3,8 @@
 Tolerances: index records, bin counts and bin membership are bit-exact;
 FP32 grids and degridded visibilities within relative L2 1e-5 of the FP64
 oracle; kernel tables within 2e-7 of the table's peak (FP32 storage of FP64
-values); the corrector within 1e-9 relative.
+values); the corrector's reciprocal within 1e-12 absolute (and h within
+1e-9 relative where |h| < 1e3).
 """
 import os
 
@@ -140,7 +141,12 @@ def test_tables_match_oracle(gw, case):
     peak = np.max(np.abs(flat))
     assert np.max(np.abs(tab.astype(np.complex128) - flat)) <= 2e-7 * peak
     href = corrector(prm)
-    assert np.max(np.abs(h - href) / np.abs(href)) <= 1e-9
+    # 1/h = chat * sinc is a sum of O(1) terms: compare it absolutely (h itself
+    # reaches 1e9 at the field edge for wide tapers, where both sides lose
+    # relative precision to cancellation)
+    assert np.max(np.abs(1.0 / h - 1.0 / href)) <= 1e-12
+    mid = np.abs(href) < 1e3
+    assert np.max(np.abs(h[mid] - href[mid]) / np.abs(href[mid])) <= 1e-9
 
 
 # ---------------------------------------------------------------------------
