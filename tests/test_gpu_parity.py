@@ -257,21 +257,33 @@ def test_adjoint_dot_gpu(gw):
 # ---------------------------------------------------------------------------
 
 def test_correction_pipeline_matches_oracle(gw):
+    """shift -> unnormalised inverse FFT -> correct(+1) equals the oracle's
+    centred IDFT x h(m) h(l).  The corrector grows towards the field edge
+    (h^2 ~ 1e7 in the corners for S_min = 7), amplifying FP32 FFT rounding
+    there, so the corrected image is compared over the central half (where
+    the thesis evaluates images) and the uncorrected transform everywhere."""
     obs = CASES["small-w"]()
     prm = Params(**obs.plan_kwargs())
     orc = oracle_for(prm)
     ref_grid = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis)
-    ref_img = correct(centred_idft(ref_grid), corrector(prm))
+    ref_raw = centred_idft(ref_grid)
+    ref_img = correct(ref_raw, corrector(prm))
+    N = prm.grid_n
+    c = slice(N // 4, 3 * N // 4)
     with gw.Plan.from_observation(obs) as plan:
         g = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis))
         plan.shift(g)
         img = torch.fft.ifft2(g, norm="forward")      # unnormalised inverse FFT
+        raw = img.clone()
         plan.correct(img, direction=+1)
         got = img.cpu().numpy().astype(np.complex128)
-    assert rel_l2(got, ref_img) <= 2e-5
+        rawn = raw.cpu().numpy().astype(np.complex128)
+    ii = np.arange(N)
+    checker = np.where((ii[:, None] + ii[None, :]) % 2 == 1, -1.0, 1.0)
+    assert rel_l2(rawn * checker, ref_raw) <= 2e-5
+    assert rel_l2(got[:, c, c], ref_img[:, c, c]) <= 2e-5
     # direction 0: correction only
-    x = (np.arange(prm.npol * prm.grid_n ** 2).reshape(prm.npol, prm.grid_n, prm.grid_n) % 7
-         + 1j).astype(np.complex64)
+    x = (np.arange(prm.npol * N ** 2).reshape(prm.npol, N, N) % 7 + 1j).astype(np.complex64)
     with gw.Plan.from_observation(obs) as plan:
         t = dev(x)
         plan.correct(t, direction=0)
