@@ -50,6 +50,9 @@ struct gw_plan_s {
     int64_t chunk = 0;
     // device state
     float2* table = nullptr;
+    float2* ptable = nullptr;
+    std::vector<int64_t> pplane_off;
+    int64_t* d_pplane_off = nullptr;
     int64_t* d_plane_off = nullptr;
     int* d_support = nullptr;
     double* d_h = nullptr;
@@ -71,6 +74,8 @@ void plan_free(gw_plan p) {
     for (auto e : p->pool) cudaEventDestroy(e);
     cudaFree(p->sc.work);
     cudaFree(p->table);
+    cudaFree(p->ptable);
+    cudaFree(p->d_pplane_off);
     cudaFree(p->d_plane_off);
     cudaFree(p->d_support);
     cudaFree(p->d_h);
@@ -245,15 +250,18 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     p->wplane.resize(P);
     p->plane_off.resize(P + 1);
     p->plane_off[0] = 0;
+    p->pplane_off.resize(P + 1);
+    p->pplane_off[0] = 0;
     int smax_real = 0;
     for (int q = 0; q < P; ++q) {
         p->support[q] = plane_support(q, P, desc->support_min, desc->support_max);
         const double r = P > 1 ? (double)q / (double)(P - 1) : 0.0;
         p->wplane[q] = P > 1 ? desc->w_max_lambda * (r * r) : 0.0;
         p->plane_off[q + 1] = p->plane_off[q] + (int64_t)beta * beta * p->support[q] * p->support[q];
+        p->pplane_off[q + 1] = p->pplane_off[q] + padded_table_elems(p->support[q], beta);
         smax_real = std::max(smax_real, p->support[q]);
     }
-    if (p->plane_off[P] >= (int64_t)1 << 31) {
+    if (p->pplane_off[P] >= (int64_t)1 << 31) {
         plan_free(p);
         return fail(GW_EINVAL, "kernel tables exceed 2^31 elements");
     }
@@ -282,6 +290,8 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 #define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { plan_free(p); \
         return fail(GW_ENOMEM, "device allocation of %s failed", #x); } } while (0)
     GW_ALLOC(p->table, (size_t)p->plane_off[P]);
+    GW_ALLOC(p->ptable, (size_t)p->pplane_off[P]);
+    GW_ALLOC(p->d_pplane_off, (size_t)P + 1);
     GW_ALLOC(p->d_plane_off, (size_t)P + 1);
     GW_ALLOC(p->d_support, (size_t)P);
     GW_ALLOC(p->d_h, (size_t)N);
@@ -302,6 +312,9 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     e = cudaMemcpyAsync(p->d_plane_off, p->plane_off.data(), sizeof(int64_t) * (P + 1),
                         cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_pplane_off, p->pplane_off.data(), sizeof(int64_t) * (P + 1),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_support, p->support.data(), sizeof(int) * P,
                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "uploading plane metadata"); }
@@ -320,6 +333,10 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     tb.num_sms = p->num_sms;
     e = build_tables(tb, p->table, p->d_h, p->d_hf, &p->table_scale, s);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "building kernel tables"); }
+    launch_pad_tables(p->table, p->d_plane_off, p->d_pplane_off, p->d_support, P, beta, p->ptable, s);
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "padding kernel tables"); }
     *out = p;
     return GW_OK;
 }
@@ -364,6 +381,8 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
         if (st != GW_OK) return st;
         GridArgs a;
         a.rec = p->sc.rec;
+        a.ptable = p->ptable;
+        a.pplane_off = p->d_pplane_off;
         a.vis = reinterpret_cast<const float2*>(vis) + v0 * npol;
         a.weight = weight ? weight + v0 * npol : nullptr;
         a.table = p->table;

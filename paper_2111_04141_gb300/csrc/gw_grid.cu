@@ -4,145 +4,289 @@
 // (Section 2.4.5) with the w-projection GCF (Section 1.7.1):
 //     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
 //
-// Design (GB300): each CTA owns one kTile x kTile tile of the grid for the
-// whole of a work item (a run of that tile's bin) and keeps the tile's
-// accumulators in registers, so every grid point is read-modify-written once
-// per work item instead of once per visibility.  A warp owns an 8 x 16
-// block of the tile: lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..3,
-// for all polarisations.  Visibilities are staged in shared memory in
-// batches; for each one a warp skips it unless the footprint meets its
-// block, and skips each 8 x 4 slot the footprint's rows miss, so the
-// granularity of wasted multiply-adds is an 8 x 4 patch.  Kernel values come
-// through the read-only cache (the tables stay resident in L2).  Per tap and
-// polarisation the update is 4 FFMA:
+// Design (GB300):
+// * A CTA owns one kTile x kTile tile of the grid for a work item (a run of
+//   that tile's bin) and keeps the tile's accumulators in registers, so each
+//   grid point is committed once per work item (vector atomics, red.global).
+// * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
+//   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
+//   polarisation.
+// * A ninth, producer warp stages batches of records into shared memory
+//   (double-buffered, handed over with named barriers) and, for every record,
+//   appends it to the list of each compute warp whose block its footprint
+//   meets, together with the range of slots its rows meet.  Compute warps
+//   therefore only see records that touch them, and skip untouched slots with
+//   one uniform test.
+// * Kernel values come from zero-padded slices (7 zero columns and 3 zero
+//   rows around each S x S slice), so lanes outside the footprint read zeros
+//   without predication; loads for the next record are issued before the
+//   multiply-adds of the current one.
+// * Per tap and polarisation the update is 4 FFMA:
 //     acc.re += K.re A.re + K.im B.re,  acc.im += K.re A.im + K.im B.im
-// with A = V and B = (-V.im, V.re) (or (V.im, -V.re) for the conjugate
-// kernel), precomputed per visibility, so conjugation costs nothing per tap.
-// Work items of one tile commit with vector atomics (red.global.add); CTAs
-// are persistent and pull items from a queue.
+//   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
+//   kernel, precomputed per record.
 #include "gw_internal.cuh"
 
 namespace gw {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kComputeWarps = 8;
+constexpr int kThreads = (kComputeWarps + 1) * 32;
 constexpr int kBatch = 256;
+constexpr int kBufs = 2;
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
     int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
     return *reinterpret_cast<gw_index_rec*>(&v);
 }
 
-template <int NPOL>
-__global__ void __launch_bounds__(kThreads) k_grid(GridArgs a) {
-    __shared__ int4 s_idx[kBatch];
-    __shared__ float4 s_v[kBatch][NPOL];
-    __shared__ uint32_t s_item;
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
+template <int NPOL>
+struct Smem {
+    int2 rec[kBufs][kBatch];               // (padded-table base of the tile origin, row stride)
+    float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
+    int cnt[kBufs][kComputeWarps];
+    int tile[kBufs];                       // tile of the batch; -1 = end of work
+    int last[kBufs];                       // batch ends its work item
+};
+
+template <int NPOL>
+__global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
-    const int lu = lane & 7, lv = lane >> 3;
-    const uint32_t nitems = *a.item_count;
-    const int N = a.N;
+    const int side = a.ntiles_side;
     const int hb = a.beta / 2;
 
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1u);
-        __syncthreads();
-        const uint32_t it = s_item;
-        __syncthreads();
-        if (it >= nitems) break;
-        const Item item = a.items[it];
-        const int tu0 = (item.tile % a.ntiles_side) * kTile;
-        const int tv0 = (item.tile / a.ntiles_side) * kTile;
-
-        float acc[4][NPOL][2];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) acc[j][p][0] = acc[j][p][1] = 0.f;
-
-        for (int b0 = 0; b0 < item.len; b0 += kBatch) {
-            const int nb = min(kBatch, item.len - b0);
-            if ((int)threadIdx.x < nb) {
-                const uint32_t id = __ldg(a.entries + item.start + b0 + threadIdx.x);
-                const gw_index_rec r = load_rec(a.rec, id);
-                const int S = __ldg(a.support + r.plane);
-                const int64_t off = __ldg(a.plane_off + r.plane) +
-                                    ((int64_t)(r.ov + hb) * a.beta + (r.ou + hb)) * S * S;
-                s_idx[threadIdx.x] = make_int4(r.ku, r.kv, S, (int)off);
-                const bool conj = (r.flags & GW_FLAG_CONJ) != 0;
-#pragma unroll
-                for (int p = 0; p < NPOL; ++p) {
-                    float2 v = __ldg(a.vis + (int64_t)id * NPOL + p);
-                    if (a.weight) {
-                        const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
-                        v.x *= w;
-                        v.y *= w;
+    if (warp == kComputeWarps) {
+        // ------------------------------------------------------------ producer
+        const uint32_t nitems = *a.item_count;
+        int buf = 0, uses = 0;
+        for (;;) {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(a.queue, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            const bool done = it >= nitems;
+            Item item{};
+            if (!done) item = a.items[it];
+            const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
+            for (int b = 0; b < nb_total; ++b) {
+                if (uses >= kBufs) bar_sync(3 + buf, kThreads);  // wait until consumed
+                if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
+                __syncwarp();
+                if (done) {
+                    if (lane == 0) {
+                        sm.tile[buf] = -1;
+                        sm.last[buf] = 1;
                     }
-                    s_v[threadIdx.x][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
-                                               : make_float4(v.x, v.y, -v.y, v.x);
+                } else {
+                    const int tu0 = (item.tile % side) * kTile;
+                    const int tv0 = (item.tile / side) * kTile;
+                    const int b0 = b * kBatch;
+                    const int nb = min(kBatch, item.len - b0);
+                    for (int r = lane; r < nb; r += 32) {
+                        const uint32_t id = __ldg(a.entries + item.start + b0 + r);
+                        const gw_index_rec rc = load_rec(a.rec, id);
+                        const int S = __ldg(a.support + rc.plane), h = S >> 1;
+                        const int SP = S + 14;
+                        const int64_t slice = __ldg(a.pplane_off + rc.plane) +
+                                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
+                                                  (int64_t)(S + 6) * SP;
+                        // padded index of the tile origin relative to this record
+                        const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
+                        sm.rec[buf][r] = make_int2(base, SP);
+                        const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
+#pragma unroll
+                        for (int p = 0; p < NPOL; ++p) {
+                            float2 v = __ldg(a.vis + (int64_t)id * NPOL + p);
+                            if (a.weight) {
+                                const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
+                                v.x *= w;
+                                v.y *= w;
+                            }
+                            sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
+                                                   : make_float4(v.x, v.y, -v.y, v.x);
+                        }
+                        // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
+                        const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
+                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
+                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTile - 1, uhi) >> 3;
+                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTile - 1, vhi) >> 4;
+                        for (int cv = cv0; cv <= cv1; ++cv) {
+                            const int j0 = max(0, vlo - 16 * cv) >> 2;
+                            const int j1 = min(15, vhi - 16 * cv) >> 2;
+                            const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
+                            for (int cu = cu0; cu <= cu1; ++cu) {
+                                const int w = cv * 4 + cu;
+                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
+                                sm.list[buf][w][pos] = e;
+                            }
+                        }
+                    }
+                    if (lane == 0) {
+                        sm.tile[buf] = item.tile;
+                        sm.last[buf] = (b == nb_total - 1);
+                    }
                 }
+                __syncwarp();
+                __threadfence_block();
+                bar_arrive(1 + buf, kThreads);  // batch ready
+                buf ^= 1;
+                ++uses;
             }
-            __syncthreads();
-            for (int r = 0; r < nb; ++r) {
-                const int4 ri = s_idx[r];
-                const int S = ri.z, h = S >> 1;
-                const int du0 = tu0 + bu - ri.x;
-                if (du0 + 7 < -h || du0 > h) continue;
-                const int dv0 = tv0 + bv - ri.y;
-                if (dv0 + 15 < -h || dv0 > h) continue;
-                const int tu = du0 + lu;
-                const bool oku = (tu >= -h) && (tu <= h);
-                float4 V[NPOL];
+            if (done) {
+                // complete the consumers' last release of the other buffer so
+                // that every barrier generation is balanced before exit
+                if (uses >= 2) bar_sync(3 + buf, kThreads);
+                break;
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
+    const int lu = lane & 7, lv = lane >> 3;
+    const float2* __restrict__ tab = a.ptable;
+    const int N = a.N;
+    float acc[4][NPOL][2];
 #pragma unroll
-                for (int p = 0; p < NPOL; ++p) V[p] = s_v[r][p];
-                const float2* krow = a.table + ri.w + (tu + h);
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int dvj = dv0 + 4 * j;
-                    if (dvj + 3 < -h || dvj > h) continue;
-                    const int tv = dvj + lv;
-                    float2 K = make_float2(0.f, 0.f);
-                    if (oku && tv >= -h && tv <= h) K = __ldg(krow + (tv + h) * S);
+        for (int p = 0; p < NPOL; ++p) acc[j][p][0] = acc[j][p][1] = 0.f;
+
+    int buf = 0;
+    for (;;) {
+        bar_sync(1 + buf, kThreads);  // wait for the batch
+        const int tile = sm.tile[buf];
+        if (tile < 0) break;
+        const int last = sm.last[buf];
+        const int n = sm.cnt[buf][warp];
+        const uint32_t* lst = sm.list[buf][warp];
+
+        // software pipeline: kernel values of entry i+1 load during entry i's FMAs
+        float2 Kc0, Kc1, Kc2, Kc3, Kn0 = {}, Kn1 = {}, Kn2 = {}, Kn3 = {};
+        uint32_t ec = 0, en = 0;
+#define GW_LOAD_K(e, K0, K1, K2, K3)                                                  \
+        do {                                                                          \
+            const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
+            const int2 rc_ = sm.rec[buf][r_];                                          \
+            const float2* p_ = tab + rc_.x + (bv + lv) * rc_.y + bu + lu;              \
+            const int st_ = 4 * rc_.y;                                                 \
+            K0 = K1 = K2 = K3 = make_float2(0.f, 0.f);                                 \
+            if (0 >= j0_ && 0 <= j1_) K0 = __ldg(p_);                                  \
+            if (1 >= j0_ && 1 <= j1_) K1 = __ldg(p_ + st_);                            \
+            if (2 >= j0_ && 2 <= j1_) K2 = __ldg(p_ + 2 * st_);                        \
+            if (3 >= j0_ && 3 <= j1_) K3 = __ldg(p_ + 3 * st_);                        \
+        } while (0)
+        if (n > 0) {
+            ec = lst[0];
+            GW_LOAD_K(ec, Kc0, Kc1, Kc2, Kc3);
+        }
+        for (int i = 0; i < n; ++i) {
+            if (i + 1 < n) {
+                en = lst[i + 1];
+                GW_LOAD_K(en, Kn0, Kn1, Kn2, Kn3);
+            }
+            const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
+            float4 V[NPOL];
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
+            const float2 Kc[4] = {Kc0, Kc1, Kc2, Kc3};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= j0 && j <= j1) {
 #pragma unroll
                     for (int p = 0; p < NPOL; ++p) {
-                        acc[j][p][0] = fmaf(K.x, V[p].x, acc[j][p][0]);
-                        acc[j][p][0] = fmaf(K.y, V[p].z, acc[j][p][0]);
-                        acc[j][p][1] = fmaf(K.x, V[p].y, acc[j][p][1]);
-                        acc[j][p][1] = fmaf(K.y, V[p].w, acc[j][p][1]);
+                        acc[j][p][0] = fmaf(Kc[j].x, V[p].x, acc[j][p][0]);
+                        acc[j][p][0] = fmaf(Kc[j].y, V[p].z, acc[j][p][0]);
+                        acc[j][p][1] = fmaf(Kc[j].x, V[p].y, acc[j][p][1]);
+                        acc[j][p][1] = fmaf(Kc[j].y, V[p].w, acc[j][p][1]);
                     }
                 }
             }
-            __syncthreads();
+            ec = en;
+            Kc0 = Kn0;
+            Kc1 = Kn1;
+            Kc2 = Kn2;
+            Kc3 = Kn3;
         }
-        // commit the tile
-        const int u = tu0 + bu + lu;
+#undef GW_LOAD_K
+        if (last) {
+            // commit the tile's accumulators of this work item
+            const int u = (tile % a.ntiles_side) * kTile + bu + lu;
+            const int v0 = (tile / a.ntiles_side) * kTile + bv + lv;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int v = tv0 + bv + 4 * j + lv;
-            if (u >= N || v >= N) continue;
+            for (int j = 0; j < 4; ++j) {
+                const int v = v0 + 4 * j;
 #pragma unroll
-            for (int p = 0; p < NPOL; ++p) {
-                if (acc[j][p][0] != 0.f || acc[j][p][1] != 0.f)
-                    atomicAdd(a.grid + ((int64_t)p * N + v) * N + u,
-                              make_float2(acc[j][p][0], acc[j][p][1]));
+                for (int p = 0; p < NPOL; ++p) {
+                    if (u < N && v < N && (acc[j][p][0] != 0.f || acc[j][p][1] != 0.f))
+                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u,
+                                  make_float2(acc[j][p][0], acc[j][p][1]));
+                    acc[j][p][0] = acc[j][p][1] = 0.f;
+                }
             }
         }
+        bar_arrive(3 + buf, kThreads);  // buffer free
+        buf ^= 1;
     }
 }
 
 template <int NPOL>
 void launch_t(const GridArgs& a, int num_sms, cudaStream_t s) {
+    const size_t smem = sizeof(Smem<NPOL>);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_grid<NPOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL>, kThreads, smem);
     if (per_sm < 1) per_sm = 1;
-    k_grid<NPOL><<<num_sms * per_sm, kThreads, 0, s>>>(a);
+    k_grid<NPOL><<<num_sms * per_sm, kThreads, smem, s>>>(a);
     note_launch();
 }
 
+// Zero-padded copy of the tables: slice (p, o) becomes (S + 6) rows x (S + 14)
+// columns with the S x S values at row 3, column 7.
+__global__ void k_pad_tables(const float2* __restrict__ tab, const int64_t* __restrict__ plane_off,
+                             const int64_t* __restrict__ pplane_off, const int* __restrict__ support,
+                             int P, int beta, float2* __restrict__ ptab) {
+    const int p = blockIdx.y;
+    if (p >= P) return;
+    const int S = support[p], SP = S + 14, SR = S + 6;
+    const int64_t per = (int64_t)SR * SP;
+    const int64_t n = (int64_t)beta * beta * per;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = e / per;
+        const int rem = (int)(e - o * per);
+        const int row = rem / SP - 3, col = rem % SP - 7;
+        float2 v = make_float2(0.f, 0.f);
+        if (row >= 0 && row < S && col >= 0 && col < S)
+            v = tab[plane_off[p] + o * S * S + (int64_t)row * S + col];
+        ptab[pplane_off[p] + e] = v;
+    }
+}
+
 }  // namespace
+
+int64_t padded_table_elems(int S, int beta) { return (int64_t)beta * beta * (S + 6) * (S + 14); }
+
+void launch_pad_tables(const float2* tab, const int64_t* plane_off, const int64_t* pplane_off,
+                       const int* support, int P, int beta, float2* ptab, cudaStream_t s) {
+    k_pad_tables<<<dim3(256, P), 256, 0, s>>>(tab, plane_off, pplane_off, support, P, beta, ptab);
+    note_launch();
+}
 
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s) {
     cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);

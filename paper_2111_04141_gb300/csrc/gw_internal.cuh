@@ -94,6 +94,8 @@ int quad_nodes(double field, double w, int support, int smin);
 // ---- gridding / degridding (gw_grid.cu, gw_degrid.cu) -----------------------
 struct GridArgs {
     const gw_index_rec* rec;
+    const float2* ptable;        // zero-padded tables (launch_pad_tables)
+    const int64_t* pplane_off;   // device [P]: padded plane offsets
     const float2* vis;         // [nvis][npol]
     const float* weight;       // [nvis][npol] or null
     const float2* table;
@@ -107,6 +109,10 @@ struct GridArgs {
     int N, npol, beta, ntiles_side;
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
+// Zero-padded slice layout used by the gridder: (S + 6) rows x (S + 14) columns.
+int64_t padded_table_elems(int S, int beta);
+void launch_pad_tables(const float2* tab, const int64_t* plane_off, const int64_t* pplane_off,
+                       const int* support, int P, int beta, float2* ptab, cudaStream_t s);
 
 struct DegridArgs {
     const gw_index_rec* rec;
