@@ -97,7 +97,8 @@ typedef struct {
 /* Read-only facts about a plan (gw_plan_info). */
 typedef struct {
     int32_t grid_n, npol, oversample, n_wplanes;
-    int32_t tile;             /* grid tile side used by the binner and gridder */
+    int32_t grid_tile_u, grid_tile_v;  /* gridder tile (footprint-mode bins), pixels */
+    int32_t degrid_tile;      /* degridder tile side (centre-mode bins), pixels */
     int32_t device;           /* CUDA device ordinal the plan lives on */
     int64_t table_elems;      /* complex elements in all kernel tables */
     int64_t chunk_vis;        /* visibilities per internal chunk */
@@ -208,11 +209,13 @@ gw_status gw_plan_copy_tables(gw_plan plan, float* out, int64_t* plane_offsets, 
 /* Copy the corrector h(l_i), i = 0..N-1, to host memory (float64).  Synchronous. */
 gw_status gw_plan_copy_corrector(gw_plan plan, double* out);
 
-/* Run index + binning and copy the bins to host memory (tests): tile_offsets
- * receives ntiles + 1 offsets (ntiles = ceil(N/tile)^2), entries receives
- * the binned visibility ids, each visibility appearing once in every tile
- * its footprint touches ("footprint" mode, mode = 0) or once in the tile of
- * its centre pixel (mode = 1).  Order within a tile is unspecified.
+/* Run index + binning and copy the bins to host memory (tests).  Mode 0
+ * ("footprint", the gridder's bins): tiles of grid_tile_u x grid_tile_v
+ * pixels, each visibility listed once in every tile its footprint touches.
+ * Mode 1 ("centre", the degridder's bins): degrid_tile^2 tiles, each
+ * visibility listed once, in the tile of its centre pixel.  Tiles are
+ * row-major (v rows); tile_offsets receives ntiles + 1 offsets, entries the
+ * visibility ids.  Order within a tile is unspecified.
  * `capacity` is the size of `entries`; GW_EINVAL if too small.  Synchronous. */
 gw_status gw_debug_bins(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
                         int32_t nchan, int32_t mode, int64_t* tile_offsets, uint32_t* entries,

@@ -32,7 +32,8 @@ class PlanDesc(ctypes.Structure):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("grid_n", c_i32), ("npol", c_i32), ("oversample", c_i32), ("n_wplanes", c_i32),
-                ("tile", c_i32), ("device", c_i32), ("table_elems", c_i64), ("chunk_vis", c_i64),
+                ("grid_tile_u", c_i32), ("grid_tile_v", c_i32), ("degrid_tile", c_i32),
+                ("device", c_i32), ("table_elems", c_i64), ("chunk_vis", c_i64),
                 ("field", c_f64), ("taper_c", c_f64), ("table_scale", c_f64)]
 
 

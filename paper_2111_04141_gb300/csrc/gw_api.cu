@@ -40,8 +40,9 @@ struct gw_plan_s {
     gw_plan_desc desc{};
     int device = -1;
     int num_sms = 0;
-    int side = 0;        // tiles per grid side
-    int ntiles = 0;
+    BinGeom geom_grid{}, geom_degrid{};
+    int ntiles = 0;      // bins allocated (max over both geometries)
+    int pad_stride = 0;
     double field = 0, table_scale = 0;
     std::vector<int> support;
     std::vector<double> wplane;
@@ -171,8 +172,8 @@ gw_status index_and_bin(gw_plan p, const double* uvw, const double* freq, int64_
     }
     {
         StageTimer t(p, kStBin, s);
-        launch_bin(p->sc.rec, nrow * (int64_t)nchan, mode, p->desc.grid_n, p->desc.n_wplanes,
-                   p->desc.support_min, p->desc.support_max, p->sc, p->side, s);
+        launch_bin(p->sc.rec, nrow * (int64_t)nchan, mode == 0 ? p->geom_grid : p->geom_degrid,
+                   p->desc.n_wplanes, p->desc.support_min, p->desc.support_max, p->sc, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "index/bin launch");
@@ -244,8 +245,9 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 
     const int N = desc->grid_n, P = desc->n_wplanes, beta = desc->oversample;
     p->field = (double)N * desc->cell_rad;
-    p->side = (N + kTile - 1) / kTile;
-    p->ntiles = p->side * p->side;
+    p->geom_grid = BinGeom{0, 7, 5, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
+    p->geom_degrid = BinGeom{1, 5, 5, (N + kTile - 1) / kTile, (N + kTile - 1) / kTile};
+    p->ntiles = std::max(p->geom_grid.ntu * p->geom_grid.ntv, p->geom_degrid.ntu * p->geom_degrid.ntv);
     p->support.resize(P);
     p->wplane.resize(P);
     p->plane_off.resize(P + 1);
@@ -255,18 +257,20 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     int smax_real = 0;
     for (int q = 0; q < P; ++q) {
         p->support[q] = plane_support(q, P, desc->support_min, desc->support_max);
+        smax_real = std::max(smax_real, p->support[q]);
+    }
+    p->pad_stride = padded_stride(smax_real);
+    for (int q = 0; q < P; ++q) {
         const double r = P > 1 ? (double)q / (double)(P - 1) : 0.0;
         p->wplane[q] = P > 1 ? desc->w_max_lambda * (r * r) : 0.0;
         p->plane_off[q + 1] = p->plane_off[q] + (int64_t)beta * beta * p->support[q] * p->support[q];
-        p->pplane_off[q + 1] = p->pplane_off[q] + padded_table_elems(p->support[q], beta);
-        smax_real = std::max(smax_real, p->support[q]);
+        p->pplane_off[q + 1] = p->pplane_off[q] + padded_table_elems(p->support[q], beta, p->pad_stride);
     }
     if (p->pplane_off[P] >= (int64_t)1 << 31) {
         plan_free(p);
         return fail(GW_EINVAL, "kernel tables exceed 2^31 elements");
     }
-    const int span = (smax_real - 1) / kTile + 2;
-    p->max_tiles_per_vis = span * span;
+    p->max_tiles_per_vis = std::max(((smax_real - 1) / kGridTileU + 2) * ((smax_real - 1) / kGridTileV + 2), 1);
     p->chunk = desc->max_vis_per_call > 0 ? desc->max_vis_per_call : ((int64_t)1 << 23);
     if (p->chunk * p->max_tiles_per_vis >= ((int64_t)1 << 32)) {
         plan_free(p);
@@ -333,7 +337,8 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     tb.num_sms = p->num_sms;
     e = build_tables(tb, p->table, p->d_h, p->d_hf, &p->table_scale, s);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "building kernel tables"); }
-    launch_pad_tables(p->table, p->d_plane_off, p->d_pplane_off, p->d_support, P, beta, p->ptable, s);
+    launch_pad_tables(p->table, p->d_plane_off, p->d_pplane_off, p->d_support, P, beta,
+                      p->pad_stride, p->ptable, s);
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "padding kernel tables"); }
@@ -352,7 +357,9 @@ gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
     out->npol = p->desc.npol;
     out->oversample = p->desc.oversample;
     out->n_wplanes = p->desc.n_wplanes;
-    out->tile = kTile;
+    out->grid_tile_u = kGridTileU;
+    out->grid_tile_v = kGridTileV;
+    out->degrid_tile = kTile;
     out->device = p->device;
     out->table_elems = p->plane_off.back();
     out->chunk_vis = p->chunk;
@@ -390,13 +397,14 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
         a.support = p->d_support;
         a.entries = p->sc.entries;
         a.items = p->sc.items;
-        a.item_count = p->sc.item_off + p->ntiles;
+        a.item_count = p->sc.item_off + p->geom_grid.ntu * p->geom_grid.ntv;
         a.queue = p->sc.counters;
         a.grid = reinterpret_cast<float2*>(grid);
         a.N = p->desc.grid_n;
         a.npol = npol;
         a.beta = p->desc.oversample;
-        a.ntiles_side = p->side;
+        a.ntiles_u = p->geom_grid.ntu;
+        a.pad_stride = p->pad_stride;
         {
             StageTimer t(p, kStGrid, s);
             launch_grid(a, p->num_sms, s);
@@ -434,7 +442,7 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = p->sc.entries;
-        a.n_entries = p->sc.offsets + p->ntiles;
+        a.n_entries = p->sc.offsets + p->geom_degrid.ntu * p->geom_degrid.ntv;
         a.vis_out = out;
         a.N = p->desc.grid_n;
         a.npol = npol;
@@ -553,7 +561,8 @@ gw_status gw_debug_bins(gw_plan p, const double* uvw_m, const double* freq_hz, i
     cudaStream_t s = (cudaStream_t)cuda_stream;
     st = index_and_bin(p, uvw_m, freq_hz, nrow, nchan, mode, s);
     if (st != GW_OK) return st;
-    std::vector<uint32_t> offs(p->ntiles + 1);
+    const BinGeom& g = mode == 0 ? p->geom_grid : p->geom_degrid;
+    std::vector<uint32_t> offs(g.ntu * g.ntv + 1);
     cudaError_t e = cudaMemcpyAsync(offs.data(), p->sc.offsets, sizeof(uint32_t) * offs.size(),
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

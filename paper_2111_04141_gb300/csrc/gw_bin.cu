@@ -2,7 +2,7 @@
 //
 // The thesis orders records by their position on the NN grid ("SS" mode,
 // Section 3.3.5) because record order controls commit traffic.  Here the
-// equivalent is a bin per kTile x kTile grid tile:
+// equivalent is a bin per grid tile (2^su x 2^sv pixels):
 //   footprint mode: a record is listed in every tile its S_p x S_p footprint
 //                   touches (the gridder owns a tile and needs all of them);
 //   centre mode:    a record is listed once, in the tile of its pixel (the
@@ -20,18 +20,18 @@ struct TileRange {
     int tu0, tu1, tv0, tv1;
 };
 
-__device__ __forceinline__ TileRange tile_range(const gw_index_rec& r, int mode, int P, int smin,
-                                                int smax) {
+__device__ __forceinline__ TileRange tile_range(const gw_index_rec& r, const BinGeom& g, int P,
+                                                int smin, int smax) {
     TileRange t;
-    if (mode == 1) {
-        t.tu0 = t.tu1 = r.ku / kTile;
-        t.tv0 = t.tv1 = r.kv / kTile;
+    if (g.mode == 1) {
+        t.tu0 = t.tu1 = r.ku >> g.su;
+        t.tv0 = t.tv1 = r.kv >> g.sv;
     } else {
         const int h = plane_support(r.plane, P, smin, smax) / 2;
-        t.tu0 = (r.ku - h) / kTile;
-        t.tu1 = (r.ku + h) / kTile;
-        t.tv0 = (r.kv - h) / kTile;
-        t.tv1 = (r.kv + h) / kTile;
+        t.tu0 = (r.ku - h) >> g.su;
+        t.tu1 = (r.ku + h) >> g.su;
+        t.tv0 = (r.kv - h) >> g.sv;
+        t.tv1 = (r.kv + h) >> g.sv;
     }
     return t;
 }
@@ -41,8 +41,8 @@ __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, int64_
     return *reinterpret_cast<gw_index_rec*>(&v);
 }
 
-__global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, int mode, int P,
-                        int smin, int smax, int side, uint32_t* __restrict__ count,
+__global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, BinGeom g, int P,
+                        int smin, int smax, uint32_t* __restrict__ count,
                         unsigned long long* __restrict__ work) {
     unsigned long long n_valid = 0, n_taps = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
@@ -52,9 +52,9 @@ __global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, int 
         const int S = plane_support(r.plane, P, smin, smax);
         ++n_valid;
         n_taps += (unsigned long long)(S * S);
-        const TileRange t = tile_range(r, mode, P, smin, smax);
+        const TileRange t = tile_range(r, g, P, smin, smax);
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
-            for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(count + tv * side + tu, 1u);
+            for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(count + tv * g.ntu + tu, 1u);
     }
     for (int d = 16; d > 0; d >>= 1) {
         n_valid += __shfl_down_sync(0xffffffffu, n_valid, d);
@@ -112,17 +112,17 @@ __global__ void k_scan(const uint32_t* __restrict__ count, int n, uint32_t* __re
     }
 }
 
-__global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, int mode, int P,
-                          int smin, int smax, int side, const uint32_t* __restrict__ offsets,
+__global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, BinGeom g, int P,
+                          int smin, int smax, const uint32_t* __restrict__ offsets,
                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
          i += (int64_t)gridDim.x * blockDim.x) {
         const gw_index_rec r = load_rec(rec, i);
         if (!(r.flags & GW_FLAG_VALID)) continue;
-        const TileRange t = tile_range(r, mode, P, smin, smax);
+        const TileRange t = tile_range(r, g, P, smin, smax);
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu) {
-                const int tile = tv * side + tu;
+                const int tile = tv * g.ntu + tu;
                 const uint32_t pos = atomicAdd(cursor + tile, 1u);
                 entries[offsets[tile] + pos] = (uint32_t)i;
             }
@@ -147,32 +147,30 @@ __global__ void k_items(const uint32_t* __restrict__ count, const uint32_t* __re
 
 }  // namespace
 
-void launch_bin(const gw_index_rec* rec, int64_t nvis, int mode, int N, int P, int smin, int smax,
-                Scratch& sc, int side, cudaStream_t s) {
-    const int ntiles = side * side;
+void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
+                Scratch& sc, cudaStream_t s) {
+    const int ntiles = g.ntu * g.ntv;
     cudaMemsetAsync(sc.count, 0, sizeof(uint32_t) * ntiles, s);
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     if (nvis > 0) {
-        k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, mode, P, smin, smax, side, sc.count,
-                                                     sc.work);
+        k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, g, P, smin, smax, sc.count, sc.work);
         note_launch();
     }
     k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, sc.offsets, sc.item_off, sc.cursor);
     note_launch();
     if (nvis > 0) {
-        k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, mode, P, smin, smax, side,
-                                                       sc.offsets, sc.cursor, sc.entries);
+        k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, g, P, smin, smax, sc.offsets,
+                                                       sc.cursor, sc.entries);
         note_launch();
     }
-    if (mode == 0) {
+    if (g.mode == 0) {
         const int tb = (ntiles + 255) / 256;
         k_items<<<tb, 256, 0, s>>>(sc.count, sc.offsets, sc.item_off, ntiles, sc.items);
         note_launch();
     }
-    (void)N;
 }
 
 }  // namespace gw

@@ -8,19 +8,20 @@
 // * A CTA owns one kTile x kTile tile of the grid for a work item (a run of
 //   that tile's bin) and keeps the tile's accumulators in registers, so each
 //   grid point is committed once per work item (vector atomics, red.global).
-// * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
-//   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
-//   polarisation.
-// * A ninth, producer warp stages batches of records into shared memory
+// * The tile is 128 (u) x 32 (v).  Sixteen compute warps each own an 8 (u) x
+//   32 (v) column; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..7 ("slots" of
+//   8 x 4 points), for every polarisation.
+// * A seventeenth, producer warp stages batches of records into shared memory
 //   (double-buffered, handed over with named barriers) and, for every record,
 //   appends it to the list of each compute warp whose block its footprint
 //   meets, together with the range of slots its rows meet.  Compute warps
 //   therefore only see records that touch them, and skip untouched slots with
 //   one uniform test.
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
-//   rows around each S x S slice), so lanes outside the footprint read zeros
-//   without predication; loads for the next record are issued before the
-//   multiply-adds of the current one.
+//   rows around each S x S slice, one compile-time row stride per plan), so
+//   lanes outside the footprint read zeros without predication and slot
+//   addresses are immediate offsets; loads for the next record are issued
+//   before the multiply-adds of the current one (ping-pong registers).
 // * Per tap and polarisation the update is 4 FFMA:
 //     acc.re += K.re A.re + K.im B.re,  acc.im += K.re A.im + K.im B.im
 //   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
@@ -31,10 +32,13 @@ namespace gw {
 
 namespace {
 
-constexpr int kComputeWarps = 8;
+constexpr int kComputeWarps = 16;
 constexpr int kThreads = (kComputeWarps + 1) * 32;
 constexpr int kBatch = 256;
 constexpr int kBufs = 2;
+constexpr int kSlots = 8;            // 8 x 4-row slots: a warp block is 8 (u) x 32 (v)
+constexpr int kTileU = 128, kTileV = 32;
+static_assert(kTileU == kGridTileU && kTileV == kGridTileV, "tile shape");
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
     int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
@@ -50,20 +54,20 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 
 template <int NPOL>
 struct Smem {
-    int2 rec[kBufs][kBatch];               // (padded-table base of the tile origin, row stride)
+    int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
     float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
-    uint32_t list[kBufs][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | slot mask << 16
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
 };
 
-template <int NPOL>
-__global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
+template <int NPOL, int SP>
+__global__ void __maxnreg__(120) k_grid(GridArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int side = a.ntiles_side;
+    const int side_u = a.ntiles_u;
     const int hb = a.beta / 2;
 
     if (warp == kComputeWarps) {
@@ -88,21 +92,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                         sm.last[buf] = 1;
                     }
                 } else {
-                    const int tu0 = (item.tile % side) * kTile;
-                    const int tv0 = (item.tile / side) * kTile;
+                    const int tu0 = (item.tile % side_u) * kTileU;
+                    const int tv0 = (item.tile / side_u) * kTileV;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
                     for (int r = lane; r < nb; r += 32) {
                         const uint32_t id = __ldg(a.entries + item.start + b0 + r);
                         const gw_index_rec rc = load_rec(a.rec, id);
                         const int S = __ldg(a.support + rc.plane), h = S >> 1;
-                        const int SP = S + 14;
                         const int64_t slice = __ldg(a.pplane_off + rc.plane) +
                                               ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
                                                   (int64_t)(S + 6) * SP;
                         // padded index of the tile origin relative to this record
-                        const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                        sm.rec[buf][r] = make_int2(base, SP);
+                        sm.rec[buf][r] = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
                         const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
 #pragma unroll
                         for (int p = 0; p < NPOL; ++p) {
@@ -115,20 +117,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                             sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
                                                    : make_float4(v.x, v.y, -v.y, v.x);
                         }
-                        // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
+                        // footprint relative to the tile; slots are 4-row bands
                         const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
-                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
-                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTile - 1, uhi) >> 3;
-                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTile - 1, vhi) >> 4;
-                        for (int cv = cv0; cv <= cv1; ++cv) {
-                            const int j0 = max(0, vlo - 16 * cv) >> 2;
-                            const int j1 = min(15, vhi - 16 * cv) >> 2;
-                            const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
-                            for (int cu = cu0; cu <= cu1; ++cu) {
-                                const int w = cv * 4 + cu;
-                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
-                                sm.list[buf][w][pos] = e;
-                            }
+                        const int vlo = max(0, rc.kv - h - tv0), vhi = min(kTileV - 1, rc.kv + h - tv0);
+                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTileU - 1, uhi) >> 3;
+                        const int j0 = vlo >> 2, j1 = vhi >> 2;
+                        const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
+                        const uint32_t e = (uint32_t)r | (mask << 16);
+                        for (int cu = cu0; cu <= cu1; ++cu) {
+                            const int pos = atomicAdd(&sm.cnt[buf][cu], 1);
+                            sm.list[buf][cu][pos] = e;
                         }
                     }
                     if (lane == 0) {
@@ -153,13 +151,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
     }
 
     // ---------------------------------------------------------------- consumers
-    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
+    const int bu = warp * 8;
     const int lu = lane & 7, lv = lane >> 3;
-    const float2* __restrict__ tab = a.ptable;
+    const float2* __restrict__ tab = a.ptable + lv * SP + bu + lu;
     const int N = a.N;
-    float acc[4][NPOL][2];
+    float acc[kSlots][NPOL][2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < kSlots; ++j)
 #pragma unroll
         for (int p = 0; p < NPOL; ++p) acc[j][p][0] = acc[j][p][1] = 0.f;
 
@@ -172,60 +170,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
         const int n = sm.cnt[buf][warp];
         const uint32_t* lst = sm.list[buf][warp];
 
-        // software pipeline: kernel values of entry i+1 load during entry i's FMAs
-        float2 Kc0, Kc1, Kc2, Kc3, Kn0 = {}, Kn1 = {}, Kn2 = {}, Kn3 = {};
-        uint32_t ec = 0, en = 0;
-#define GW_LOAD_K(e, K0, K1, K2, K3)                                                  \
-        do {                                                                          \
-            const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
-            const int2 rc_ = sm.rec[buf][r_];                                          \
-            const float2* p_ = tab + rc_.x + (bv + lv) * rc_.y + bu + lu;              \
-            const int st_ = 4 * rc_.y;                                                 \
-            K0 = K1 = K2 = K3 = make_float2(0.f, 0.f);                                 \
-            if (0 >= j0_ && 0 <= j1_) K0 = __ldg(p_);                                  \
-            if (1 >= j0_ && 1 <= j1_) K1 = __ldg(p_ + st_);                            \
-            if (2 >= j0_ && 2 <= j1_) K2 = __ldg(p_ + 2 * st_);                        \
-            if (3 >= j0_ && 3 <= j1_) K3 = __ldg(p_ + 3 * st_);                        \
-        } while (0)
+        // rolling prefetch: as soon as slot j of the current record has been
+        // consumed, its register is reloaded with slot j of the next record
+        float2 K[kSlots];
+        uint32_t e = 0;
         if (n > 0) {
-            ec = lst[0];
-            GW_LOAD_K(ec, Kc0, Kc1, Kc2, Kc3);
+            e = lst[0];
+            const float2* p0 = tab + sm.rec[buf][e & 0xffff];
+            const uint32_t m0 = e >> 16;
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j)
+                if (m0 & (1u << j)) K[j] = __ldg(p0 + j * 4 * SP);
         }
         for (int i = 0; i < n; ++i) {
-            if (i + 1 < n) {
-                en = lst[i + 1];
-                GW_LOAD_K(en, Kn0, Kn1, Kn2, Kn3);
-            }
-            const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
+            const uint32_t en = (i + 1 < n) ? lst[i + 1] : 0u;
+            const float2* pn = tab + sm.rec[buf][en & 0xffff];
+            const uint32_t m = e >> 16, mn = en >> 16;
             float4 V[NPOL];
 #pragma unroll
-            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
-            const float2 Kc[4] = {Kc0, Kc1, Kc2, Kc3};
+            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][e & 0xffff][p];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j >= j0 && j <= j1) {
+            for (int j = 0; j < kSlots; ++j) {
+                if (m & (1u << j)) {
 #pragma unroll
                     for (int p = 0; p < NPOL; ++p) {
-                        acc[j][p][0] = fmaf(Kc[j].x, V[p].x, acc[j][p][0]);
-                        acc[j][p][0] = fmaf(Kc[j].y, V[p].z, acc[j][p][0]);
-                        acc[j][p][1] = fmaf(Kc[j].x, V[p].y, acc[j][p][1]);
-                        acc[j][p][1] = fmaf(Kc[j].y, V[p].w, acc[j][p][1]);
+                        acc[j][p][0] = fmaf(K[j].x, V[p].x, acc[j][p][0]);
+                        acc[j][p][0] = fmaf(K[j].y, V[p].z, acc[j][p][0]);
+                        acc[j][p][1] = fmaf(K[j].x, V[p].y, acc[j][p][1]);
+                        acc[j][p][1] = fmaf(K[j].y, V[p].w, acc[j][p][1]);
                     }
                 }
+                if (mn & (1u << j)) K[j] = __ldg(pn + j * 4 * SP);
             }
-            ec = en;
-            Kc0 = Kn0;
-            Kc1 = Kn1;
-            Kc2 = Kn2;
-            Kc3 = Kn3;
+            e = en;
         }
-#undef GW_LOAD_K
         if (last) {
             // commit the tile's accumulators of this work item
-            const int u = (tile % a.ntiles_side) * kTile + bu + lu;
-            const int v0 = (tile / a.ntiles_side) * kTile + bv + lv;
+            const int u = (tile % side_u) * kTileU + bu + lu;
+            const int v0 = (tile / side_u) * kTileV + lv;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kSlots; ++j) {
                 const int v = v0 + 4 * j;
 #pragma unroll
                 for (int p = 0; p < NPOL; ++p) {
@@ -241,29 +225,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
     }
 }
 
-template <int NPOL>
-void launch_t(const GridArgs& a, int num_sms, cudaStream_t s) {
+template <int NPOL, int SP>
+void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
     const size_t smem = sizeof(Smem<NPOL>);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_grid<NPOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    cudaFuncSetAttribute(k_grid<NPOL, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP>, kThreads, smem);
     if (per_sm < 1) per_sm = 1;
-    k_grid<NPOL><<<num_sms * per_sm, kThreads, smem, s>>>(a);
+    k_grid<NPOL, SP><<<num_sms * per_sm, kThreads, smem, s>>>(a);
     note_launch();
 }
 
-// Zero-padded copy of the tables: slice (p, o) becomes (S + 6) rows x (S + 14)
+template <int NPOL>
+void launch_t(const GridArgs& a, int num_sms, cudaStream_t s) {
+    switch (a.pad_stride) {
+        case 24: launch_sp<NPOL, 24>(a, num_sms, s); break;
+        case 32: launch_sp<NPOL, 32>(a, num_sms, s); break;
+        case 48: launch_sp<NPOL, 48>(a, num_sms, s); break;
+        case 80: launch_sp<NPOL, 80>(a, num_sms, s); break;
+        case 144: launch_sp<NPOL, 144>(a, num_sms, s); break;
+        default: launch_sp<NPOL, 272>(a, num_sms, s); break;
+    }
+}
+
+// Zero-padded copy of the tables: slice (p, o) becomes (S + 6) rows x SP
 // columns with the S x S values at row 3, column 7.
 __global__ void k_pad_tables(const float2* __restrict__ tab, const int64_t* __restrict__ plane_off,
                              const int64_t* __restrict__ pplane_off, const int* __restrict__ support,
-                             int P, int beta, float2* __restrict__ ptab) {
+                             int P, int beta, int SP, float2* __restrict__ ptab) {
     const int p = blockIdx.y;
     if (p >= P) return;
-    const int S = support[p], SP = S + 14, SR = S + 6;
+    const int S = support[p], SR = S + 6;
     const int64_t per = (int64_t)SR * SP;
     const int64_t n = (int64_t)beta * beta * per;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -280,11 +272,17 @@ __global__ void k_pad_tables(const float2* __restrict__ tab, const int64_t* __re
 
 }  // namespace
 
-int64_t padded_table_elems(int S, int beta) { return (int64_t)beta * beta * (S + 6) * (S + 14); }
+int padded_stride(int smax) {
+    const int need = smax + 14;
+    for (int sp : {24, 32, 48, 80, 144}) if (need <= sp) return sp;
+    return 272;
+}
+
+int64_t padded_table_elems(int S, int beta, int SP) { return (int64_t)beta * beta * (S + 6) * SP; }
 
 void launch_pad_tables(const float2* tab, const int64_t* plane_off, const int64_t* pplane_off,
-                       const int* support, int P, int beta, float2* ptab, cudaStream_t s) {
-    k_pad_tables<<<dim3(256, P), 256, 0, s>>>(tab, plane_off, pplane_off, support, P, beta, ptab);
+                       const int* support, int P, int beta, int SP, float2* ptab, cudaStream_t s) {
+    k_pad_tables<<<dim3(256, P), 256, 0, s>>>(tab, plane_off, pplane_off, support, P, beta, SP, ptab);
     note_launch();
 }
 

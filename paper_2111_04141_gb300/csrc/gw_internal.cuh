@@ -12,7 +12,9 @@
 namespace gw {
 
 constexpr double kC0 = 299792458.0;   // speed of light, m/s
-constexpr int kTile = 32;             // grid tile side of the binner and gridder
+constexpr int kTile = 32;             // grid tile side of the degridding binner
+constexpr int kGridTileU = 128;       // gridder tile: 128 (u) x 32 (v)
+constexpr int kGridTileV = 32;
 constexpr int kItemMax = 1024;        // max bin entries per gridder work item
 constexpr double kQLimit = 1073741824.0;  // 2^30: |q| bound for a representable record
 
@@ -72,9 +74,13 @@ void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan
 // ---- binner (gw_bin.cu) ----------------------------------------------------
 // mode 0: footprint tiles (every tile a record's footprint touches)
 // mode 1: centre tile (the tile holding pixel (ku, kv))
+// Tiles are 2^su (u) x 2^sv (v) pixels, ntu x ntv of them (row-major, v rows).
+struct BinGeom {
+    int mode, su, sv, ntu, ntv;
+};
 // Also accumulates sc.work[0] += valid records, sc.work[1] += sum of S_p^2.
-void launch_bin(const gw_index_rec* rec, int64_t nvis, int mode, int N, int P, int smin, int smax,
-                Scratch& sc, int ntiles_side, cudaStream_t s);
+void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
+                Scratch& sc, cudaStream_t s);
 
 // ---- kernel tables (gw_tables.cu) -----------------------------------------
 struct TableBuild {
@@ -106,13 +112,16 @@ struct GridArgs {
     const uint32_t* item_count;  // device scalar: item_off[ntiles]
     uint32_t* queue;             // device scalar: work queue head (zeroed before launch)
     float2* grid;                // [npol][N][N]
-    int N, npol, beta, ntiles_side;
+    int N, npol, beta, ntiles_u;  // ntiles_u: gridder tiles along u
+    int pad_stride;              // padded row stride (padded_stride(S_max))
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
-// Zero-padded slice layout used by the gridder: (S + 6) rows x (S + 14) columns.
-int64_t padded_table_elems(int S, int beta);
+// Zero-padded slice layout used by the gridder: (S + 6) rows x SP columns,
+// SP = padded_stride(S_max) >= S_max + 14, one of a few compile-time strides.
+int padded_stride(int smax);
+int64_t padded_table_elems(int S, int beta, int SP);
 void launch_pad_tables(const float2* tab, const int64_t* plane_off, const int64_t* pplane_off,
-                       const int* support, int P, int beta, float2* ptab, cudaStream_t s);
+                       const int* support, int P, int beta, int SP, float2* ptab, cudaStream_t s);
 
 struct DegridArgs {
     const gw_index_rec* rec;

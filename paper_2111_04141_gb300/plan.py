@@ -208,8 +208,12 @@ class Plan:
 
     def debug_bins(self, uvw, freq, mode: int = 0, capacity: Optional[int] = None, stream=None):
         nrow, nchan = self._coords(uvw, freq)
-        side = (self.grid_n + self.info.tile - 1) // self.info.tile
-        offs = np.empty(side * side + 1, dtype=np.int64)
+        if mode == 0:
+            tu, tv = self.info.grid_tile_u, self.info.grid_tile_v
+        else:
+            tu = tv = self.info.degrid_tile
+        ntiles = ((self.grid_n + tu - 1) // tu) * ((self.grid_n + tv - 1) // tv)
+        offs = np.empty(ntiles + 1, dtype=np.int64)
         cap = capacity if capacity is not None else max(1, nrow * nchan * 16)
         ent = np.empty(cap, dtype=np.uint32)
         with torch.cuda.device(self.device):

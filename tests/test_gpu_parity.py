@@ -157,24 +157,25 @@ def test_tables_match_oracle(gw, case):
 def test_bins(gw, case, mode):
     name, obs, prm = case
     ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
-    tile = 32
-    side = (prm.grid_n + tile - 1) // tile
+    tu_, tv_ = (128, 32) if mode == 0 else (32, 32)
+    ntu = (prm.grid_n + tu_ - 1) // tu_
+    ntv = (prm.grid_n + tv_ - 1) // tv_
     S = plane_support(prm)
-    want = [[] for _ in range(side * side)]
+    want = [[] for _ in range(ntu * ntv)]
     for i in np.nonzero(ref["valid"])[0]:
         h = int(S[ref["plane"][i]]) // 2
         ku, kv = int(ref["ku"][i]), int(ref["kv"][i])
         if mode == 1:
-            want[(kv // tile) * side + ku // tile].append(i)
+            want[(kv // tv_) * ntu + ku // tu_].append(i)
             continue
-        for tv in range((kv - h) // tile, (kv + h) // tile + 1):
-            for tu in range((ku - h) // tile, (ku + h) // tile + 1):
-                want[tv * side + tu].append(i)
+        for tv in range((kv - h) // tv_, (kv + h) // tv_ + 1):
+            for tu in range((ku - h) // tu_, (ku + h) // tu_ + 1):
+                want[tv * ntu + tu].append(i)
     with gw.Plan.from_observation(obs) as plan:
         offs, ent = plan.debug_bins(dev(obs.uvw_m), dev(obs.freq_hz), mode=mode)
     counts = np.diff(offs)
     assert list(counts) == [len(w) for w in want]
-    for t in range(side * side):
+    for t in range(ntu * ntv):
         assert sorted(ent[offs[t]:offs[t + 1]].tolist()) == want[t]
 
 
