@@ -11,7 +11,8 @@
 // * The tile is 128 (u) x 32 (v).  Sixteen compute warps each own an 8 (u) x
 //   32 (v) column; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..7 ("slots" of
 //   8 x 4 points), for every polarisation.
-// * A seventeenth, producer warp stages batches of records into shared memory
+// * A producer warp (in a fifth warpgroup that hands registers to the
+//   consumers with setmaxnreg) stages batches of records into shared memory
 //   (double-buffered, handed over with named barriers) and, for every record,
 //   appends it to the list of each compute warp whose block its footprint
 //   meets, together with the range of slots its rows meet.  Compute warps
@@ -22,10 +23,9 @@
 //   lanes outside the footprint read zeros without predication and slot
 //   addresses are immediate offsets; loads for the next record are issued
 //   before the multiply-adds of the current one (ping-pong registers).
-// * Per tap and polarisation the update is 4 FFMA:
-//     acc.re += K.re A.re + K.im B.re,  acc.im += K.re A.im + K.im B.im
-//   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
-//   kernel, precomputed per record.
+// * Per tap and polarisation the update is 4 FFMA (the complex product
+//   K V, or conj(K) V for records with w < 0, chosen by a warp-uniform branch;
+//   operand negation is free in FFMA).
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -33,7 +33,13 @@ namespace gw {
 namespace {
 
 constexpr int kComputeWarps = 16;
-constexpr int kThreads = (kComputeWarps + 1) * 32;
+// Four consumer warpgroups plus one producer warpgroup (one working warp).
+// Register split (setmaxnreg): launched at 96 per thread; the producer
+// warpgroup gives back to 32, the consumers take 112:
+// 128 x 32 + 512 x 112 = 61440 = 640 x 96.
+constexpr int kThreads = (kComputeWarps + 4) * 32;
+constexpr int kSyncThreads = (kComputeWarps + 1) * 32;   // threads in the named barriers
+constexpr int kProducerRegs = 32, kConsumerRegs = 112;
 constexpr int kBatch = 256;
 constexpr int kBufs = 2;
 constexpr int kSlots = 8;            // 8 x 4-row slots: a warp block is 8 (u) x 32 (v)
@@ -55,22 +61,24 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 template <int NPOL>
 struct Smem {
     int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
-    float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
-    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | slot mask << 16
+    float2 v[kBufs][kBatch][NPOL];         // weighted visibility per polarisation
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | slot mask << 16 | conj << 24
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
 };
 
 template <int NPOL, int SP>
-__global__ void __maxnreg__(120) k_grid(GridArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int side_u = a.ntiles_u;
     const int hb = a.beta / 2;
 
-    if (warp == kComputeWarps) {
+    if (warp >= kComputeWarps) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
+        if (warp > kComputeWarps) return;   // only one producer warp works
         // ------------------------------------------------------------ producer
         const uint32_t nitems = *a.item_count;
         int buf = 0, uses = 0;
@@ -83,7 +91,7 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
             if (!done) item = a.items[it];
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
-                if (uses >= kBufs) bar_sync(3 + buf, kThreads);  // wait until consumed
+                if (uses >= kBufs) bar_sync(3 + buf, kSyncThreads);  // wait until consumed
                 if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
                 __syncwarp();
                 if (done) {
@@ -114,8 +122,7 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
                                 v.x *= w;
                                 v.y *= w;
                             }
-                            sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
-                                                   : make_float4(v.x, v.y, -v.y, v.x);
+                            sm.v[buf][r][p] = v;
                         }
                         // footprint relative to the tile; slots are 4-row bands
                         const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
@@ -123,7 +130,7 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
                         const int cu0 = max(0, ulo) >> 3, cu1 = min(kTileU - 1, uhi) >> 3;
                         const int j0 = vlo >> 2, j1 = vhi >> 2;
                         const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
-                        const uint32_t e = (uint32_t)r | (mask << 16);
+                        const uint32_t e = (uint32_t)r | (mask << 16) | ((uint32_t)conj << 24);
                         for (int cu = cu0; cu <= cu1; ++cu) {
                             const int pos = atomicAdd(&sm.cnt[buf][cu], 1);
                             sm.list[buf][cu][pos] = e;
@@ -136,14 +143,14 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
                 }
                 __syncwarp();
                 __threadfence_block();
-                bar_arrive(1 + buf, kThreads);  // batch ready
+                bar_arrive(1 + buf, kSyncThreads);  // batch ready
                 buf ^= 1;
                 ++uses;
             }
             if (done) {
                 // complete the consumers' last release of the other buffer so
                 // that every barrier generation is balanced before exit
-                if (uses >= 2) bar_sync(3 + buf, kThreads);
+                if (uses >= 2) bar_sync(3 + buf, kSyncThreads);
                 break;
             }
         }
@@ -151,6 +158,7 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
     }
 
     // ---------------------------------------------------------------- consumers
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
     const int bu = warp * 8;
     const int lu = lane & 7, lv = lane >> 3;
     const float2* __restrict__ tab = a.ptable + lv * SP + bu + lu;
@@ -163,7 +171,7 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
 
     int buf = 0;
     for (;;) {
-        bar_sync(1 + buf, kThreads);  // wait for the batch
+        bar_sync(1 + buf, kSyncThreads);  // wait for the batch
         const int tile = sm.tile[buf];
         if (tile < 0) break;
         const int last = sm.last[buf];
@@ -185,23 +193,29 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
         for (int i = 0; i < n; ++i) {
             const uint32_t en = (i + 1 < n) ? lst[i + 1] : 0u;
             const float2* pn = tab + sm.rec[buf][en & 0xffff];
-            const uint32_t m = e >> 16, mn = en >> 16;
-            float4 V[NPOL];
+            const uint32_t m = (e >> 16) & 0xff, mn = (en >> 16) & 0xff;
+            float2 V[NPOL];
 #pragma unroll
             for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][e & 0xffff][p];
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) {
-                if (m & (1u << j)) {
-#pragma unroll
-                    for (int p = 0; p < NPOL; ++p) {
-                        acc[j][p][0] = fmaf(K[j].x, V[p].x, acc[j][p][0]);
-                        acc[j][p][0] = fmaf(K[j].y, V[p].z, acc[j][p][0]);
-                        acc[j][p][1] = fmaf(K[j].x, V[p].y, acc[j][p][1]);
-                        acc[j][p][1] = fmaf(K[j].y, V[p].w, acc[j][p][1]);
-                    }
-                }
-                if (mn & (1u << j)) K[j] = __ldg(pn + j * 4 * SP);
+            // K * V, or conj(K) * V for records with w < 0 (warp-uniform branch)
+#define GW_SLOTS(SGN)                                                                   \
+    _Pragma("unroll") for (int j = 0; j < kSlots; ++j) {                                \
+        if (m & (1u << j)) {                                                            \
+            _Pragma("unroll") for (int p = 0; p < NPOL; ++p) {                          \
+                acc[j][p][0] = fmaf(K[j].x, V[p].x, acc[j][p][0]);                      \
+                acc[j][p][0] = fmaf(-(SGN) * K[j].y, V[p].y, acc[j][p][0]);             \
+                acc[j][p][1] = fmaf(K[j].x, V[p].y, acc[j][p][1]);                      \
+                acc[j][p][1] = fmaf((SGN) * K[j].y, V[p].x, acc[j][p][1]);              \
+            }                                                                           \
+        }                                                                               \
+        if (mn & (1u << j)) K[j] = __ldg(pn + j * 4 * SP);                              \
+    }
+            if (e & (1u << 24)) {
+                GW_SLOTS(-1.f)
+            } else {
+                GW_SLOTS(1.f)
             }
+#undef GW_SLOTS
             e = en;
         }
         if (last) {
@@ -220,7 +234,7 @@ __global__ void __maxnreg__(120) k_grid(GridArgs a) {
                 }
             }
         }
-        bar_arrive(3 + buf, kThreads);  // buffer free
+        bar_arrive(3 + buf, kSyncThreads);  // buffer free
         buf ^= 1;
     }
 }
