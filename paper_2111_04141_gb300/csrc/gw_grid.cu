@@ -8,9 +8,9 @@
 // * A CTA owns one kTile x kTile tile of the grid for a work item (a run of
 //   that tile's bin) and keeps the tile's accumulators in registers, so each
 //   grid point is committed once per work item (vector atomics, red.global).
-// * The tile is 128 (u) x 32 (v).  Sixteen compute warps each own an 8 (u) x
-//   32 (v) column; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..7 ("slots" of
-//   8 x 4 points), for every polarisation.
+// * The tile is 64 (u) x 32 (v).  Sixteen compute warps each own an 8 (u) x
+//   16 (v) block; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..3
+//   ("slots" of 8 x 4 points), for every polarisation.
 // * A producer warp (in a fifth warpgroup that hands registers to the
 //   consumers with setmaxnreg) stages batches of records into shared memory
 //   (double-buffered, handed over with named barriers) and, for every record,
@@ -23,9 +23,13 @@
 //   lanes outside the footprint read zeros without predication and slot
 //   addresses are immediate offsets; loads for the next record are issued
 //   before the multiply-adds of the current one (ping-pong registers).
-// * Per tap and polarisation the update is 4 FFMA (the complex product
-//   K V, or conj(K) V for records with w < 0, chosen by a warp-uniform branch;
-//   operand negation is free in FFMA).
+// * Per tap and polarisation the complex update costs two packed FP32x2 FMAs
+//   (Blackwell FFMA2: two multiply-adds per issued instruction, so control
+//   instructions issue in the FMA pipe's spare slots).  Without broadcasting K:
+//     P += K (.) (V.x, -s V.y),  Q += K (.) (V.y, s V.x),
+//     re = P.x + P.y,  im = Q.x + Q.y   at commit,
+//   s = +1, or -1 for records with w < 0 (conj(K) V), folded into the staged
+//   visibility so mixed records share accumulators.
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -35,15 +39,15 @@ namespace {
 constexpr int kComputeWarps = 16;
 // Four consumer warpgroups plus one producer warpgroup (one working warp).
 // Register split (setmaxnreg): launched at 96 per thread; the producer
-// warpgroup gives back to 32, the consumers take 112:
-// 128 x 32 + 512 x 112 = 61440 = 640 x 96.
+// warpgroup gives back to 40, the consumers take 104:
+// 128 x 40 + 512 x 104 = 58368 <= 61440 = 640 x 96.
 constexpr int kThreads = (kComputeWarps + 4) * 32;
 constexpr int kSyncThreads = (kComputeWarps + 1) * 32;   // threads in the named barriers
-constexpr int kProducerRegs = 32, kConsumerRegs = 112;
+constexpr int kProducerRegs = 40, kConsumerRegs = 104;
 constexpr int kBatch = 256;
 constexpr int kBufs = 2;
-constexpr int kSlots = 8;            // 8 x 4-row slots: a warp block is 8 (u) x 32 (v)
-constexpr int kTileU = 128, kTileV = 32;
+constexpr int kSlots = 4;            // 4 x 4-row slots: a warp block is 8 (u) x 16 (v)
+constexpr int kTileU = 64, kTileV = 32;
 static_assert(kTileU == kGridTileU && kTileV == kGridTileV, "tile shape");
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
@@ -61,8 +65,8 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 template <int NPOL>
 struct Smem {
     int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
-    float2 v[kBufs][kBatch][NPOL];         // weighted visibility per polarisation
-    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | slot mask << 16 | conj << 24
+    float4 v[kBufs][kBatch][NPOL];         // (V.x, -s V.y, V.y, s V.x), s = -1 for w < 0
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | slot mask << 8
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                                                   (int64_t)(S + 6) * SP;
                         // padded index of the tile origin relative to this record
                         sm.rec[buf][r] = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                        const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
+                        const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
 #pragma unroll
                         for (int p = 0; p < NPOL; ++p) {
                             float2 v = __ldg(a.vis + (int64_t)id * NPOL + p);
@@ -122,18 +126,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                                 v.x *= w;
                                 v.y *= w;
                             }
-                            sm.v[buf][r][p] = v;
+                            sm.v[buf][r][p] = make_float4(v.x, -sg * v.y, v.y, sg * v.x);
                         }
                         // footprint relative to the tile; slots are 4-row bands
                         const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
-                        const int vlo = max(0, rc.kv - h - tv0), vhi = min(kTileV - 1, rc.kv + h - tv0);
+                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
                         const int cu0 = max(0, ulo) >> 3, cu1 = min(kTileU - 1, uhi) >> 3;
-                        const int j0 = vlo >> 2, j1 = vhi >> 2;
-                        const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
-                        const uint32_t e = (uint32_t)r | (mask << 16) | ((uint32_t)conj << 24);
-                        for (int cu = cu0; cu <= cu1; ++cu) {
-                            const int pos = atomicAdd(&sm.cnt[buf][cu], 1);
-                            sm.list[buf][cu][pos] = e;
+                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTileV - 1, vhi) >> 4;
+                        for (int cv = cv0; cv <= cv1; ++cv) {
+                            const int j0 = max(0, vlo - 16 * cv) >> 2;
+                            const int j1 = min(15, vhi - 16 * cv) >> 2;
+                            const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
+                            const uint32_t e = (uint32_t)r | (mask << 8);
+                            for (int cu = cu0; cu <= cu1; ++cu) {
+                                const int w = cv * 8 + cu;
+                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
+                                sm.list[buf][w][pos] = e;
+                            }
                         }
                     }
                     if (lane == 0) {
@@ -159,15 +168,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
 
     // ---------------------------------------------------------------- consumers
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
-    const int bu = warp * 8;
+    const int bu = (warp & 7) * 8, bv = (warp >> 3) * 16;
     const int lu = lane & 7, lv = lane >> 3;
-    const float2* __restrict__ tab = a.ptable + lv * SP + bu + lu;
+    const float2* __restrict__ tab = a.ptable + (bv + lv) * SP + bu + lu;
     const int N = a.N;
-    float acc[kSlots][NPOL][2];
+    // P = sum K (.) (V.x, -s V.y), Q = sum K (.) (V.y, s V.x):
+    // re = P.x + P.y, im = Q.x + Q.y  (s = -1 for the conjugate kernel)
+    float2 P[kSlots][NPOL], Q[kSlots][NPOL];
 #pragma unroll
     for (int j = 0; j < kSlots; ++j)
 #pragma unroll
-        for (int p = 0; p < NPOL; ++p) acc[j][p][0] = acc[j][p][1] = 0.f;
+        for (int p = 0; p < NPOL; ++p) P[j][p] = Q[j][p] = make_float2(0.f, 0.f);
+
+#define GW_LOAD(K, e)                                                          \
+    do {                                                                       \
+        const float2* p_ = tab + sm.rec[buf][(e) & 0xff];                      \
+        const uint32_t m_ = (e) >> 8;                                          \
+        _Pragma("unroll") for (int j = 0; j < kSlots; ++j)                     \
+            if (m_ & (1u << j)) K[j] = __ldg(p_ + j * 4 * SP);                 \
+    } while (0)
+#define GW_FMA(K, e)                                                           \
+    do {                                                                       \
+        const float4* v_ = sm.v[buf][(e) & 0xff];                              \
+        float4 V[NPOL];                                                        \
+        _Pragma("unroll") for (int p = 0; p < NPOL; ++p) V[p] = v_[p];         \
+        const uint32_t m_ = (e) >> 8;                                          \
+        _Pragma("unroll") for (int j = 0; j < kSlots; ++j) {                   \
+            if (m_ & (1u << j)) {                                              \
+                _Pragma("unroll") for (int p = 0; p < NPOL; ++p) {             \
+                    P[j][p] = __ffma2_rn(K[j], make_float2(V[p].x, V[p].y), P[j][p]); \
+                    Q[j][p] = __ffma2_rn(K[j], make_float2(V[p].z, V[p].w), Q[j][p]); \
+                }                                                              \
+            }                                                                  \
+        }                                                                      \
+    } while (0)
 
     int buf = 0;
     for (;;) {
@@ -177,66 +211,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
         const int last = sm.last[buf];
         const int n = sm.cnt[buf][warp];
         const uint32_t* lst = sm.list[buf][warp];
-
-        // rolling prefetch: as soon as slot j of the current record has been
-        // consumed, its register is reloaded with slot j of the next record
-        float2 K[kSlots];
-        uint32_t e = 0;
+        // two-stage pipeline: kernel values of the next entry load while the
+        // current entry's multiply-adds issue (ping-pong registers)
+        float2 KA[kSlots], KB[kSlots];
+        uint32_t eA = 0, eB = 0;
         if (n > 0) {
-            e = lst[0];
-            const float2* p0 = tab + sm.rec[buf][e & 0xffff];
-            const uint32_t m0 = e >> 16;
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j)
-                if (m0 & (1u << j)) K[j] = __ldg(p0 + j * 4 * SP);
+            eA = lst[0];
+            GW_LOAD(KA, eA);
         }
-        for (int i = 0; i < n; ++i) {
-            const uint32_t en = (i + 1 < n) ? lst[i + 1] : 0u;
-            const float2* pn = tab + sm.rec[buf][en & 0xffff];
-            const uint32_t m = (e >> 16) & 0xff, mn = (en >> 16) & 0xff;
-            float2 V[NPOL];
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][e & 0xffff][p];
-            // K * V, or conj(K) * V for records with w < 0 (warp-uniform branch)
-#define GW_SLOTS(SGN)                                                                   \
-    _Pragma("unroll") for (int j = 0; j < kSlots; ++j) {                                \
-        if (m & (1u << j)) {                                                            \
-            _Pragma("unroll") for (int p = 0; p < NPOL; ++p) {                          \
-                acc[j][p][0] = fmaf(K[j].x, V[p].x, acc[j][p][0]);                      \
-                acc[j][p][0] = fmaf(-(SGN) * K[j].y, V[p].y, acc[j][p][0]);             \
-                acc[j][p][1] = fmaf(K[j].x, V[p].y, acc[j][p][1]);                      \
-                acc[j][p][1] = fmaf((SGN) * K[j].y, V[p].x, acc[j][p][1]);              \
-            }                                                                           \
-        }                                                                               \
-        if (mn & (1u << j)) K[j] = __ldg(pn + j * 4 * SP);                              \
-    }
-            if (e & (1u << 24)) {
-                GW_SLOTS(-1.f)
-            } else {
-                GW_SLOTS(1.f)
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+            eB = lst[i + 1];
+            GW_LOAD(KB, eB);
+            GW_FMA(KA, eA);
+            if (i + 2 < n) {
+                eA = lst[i + 2];
+                GW_LOAD(KA, eA);
             }
-#undef GW_SLOTS
-            e = en;
+            GW_FMA(KB, eB);
         }
+        if (i < n) GW_FMA(KA, eA);
         if (last) {
             // commit the tile's accumulators of this work item
             const int u = (tile % side_u) * kTileU + bu + lu;
-            const int v0 = (tile / side_u) * kTileV + lv;
+            const int v0 = (tile / side_u) * kTileV + bv + lv;
 #pragma unroll
             for (int j = 0; j < kSlots; ++j) {
                 const int v = v0 + 4 * j;
 #pragma unroll
                 for (int p = 0; p < NPOL; ++p) {
-                    if (u < N && v < N && (acc[j][p][0] != 0.f || acc[j][p][1] != 0.f))
-                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u,
-                                  make_float2(acc[j][p][0], acc[j][p][1]));
-                    acc[j][p][0] = acc[j][p][1] = 0.f;
+                    const float re = P[j][p].x + P[j][p].y, im = Q[j][p].x + Q[j][p].y;
+                    if (u < N && v < N && (re != 0.f || im != 0.f))
+                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, make_float2(re, im));
+                    P[j][p] = Q[j][p] = make_float2(0.f, 0.f);
                 }
             }
         }
         bar_arrive(3 + buf, kSyncThreads);  // buffer free
         buf ^= 1;
     }
+#undef GW_LOAD
+#undef GW_FMA
 }
 
 template <int NPOL, int SP>
