@@ -11,7 +11,7 @@
 // * The tile is 64 (u) x 32 (v).  Sixteen compute warps each own an 8 (u) x
 //   16 (v) block; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..3
 //   ("slots" of 8 x 4 points), for every polarisation.
-// * A producer warp (in a fifth warpgroup that hands registers to the
+// * A fifth warpgroup of four producer warps (handing registers to the
 //   consumers with setmaxnreg) stages batches of records into shared memory
 //   (double-buffered, handed over with named barriers) and, for every record,
 //   appends it to the list of each compute warp whose block its footprint
@@ -42,7 +42,8 @@ constexpr int kComputeWarps = 16;
 // warpgroup gives back to 40, the consumers take 104:
 // 128 x 40 + 512 x 104 = 58368 <= 61440 = 640 x 96.
 constexpr int kThreads = (kComputeWarps + 4) * 32;
-constexpr int kSyncThreads = (kComputeWarps + 1) * 32;   // threads in the named barriers
+constexpr int kSyncThreads = kThreads;                   // threads in the batch barriers
+constexpr int kProducerThreads = 4 * 32;                 // producer-only barrier (id 5)
 constexpr int kProducerRegs = 40, kConsumerRegs = 104;
 constexpr int kBatch = 256;
 constexpr int kBufs = 2;
@@ -70,6 +71,7 @@ struct Smem {
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
+    uint32_t item;                         // work item fetched by the first producer warp
 };
 
 template <int NPOL, int SP>
@@ -82,24 +84,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
 
     if (warp >= kComputeWarps) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
-        if (warp > kComputeWarps) return;   // only one producer warp works
-        // ------------------------------------------------------------ producer
+        // ------------------------------------------------------------ producers
+        // The four warps of this warpgroup stage each batch together: warp pw
+        // takes records pw, pw + 4, ... of every 128-record group.
+        const int pw = warp - kComputeWarps;
         const uint32_t nitems = *a.item_count;
         int buf = 0, uses = 0;
         for (;;) {
-            uint32_t it = 0;
-            if (lane == 0) it = atomicAdd(a.queue, 1u);
-            it = __shfl_sync(0xffffffffu, it, 0);
+            if (warp == kComputeWarps && lane == 0) sm.item = atomicAdd(a.queue, 1u);
+            bar_sync(5, kProducerThreads);
+            const uint32_t it = sm.item;
+            bar_sync(5, kProducerThreads);   // everyone has read sm.item
             const bool done = it >= nitems;
             Item item{};
             if (!done) item = a.items[it];
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
                 if (uses >= kBufs) bar_sync(3 + buf, kSyncThreads);  // wait until consumed
-                if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
-                __syncwarp();
+                if (pw == 0 && lane < kComputeWarps) sm.cnt[buf][lane] = 0;
+                bar_sync(5, kProducerThreads);   // counters cleared before any append
                 if (done) {
-                    if (lane == 0) {
+                    if (pw == 0 && lane == 0) {
                         sm.tile[buf] = -1;
                         sm.last[buf] = 1;
                     }
@@ -108,51 +113,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                     const int tv0 = (item.tile / side_u) * kTileV;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
-                    for (int r = lane; r < nb; r += 32) {
-                        const uint32_t id = __ldg(a.entries + item.start + b0 + r);
-                        const gw_index_rec rc = load_rec(a.rec, id);
-                        const int S = __ldg(a.support + rc.plane), h = S >> 1;
-                        const int64_t slice = __ldg(a.pplane_off + rc.plane) +
-                                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
-                                                  (int64_t)(S + 6) * SP;
-                        // padded index of the tile origin relative to this record
-                        sm.rec[buf][r] = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                        const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
+                    for (int g = 0; g < nb; g += 128) {
+                        const int r = g + lane * 4 + pw;
+                        const bool act = r < nb;
+                        uint32_t e = 0;
+                        int cu0 = 1, cu1 = 0, cv0 = 1, cv1 = 0, vlo = 0, vhi = -1;
+                        if (act) {
+                            const uint32_t id = __ldg(a.entries + item.start + b0 + r);
+                            const gw_index_rec rc = load_rec(a.rec, id);
+                            const int S = __ldg(a.support + rc.plane), h = S >> 1;
+                            const int64_t slice = __ldg(a.pplane_off + rc.plane) +
+                                                  ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
+                                                      (int64_t)(S + 6) * SP;
+                            // padded index of the tile origin relative to this record
+                            sm.rec[buf][r] = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
+                            const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
+                            float2 v[NPOL];
 #pragma unroll
-                        for (int p = 0; p < NPOL; ++p) {
-                            float2 v = __ldg(a.vis + (int64_t)id * NPOL + p);
+                            for (int p = 0; p < NPOL; ++p) v[p] = __ldg(a.vis + (int64_t)id * NPOL + p);
                             if (a.weight) {
-                                const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
-                                v.x *= w;
-                                v.y *= w;
+#pragma unroll
+                                for (int p = 0; p < NPOL; ++p) {
+                                    const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
+                                    v[p].x *= w;
+                                    v[p].y *= w;
+                                }
                             }
-                            sm.v[buf][r][p] = make_float4(v.x, -sg * v.y, v.y, sg * v.x);
+#pragma unroll
+                            for (int p = 0; p < NPOL; ++p)
+                                sm.v[buf][r][p] = make_float4(v[p].x, -sg * v[p].y, v[p].y, sg * v[p].x);
+                            // footprint relative to the tile
+                            const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
+                            vlo = rc.kv - h - tv0;
+                            vhi = rc.kv + h - tv0;
+                            cu0 = max(0, ulo) >> 3;
+                            cu1 = min(kTileU - 1, uhi) >> 3;
+                            cv0 = max(0, vlo) >> 4;
+                            cv1 = min(kTileV - 1, vhi) >> 4;
+                            e = (uint32_t)r;
                         }
-                        // footprint relative to the tile; slots are 4-row bands
-                        const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
-                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
-                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTileU - 1, uhi) >> 3;
-                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTileV - 1, vhi) >> 4;
-                        for (int cv = cv0; cv <= cv1; ++cv) {
+                        // warp-aggregated appends: one shared atomic per target warp
+                        for (int cv = 0; cv < kTileV / 16; ++cv) {
+                            const bool in_v = act && cv >= cv0 && cv <= cv1;
                             const int j0 = max(0, vlo - 16 * cv) >> 2;
                             const int j1 = min(15, vhi - 16 * cv) >> 2;
-                            const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
-                            const uint32_t e = (uint32_t)r | (mask << 8);
-                            for (int cu = cu0; cu <= cu1; ++cu) {
+                            const uint32_t mask = in_v ? (((2u << j1) - 1u) & ~((1u << j0) - 1u)) : 0u;
+                            for (int cu = 0; cu < kTileU / 8; ++cu) {
+                                const bool want = in_v && cu >= cu0 && cu <= cu1;
+                                const uint32_t bal = __ballot_sync(0xffffffffu, want);
+                                if (!bal) continue;
                                 const int w = cv * 8 + cu;
-                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
-                                sm.list[buf][w][pos] = e;
+                                int base = 0;
+                                const int leader = __ffs(bal) - 1;
+                                if (lane == leader) base = atomicAdd(&sm.cnt[buf][w], __popc(bal));
+                                base = __shfl_sync(0xffffffffu, base, leader);
+                                if (want)
+                                    sm.list[buf][w][base + __popc(bal & ((1u << lane) - 1u))] = e | (mask << 8);
                             }
                         }
                     }
-                    if (lane == 0) {
+                    if (pw == 0 && lane == 0) {
                         sm.tile[buf] = item.tile;
                         sm.last[buf] = (b == nb_total - 1);
                     }
                 }
                 __syncwarp();
                 __threadfence_block();
-                bar_arrive(1 + buf, kSyncThreads);  // batch ready
+                bar_arrive(1 + buf, kSyncThreads);  // this warp's part of the batch is ready
                 buf ^= 1;
                 ++uses;
             }
