@@ -8,12 +8,12 @@
 // * A CTA owns one kTile x kTile tile of the grid for a work item (a run of
 //   that tile's bin) and keeps the tile's accumulators in registers, so each
 //   grid point is committed once per work item (vector atomics, red.global).
-// * The tile is 64 (u) x 32 (v).  Sixteen compute warps each own an 8 (u) x
-//   16 (v) block; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..3
+// * The tile is 64 (u) x 32 (v).  Eight compute warps each own an 8 (u) x
+//   32 (v) column; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..7
 //   ("slots" of 8 x 4 points), for every polarisation.
 // * A fifth warpgroup of four producer warps (handing registers to the
 //   consumers with setmaxnreg) stages batches of records into shared memory
-//   (double-buffered, handed over with named barriers) and, for every record,
+//   (four batches in flight, handed over with named barriers) and, for every record,
 //   appends it to the list of each compute warp whose block its footprint
 //   meets, together with the range of slots its rows meet.  Compute warps
 //   therefore only see records that touch them, and skip untouched slots with
@@ -36,18 +36,18 @@ namespace gw {
 
 namespace {
 
-constexpr int kComputeWarps = 16;
-// Four consumer warpgroups plus one producer warpgroup (one working warp).
-// Register split (setmaxnreg): launched at 96 per thread; the producer
-// warpgroup gives back to 40, the consumers take 104:
-// 128 x 40 + 512 x 104 = 58368 <= 61440 = 640 x 96.
+constexpr int kComputeWarps = 8;
+// Two consumer warpgroups plus one producer warpgroup of four warps.
+// Register split (setmaxnreg): launched at 168 per thread; the producers give
+// back to 40, the consumers take 232:
+// 128 x 40 + 256 x 232 = 64512 = 384 x 168.
 constexpr int kThreads = (kComputeWarps + 4) * 32;
 constexpr int kSyncThreads = kThreads;                   // threads in the batch barriers
-constexpr int kProducerThreads = 4 * 32;                 // producer-only barrier (id 5)
-constexpr int kProducerRegs = 40, kConsumerRegs = 104;
+constexpr int kProducerThreads = 4 * 32;                 // producer-only barrier (id 9)
+constexpr int kProducerRegs = 40, kConsumerRegs = 232;
 constexpr int kBatch = 256;
-constexpr int kBufs = 2;
-constexpr int kSlots = 4;            // 4 x 4-row slots: a warp block is 8 (u) x 16 (v)
+constexpr int kBufs = 4;             // batches in flight (barriers 1..4 full, 5..8 empty)
+constexpr int kSlots = 8;            // 8 x 4-row slots: a warp block is 8 (u) x 32 (v)
 constexpr int kTileU = 64, kTileV = 32;
 static_assert(kTileU == kGridTileU && kTileV == kGridTileV, "tile shape");
 
@@ -92,17 +92,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
         int buf = 0, uses = 0;
         for (;;) {
             if (warp == kComputeWarps && lane == 0) sm.item = atomicAdd(a.queue, 1u);
-            bar_sync(5, kProducerThreads);
+            bar_sync(9, kProducerThreads);
             const uint32_t it = sm.item;
-            bar_sync(5, kProducerThreads);   // everyone has read sm.item
+            bar_sync(9, kProducerThreads);   // everyone has read sm.item
             const bool done = it >= nitems;
             Item item{};
             if (!done) item = a.items[it];
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
-                if (uses >= kBufs) bar_sync(3 + buf, kSyncThreads);  // wait until consumed
+                if (uses >= kBufs) bar_sync(1 + kBufs + buf, kSyncThreads);  // wait until consumed
                 if (pw == 0 && lane < kComputeWarps) sm.cnt[buf][lane] = 0;
-                bar_sync(5, kProducerThreads);   // counters cleared before any append
+                bar_sync(9, kProducerThreads);   // counters cleared before any append
                 if (done) {
                     if (pw == 0 && lane == 0) {
                         sm.tile[buf] = -1;
@@ -148,21 +148,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                             vhi = rc.kv + h - tv0;
                             cu0 = max(0, ulo) >> 3;
                             cu1 = min(kTileU - 1, uhi) >> 3;
-                            cv0 = max(0, vlo) >> 4;
-                            cv1 = min(kTileV - 1, vhi) >> 4;
+                            cv0 = 0;
+                            cv1 = (vhi >= 0 && vlo <= kTileV - 1) ? 0 : -1;
                             e = (uint32_t)r;
                         }
                         // warp-aggregated appends: one shared atomic per target warp
-                        for (int cv = 0; cv < kTileV / 16; ++cv) {
-                            const bool in_v = act && cv >= cv0 && cv <= cv1;
-                            const int j0 = max(0, vlo - 16 * cv) >> 2;
-                            const int j1 = min(15, vhi - 16 * cv) >> 2;
+                        {
+                            const bool in_v = act && cv0 <= cv1;
+                            const int j0 = max(0, vlo) >> 2;
+                            const int j1 = min(kTileV - 1, vhi) >> 2;
                             const uint32_t mask = in_v ? (((2u << j1) - 1u) & ~((1u << j0) - 1u)) : 0u;
                             for (int cu = 0; cu < kTileU / 8; ++cu) {
                                 const bool want = in_v && cu >= cu0 && cu <= cu1;
                                 const uint32_t bal = __ballot_sync(0xffffffffu, want);
                                 if (!bal) continue;
-                                const int w = cv * 8 + cu;
+                                const int w = cu;
                                 int base = 0;
                                 const int leader = __ffs(bal) - 1;
                                 if (lane == leader) base = atomicAdd(&sm.cnt[buf][w], __popc(bal));
@@ -180,13 +180,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                 __syncwarp();
                 __threadfence_block();
                 bar_arrive(1 + buf, kSyncThreads);  // this warp's part of the batch is ready
-                buf ^= 1;
+                buf = (buf + 1) % kBufs;
                 ++uses;
             }
             if (done) {
-                // complete the consumers' last release of the other buffer so
+                // complete the consumers' last releases of the other buffers so
                 // that every barrier generation is balanced before exit
-                if (uses >= 2) bar_sync(3 + buf, kSyncThreads);
+                // (batch k was released by the consumers for k < E = uses - 1;
+                // the producer already waited on releases of k <= E - kBufs)
+                for (int k = max(0, uses - kBufs); k <= uses - 2; ++k)
+                    bar_sync(1 + kBufs + (k % kBufs), kSyncThreads);
                 break;
             }
         }
@@ -195,9 +198,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
 
     // ---------------------------------------------------------------- consumers
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
-    const int bu = (warp & 7) * 8, bv = (warp >> 3) * 16;
+    const int bu = warp * 8;
     const int lu = lane & 7, lv = lane >> 3;
-    const float2* __restrict__ tab = a.ptable + (bv + lv) * SP + bu + lu;
+    const float2* __restrict__ tab = a.ptable + lv * SP + bu + lu;
     const int N = a.N;
     // P = sum K (.) (V.x, -s V.y), Q = sum K (.) (V.y, s V.x):
     // re = P.x + P.y, im = Q.x + Q.y  (s = -1 for the conjugate kernel)
@@ -238,30 +241,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
         const int last = sm.last[buf];
         const int n = sm.cnt[buf][warp];
         const uint32_t* lst = sm.list[buf][warp];
-        // two-stage pipeline: kernel values of the next entry load while the
-        // current entry's multiply-adds issue (ping-pong registers)
-        float2 KA[kSlots], KB[kSlots];
-        uint32_t eA = 0, eB = 0;
-        if (n > 0) {
-            eA = lst[0];
-            GW_LOAD(KA, eA);
-        }
+        // three-stage pipeline over the warp's entries: kernel values of the
+        // next two entries are in flight while one entry's multiply-adds issue
+        float2 KA[kSlots], KB[kSlots], KC[kSlots];
+        uint32_t eA = 0, eB = 0, eC = 0;
+        if (n > 0) { eA = lst[0]; GW_LOAD(KA, eA); }
+        if (n > 1) { eB = lst[1]; GW_LOAD(KB, eB); }
         int i = 0;
-        for (; i + 1 < n; i += 2) {
-            eB = lst[i + 1];
-            GW_LOAD(KB, eB);
+        for (; i + 2 < n; i += 3) {
+            eC = lst[i + 2];
+            GW_LOAD(KC, eC);
             GW_FMA(KA, eA);
-            if (i + 2 < n) {
-                eA = lst[i + 2];
-                GW_LOAD(KA, eA);
-            }
+            if (i + 3 < n) { eA = lst[i + 3]; GW_LOAD(KA, eA); }
             GW_FMA(KB, eB);
+            if (i + 4 < n) { eB = lst[i + 4]; GW_LOAD(KB, eB); }
+            GW_FMA(KC, eC);
         }
         if (i < n) GW_FMA(KA, eA);
+        if (i + 1 < n) GW_FMA(KB, eB);
         if (last) {
             // commit the tile's accumulators of this work item
             const int u = (tile % side_u) * kTileU + bu + lu;
-            const int v0 = (tile / side_u) * kTileV + bv + lv;
+            const int v0 = (tile / side_u) * kTileV + lv;
 #pragma unroll
             for (int j = 0; j < kSlots; ++j) {
                 const int v = v0 + 4 * j;
@@ -274,8 +275,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                 }
             }
         }
-        bar_arrive(3 + buf, kSyncThreads);  // buffer free
-        buf ^= 1;
+        bar_arrive(1 + kBufs + buf, kSyncThreads);  // buffer free
+        buf = (buf + 1) % kBufs;
     }
 #undef GW_LOAD
 #undef GW_FMA
