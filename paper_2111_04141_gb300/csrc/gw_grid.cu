@@ -5,26 +5,27 @@
 //     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
 //
 // Design (GB300):
-// * A CTA owns one 32 (u) x 16 (v) tile of the grid for a work item (a run of
-//   that tile's bin).  Sixteen consumer warps each own one 8 x 4 block of the
-//   tile (lane (lu, lv) holds point (lu, lv) for every polarisation) and keep
-//   its accumulators in registers for the whole work item, so each grid point
-//   is committed once per work item (vector atomics, red.global).
-// * A warpgroup of four producer warps stages batches of records into shared
-//   memory (four batches in flight, handed over with named barriers) and
-//   appends each record to the list of every consumer warp whose block its
-//   footprint meets (warp-aggregated shared atomics).  A consumer therefore
-//   only sees records that touch its block and runs no per-record control
-//   beyond a list read: wasted multiply-adds are limited to the parts of an
-//   8 x 4 block outside a footprint.
+// * A CTA owns one kTile x kTile tile of the grid for a work item (a run of
+//   that tile's bin) and keeps the tile's accumulators in registers, so each
+//   grid point is committed once per work item (vector atomics, red.global).
+// * The tile is 64 (u) x 32 (v).  Eight compute warps each own an 8 (u) x
+//   32 (v) column; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..7
+//   ("slots" of 8 x 4 points), for every polarisation.
+// * A fifth warpgroup of four producer warps (handing registers to the
+//   consumers with setmaxnreg) stages batches of records into shared memory
+//   (four batches in flight, handed over with named barriers) and, for every record,
+//   appends it to the list of each compute warp whose block its footprint
+//   meets, together with the range of slots its rows meet.  Compute warps
+//   therefore only see records that touch them, and skip untouched slots with
+//   one uniform test.
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
 //   rows around each S x S slice, one compile-time row stride per plan), so
-//   lanes outside the footprint read zeros without predication; kernel values
-//   of the next two entries are in flight while one entry's multiply-adds
-//   issue (three register sets).
+//   lanes outside the footprint read zeros without predication and slot
+//   addresses are immediate offsets; loads for the next record are issued
+//   before the multiply-adds of the current one (ping-pong registers).
 // * Per tap and polarisation the complex update costs two packed FP32x2 FMAs
-//   (Blackwell FFMA2: two multiply-adds per issued instruction).  Without
-//   broadcasting K:
+//   (Blackwell FFMA2: two multiply-adds per issued instruction, so control
+//   instructions issue in the FMA pipe's spare slots).  Without broadcasting K:
 //     P += K (.) (V.x, -s V.y),  Q += K (.) (V.y, s V.x),
 //     re = P.x + P.y,  im = Q.x + Q.y   at commit,
 //   s = +1, or -1 for records with w < 0 (conj(K) V), folded into the staged
@@ -35,14 +36,19 @@ namespace gw {
 
 namespace {
 
-constexpr int kColBlocks = 4, kRowBlocks = 4;            // 8 x 4 blocks per tile
-constexpr int kComputeWarps = kColBlocks * kRowBlocks;   // one 8 x 4 block per warp
-constexpr int kThreads = (kComputeWarps + 4) * 32;       // + one producer warpgroup
+constexpr int kComputeWarps = 8;
+// Two consumer warpgroups plus one producer warpgroup of four warps.
+// Register split (setmaxnreg): launched at 168 per thread; the producers give
+// back to 40, the consumers take 232:
+// 128 x 40 + 256 x 232 = 64512 = 384 x 168.
+constexpr int kThreads = (kComputeWarps + 4) * 32;
 constexpr int kSyncThreads = kThreads;                   // threads in the batch barriers
 constexpr int kProducerThreads = 4 * 32;                 // producer-only barrier (id 9)
+constexpr int kProducerRegs = 40, kConsumerRegs = 232;
 constexpr int kBatch = 256;
 constexpr int kBufs = 4;             // batches in flight (barriers 1..4 full, 5..8 empty)
-constexpr int kTileU = 8 * kColBlocks, kTileV = 4 * kRowBlocks;
+constexpr int kSlots = 8;            // 8 x 4-row slots: a warp block is 8 (u) x 32 (v)
+constexpr int kTileU = 64, kTileV = 32;
 static_assert(kTileU == kGridTileU && kTileV == kGridTileV, "tile shape");
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
@@ -61,7 +67,7 @@ template <int NPOL>
 struct Smem {
     int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
     float4 v[kBufs][kBatch][NPOL];         // (V.x, -s V.y, V.y, s V.x), s = -1 for w < 0
-    uint8_t list[kBufs][kComputeWarps][kBatch];   // records meeting the warp's block
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | first slot << 8 | last slot << 11
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
@@ -77,6 +83,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     const int hb = a.beta / 2;
 
     if (warp >= kComputeWarps) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
         // ------------------------------------------------------------ producers
         // The four warps of this warpgroup stage each batch together: warp pw
         // takes records pw, pw + 4, ... of every 128-record group.
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                     for (int g = 0; g < nb; g += 128) {
                         const int r = g + lane * 4 + pw;
                         const bool act = r < nb;
-                        uint32_t e = 0;   // record index within the batch
+                        uint32_t e = 0;
                         int cu0 = 1, cu1 = 0, cv0 = 1, cv1 = 0, vlo = 0, vhi = -1;
                         if (act) {
                             const uint32_t id = __ldg(a.entries + item.start + b0 + r);
@@ -146,18 +153,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                             e = (uint32_t)r;
                         }
                         // warp-aggregated appends: one shared atomic per target warp
-                        const int j0 = max(0, vlo) >> 2, j1 = min(kTileV - 1, vhi) >> 2;
-                        for (int w = 0; w < kComputeWarps; ++w) {
-                            const int cu = w % kColBlocks, j = w / kColBlocks;
-                            const bool want = act && cv0 <= cv1 && cu >= cu0 && cu <= cu1 &&
-                                              j >= j0 && j <= j1;
-                            const uint32_t bal = __ballot_sync(0xffffffffu, want);
-                            if (!bal) continue;
-                            int base = 0;
-                            const int leader = __ffs(bal) - 1;
-                            if (lane == leader) base = atomicAdd(&sm.cnt[buf][w], __popc(bal));
-                            base = __shfl_sync(0xffffffffu, base, leader);
-                            if (want) sm.list[buf][w][base + __popc(bal & ((1u << lane) - 1u))] = e;
+                        {
+                            const bool in_v = act && cv0 <= cv1;
+                            const int j0 = max(0, vlo) >> 2;
+                            const int j1 = min(kTileV - 1, vhi) >> 2;
+                            const uint32_t jr = in_v ? ((uint32_t)j0 | ((uint32_t)j1 << 3)) : 0u;
+                            for (int cu = 0; cu < kTileU / 8; ++cu) {
+                                const bool want = in_v && cu >= cu0 && cu <= cu1;
+                                const uint32_t bal = __ballot_sync(0xffffffffu, want);
+                                if (!bal) continue;
+                                const int w = cu;
+                                int base = 0;
+                                const int leader = __ffs(bal) - 1;
+                                if (lane == leader) base = atomicAdd(&sm.cnt[buf][w], __popc(bal));
+                                base = __shfl_sync(0xffffffffu, base, leader);
+                                if (want)
+                                    sm.list[buf][w][base + __popc(bal & ((1u << lane) - 1u))] = e | (jr << 8);
+                            }
                         }
                     }
                     if (pw == 0 && lane == 0) {
@@ -185,23 +197,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     }
 
     // ---------------------------------------------------------------- consumers
-    const int bu = (warp % kColBlocks) * 8, bv = (warp / kColBlocks) * 4;
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
+    const int bu = warp * 8;
     const int lu = lane & 7, lv = lane >> 3;
-    const float2* __restrict__ tab = a.ptable + (bv + lv) * SP + bu + lu;
+    const float2* __restrict__ tab = a.ptable + lv * SP + bu + lu;
     const int N = a.N;
     // P = sum K (.) (V.x, -s V.y), Q = sum K (.) (V.y, s V.x):
     // re = P.x + P.y, im = Q.x + Q.y  (s = -1 for the conjugate kernel)
-    float2 P[NPOL], Q[NPOL];
+    float2 P[kSlots][NPOL], Q[kSlots][NPOL];
 #pragma unroll
-    for (int p = 0; p < NPOL; ++p) P[p] = Q[p] = make_float2(0.f, 0.f);
+    for (int j = 0; j < kSlots; ++j)
+#pragma unroll
+        for (int p = 0; p < NPOL; ++p) P[j][p] = Q[j][p] = make_float2(0.f, 0.f);
 
-#define GW_FMA(K, r)                                                           \
+    // Active slots of an entry are the contiguous range [j0, j1]: a switch on
+    // j0 falls through the slots and breaks after j1, so inactive slots issue
+    // nothing (no predicated-off work).
+#define GW_LOAD_SLOT(K, p_, j) K[j] = __ldg((p_) + (j) * 4 * SP)
+#define GW_LOAD(K, e)                                                          \
     do {                                                                       \
-        const float4* v_ = sm.v[buf][r];                                       \
-        _Pragma("unroll") for (int p = 0; p < NPOL; ++p) {                     \
-            const float4 V = v_[p];                                            \
-            P[p] = __ffma2_rn(K, make_float2(V.x, V.y), P[p]);                 \
-            Q[p] = __ffma2_rn(K, make_float2(V.z, V.w), Q[p]);                 \
+        const float2* p_ = tab + sm.rec[buf][(e) & 0xff];                      \
+        const int j0_ = ((e) >> 8) & 7, j1_ = ((e) >> 11) & 7;                 \
+        switch (j0_) {                                                         \
+            case 0: GW_LOAD_SLOT(K, p_, 0); if (j1_ == 0) break;               \
+            case 1: GW_LOAD_SLOT(K, p_, 1); if (j1_ == 1) break;               \
+            case 2: GW_LOAD_SLOT(K, p_, 2); if (j1_ == 2) break;               \
+            case 3: GW_LOAD_SLOT(K, p_, 3); if (j1_ == 3) break;               \
+            case 4: GW_LOAD_SLOT(K, p_, 4); if (j1_ == 4) break;               \
+            case 5: GW_LOAD_SLOT(K, p_, 5); if (j1_ == 5) break;               \
+            case 6: GW_LOAD_SLOT(K, p_, 6); if (j1_ == 6) break;               \
+            default: GW_LOAD_SLOT(K, p_, 7);                                    \
+        }                                                                      \
+    } while (0)
+#define GW_FMA_SLOT(K, j)                                                      \
+    _Pragma("unroll") for (int p = 0; p < NPOL; ++p) {                         \
+        P[j][p] = __ffma2_rn(K[j], make_float2(V[p].x, V[p].y), P[j][p]);      \
+        Q[j][p] = __ffma2_rn(K[j], make_float2(V[p].z, V[p].w), Q[j][p]);      \
+    }
+#define GW_FMA(K, e)                                                           \
+    do {                                                                       \
+        const float4* v_ = sm.v[buf][(e) & 0xff];                              \
+        float4 V[NPOL];                                                        \
+        _Pragma("unroll") for (int p = 0; p < NPOL; ++p) V[p] = v_[p];         \
+        const int j0_ = ((e) >> 8) & 7, j1_ = ((e) >> 11) & 7;                 \
+        switch (j0_) {                                                         \
+            case 0: GW_FMA_SLOT(K, 0) if (j1_ == 0) break;                     \
+            case 1: GW_FMA_SLOT(K, 1) if (j1_ == 1) break;                     \
+            case 2: GW_FMA_SLOT(K, 2) if (j1_ == 2) break;                     \
+            case 3: GW_FMA_SLOT(K, 3) if (j1_ == 3) break;                     \
+            case 4: GW_FMA_SLOT(K, 4) if (j1_ == 4) break;                     \
+            case 5: GW_FMA_SLOT(K, 5) if (j1_ == 5) break;                     \
+            case 6: GW_FMA_SLOT(K, 6) if (j1_ == 6) break;                     \
+            default: GW_FMA_SLOT(K, 7)                                          \
         }                                                                      \
     } while (0)
 
@@ -212,42 +259,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
         if (tile < 0) break;
         const int last = sm.last[buf];
         const int n = sm.cnt[buf][warp];
-        const uint8_t* lst = sm.list[buf][warp];
-        const int* rec = sm.rec[buf];
-        // three-stage pipeline: kernel values of the next two entries are in
-        // flight while one entry's multiply-adds issue
-        float2 KA = make_float2(0.f, 0.f), KB = KA, KC = KA;
-        int rA = 0, rB = 0, rC = 0;
-        if (n > 0) { rA = lst[0]; KA = __ldg(tab + rec[rA]); }
-        if (n > 1) { rB = lst[1]; KB = __ldg(tab + rec[rB]); }
+        const uint32_t* lst = sm.list[buf][warp];
+        // three-stage pipeline over the warp's entries: kernel values of the
+        // next two entries are in flight while one entry's multiply-adds issue
+        float2 KA[kSlots], KB[kSlots], KC[kSlots];
+        uint32_t eA = 0, eB = 0, eC = 0;
+        if (n > 0) { eA = lst[0]; GW_LOAD(KA, eA); }
+        if (n > 1) { eB = lst[1]; GW_LOAD(KB, eB); }
         int i = 0;
         for (; i + 2 < n; i += 3) {
-            rC = lst[i + 2];
-            KC = __ldg(tab + rec[rC]);
-            GW_FMA(KA, rA);
-            if (i + 3 < n) { rA = lst[i + 3]; KA = __ldg(tab + rec[rA]); }
-            GW_FMA(KB, rB);
-            if (i + 4 < n) { rB = lst[i + 4]; KB = __ldg(tab + rec[rB]); }
-            GW_FMA(KC, rC);
+            eC = lst[i + 2];
+            GW_LOAD(KC, eC);
+            GW_FMA(KA, eA);
+            if (i + 3 < n) { eA = lst[i + 3]; GW_LOAD(KA, eA); }
+            GW_FMA(KB, eB);
+            if (i + 4 < n) { eB = lst[i + 4]; GW_LOAD(KB, eB); }
+            GW_FMA(KC, eC);
         }
-        if (i < n) GW_FMA(KA, rA);
-        if (i + 1 < n) GW_FMA(KB, rB);
+        if (i < n) GW_FMA(KA, eA);
+        if (i + 1 < n) GW_FMA(KB, eB);
         if (last) {
-            // commit the block's accumulators of this work item
+            // commit the tile's accumulators of this work item
             const int u = (tile % side_u) * kTileU + bu + lu;
-            const int v = (tile / side_u) * kTileV + bv + lv;
+            const int v0 = (tile / side_u) * kTileV + lv;
 #pragma unroll
-            for (int p = 0; p < NPOL; ++p) {
-                const float re = P[p].x + P[p].y, im = Q[p].x + Q[p].y;
-                if (u < N && v < N && (re != 0.f || im != 0.f))
-                    atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, make_float2(re, im));
-                P[p] = Q[p] = make_float2(0.f, 0.f);
+            for (int j = 0; j < kSlots; ++j) {
+                const int v = v0 + 4 * j;
+#pragma unroll
+                for (int p = 0; p < NPOL; ++p) {
+                    const float re = P[j][p].x + P[j][p].y, im = Q[j][p].x + Q[j][p].y;
+                    if (u < N && v < N && (re != 0.f || im != 0.f))
+                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, make_float2(re, im));
+                    P[j][p] = Q[j][p] = make_float2(0.f, 0.f);
+                }
             }
         }
         bar_arrive(1 + kBufs + buf, kSyncThreads);  // buffer free
         buf = (buf + 1) % kBufs;
     }
+#undef GW_LOAD
+#undef GW_LOAD_SLOT
 #undef GW_FMA
+#undef GW_FMA_SLOT
 }
 
 template <int NPOL, int SP>
