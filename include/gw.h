@@ -143,7 +143,8 @@ gw_status gw_plan_info_get(gw_plan plan, gw_plan_info* out);
  * and chunked inputs add linearly; zero it first for a fresh image.
  *   uvw_m    device, [nrow][3] float64, metres
  *   freq_hz  device, [nchan] float64, Hz
- *   vis      device, [nrow][nchan][npol] complex of the plan's vis_dtype
+ *   vis      device, [nrow][nchan][npol] complex of the plan's vis_dtype,
+ *            16-byte aligned when npol is even (8-byte aligned otherwise)
  *   weight   device, [nrow][nchan][npol] float32, or NULL for unit weights
  *   grid     device, [npol][N][N] c64, accumulated
  *   n_dropped host, optional: receives the number of visibilities dropped by

@@ -74,6 +74,7 @@ void plan_free(gw_plan p) {
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
     cudaFree(p->sc.work);
+    cudaFree(p->sc.wvis);
     cudaFree(p->table);
     cudaFree(p->ptable);
     cudaFree(p->d_pplane_off);
@@ -245,7 +246,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 
     const int N = desc->grid_n, P = desc->n_wplanes, beta = desc->oversample;
     p->field = (double)N * desc->cell_rad;
-    p->geom_grid = BinGeom{0, 6, 5, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
+    p->geom_grid = BinGeom{0, 5, 4, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
     p->geom_degrid = BinGeom{1, 5, 5, (N + kTile - 1) / kTile, (N + kTile - 1) / kTile};
     p->ntiles = std::max(p->geom_grid.ntu * p->geom_grid.ntv, p->geom_degrid.ntu * p->geom_degrid.ntv);
     p->support.resize(P);
@@ -376,6 +377,10 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
     if (st != GW_OK) return st;
     if (!grid) return fail(GW_EINVAL, "null grid");
     if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
+    if ((p->desc.npol % 2 == 0) && (reinterpret_cast<uintptr_t>(vis) % 16 != 0))
+        return fail(GW_EINVAL, "vis must be 16-byte aligned when npol is even");
+    if ((reinterpret_cast<uintptr_t>(grid) % 8 != 0) || (reinterpret_cast<uintptr_t>(vis) % 8 != 0))
+        return fail(GW_EINVAL, "vis and grid must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -391,7 +396,18 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
         a.ptable = p->ptable;
         a.pplane_off = p->d_pplane_off;
         a.vis = reinterpret_cast<const float2*>(vis) + v0 * npol;
-        a.weight = weight ? weight + v0 * npol : nullptr;
+        a.weight = nullptr;
+        if (weight) {
+            if (!p->sc.wvis) {
+                e = cudaMalloc(&p->sc.wvis, sizeof(float2) * (size_t)p->chunk * npol);
+                if (e != cudaSuccess) {
+                    p->sc.wvis = nullptr;
+                    return fail(GW_ENOMEM, "allocating weighted-visibility scratch");
+                }
+            }
+            launch_weight_vis(a.vis, weight + v0 * npol, nr * nchan * npol, p->sc.wvis, s);
+            a.vis = p->sc.wvis;
+        }
         a.table = p->table;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;

@@ -5,50 +5,44 @@
 //     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
 //
 // Design (GB300):
-// * A CTA owns one kTile x kTile tile of the grid for a work item (a run of
-//   that tile's bin) and keeps the tile's accumulators in registers, so each
-//   grid point is committed once per work item (vector atomics, red.global).
-// * The tile is 64 (u) x 32 (v).  Eight compute warps each own an 8 (u) x
-//   32 (v) column; lane (lu, lv) holds the points (lu, lv + 4 j), j = 0..7
-//   ("slots" of 8 x 4 points), for every polarisation.
-// * A fifth warpgroup of four producer warps (handing registers to the
-//   consumers with setmaxnreg) stages batches of records into shared memory
-//   (four batches in flight, handed over with named barriers) and, for every record,
-//   appends it to the list of each compute warp whose block its footprint
-//   meets, together with the range of slots its rows meet.  Compute warps
-//   therefore only see records that touch them, and skip untouched slots with
-//   one uniform test.
+// * A CTA owns one 32 (u) x 16 (v) tile of the grid for a work item (a run of
+//   that tile's bin).  Sixteen consumer warps each own one 8 x 4 block of the
+//   tile (lane (lu, lv) holds point (lu, lv) for every polarisation) and keep
+//   its accumulators in registers for the whole work item, so each grid point
+//   is committed once per work item (vector atomics, red.global).
+// * A warpgroup of four producer warps walks the work item in batches and
+//   appends, for every record, one 8-byte entry (table index of the tile
+//   origin relative to the record, visibility id, conjugation bit) to the
+//   list of every consumer warp whose block the record's footprint meets
+//   (warp-aggregated shared atomics; four batches in flight, handed over with
+//   named barriers).  A consumer reads one entry per record that touches its
+//   block and runs no other per-record control: wasted multiply-adds are
+//   limited to the parts of an 8 x 4 block outside a footprint.
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
 //   rows around each S x S slice, one compile-time row stride per plan), so
-//   lanes outside the footprint read zeros without predication and slot
-//   addresses are immediate offsets; loads for the next record are issued
-//   before the multiply-adds of the current one (ping-pong registers).
+//   lanes outside the footprint read zeros without predication.  Visibilities
+//   are read straight from the visibility array with broadcast loads (the
+//   shared-memory path is the scarce one).  Kernel values and visibilities of
+//   the next two entries are in flight while one entry's multiply-adds issue.
 // * Per tap and polarisation the complex update costs two packed FP32x2 FMAs
-//   (Blackwell FFMA2: two multiply-adds per issued instruction, so control
-//   instructions issue in the FMA pipe's spare slots).  Without broadcasting K:
-//     P += K (.) (V.x, -s V.y),  Q += K (.) (V.y, s V.x),
-//     re = P.x + P.y,  im = Q.x + Q.y   at commit,
-//   s = +1, or -1 for records with w < 0 (conj(K) V), folded into the staged
-//   visibility so mixed records share accumulators.
+//   (Blackwell FFMA2: two multiply-adds per issued instruction), accumulated
+//   as P = sum K (.) V and Q = sum (K.y, K.x) (.) V, separately for records
+//   that use the kernel and for those that use its conjugate (w < 0); the
+//   real and imaginary parts are formed at commit.
 #include "gw_internal.cuh"
 
 namespace gw {
 
 namespace {
 
-constexpr int kComputeWarps = 8;
-// Two consumer warpgroups plus one producer warpgroup of four warps.
-// Register split (setmaxnreg): launched at 168 per thread; the producers give
-// back to 40, the consumers take 232:
-// 128 x 40 + 256 x 232 = 64512 = 384 x 168.
-constexpr int kThreads = (kComputeWarps + 4) * 32;
+constexpr int kColBlocks = 4, kRowBlocks = 4;            // 8 x 4 blocks per tile
+constexpr int kComputeWarps = kColBlocks * kRowBlocks;   // one 8 x 4 block per warp
+constexpr int kThreads = (kComputeWarps + 4) * 32;       // + one producer warpgroup
 constexpr int kSyncThreads = kThreads;                   // threads in the batch barriers
 constexpr int kProducerThreads = 4 * 32;                 // producer-only barrier (id 9)
-constexpr int kProducerRegs = 40, kConsumerRegs = 232;
 constexpr int kBatch = 256;
 constexpr int kBufs = 4;             // batches in flight (barriers 1..4 full, 5..8 empty)
-constexpr int kSlots = 8;            // 8 x 4-row slots: a warp block is 8 (u) x 32 (v)
-constexpr int kTileU = 64, kTileV = 32;
+constexpr int kTileU = 8 * kColBlocks, kTileV = 4 * kRowBlocks;
 static_assert(kTileU == kGridTileU && kTileV == kGridTileV, "tile shape");
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
@@ -65,9 +59,9 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 
 template <int NPOL>
 struct Smem {
-    int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
-    float4 v[kBufs][kBatch][NPOL];         // (V.x, -s V.y, V.y, s V.x), s = -1 for w < 0
-    uint32_t list[kBufs][kComputeWarps][kBatch];  // record | first slot << 8 | last slot << 11
+    // per consumer warp: (padded-table index of the tile origin for the record,
+    // visibility id | conj << 31) of every record meeting the warp's block
+    int2 list[kBufs][kComputeWarps][kBatch];
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
@@ -83,7 +77,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     const int hb = a.beta / 2;
 
     if (warp >= kComputeWarps) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
         // ------------------------------------------------------------ producers
         // The four warps of this warpgroup stage each batch together: warp pw
         // takes records pw, pw + 4, ... of every 128-record group.
@@ -116,7 +109,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                     for (int g = 0; g < nb; g += 128) {
                         const int r = g + lane * 4 + pw;
                         const bool act = r < nb;
-                        uint32_t e = 0;
+                        int base = 0;
+                        uint32_t vidc = 0;
                         int cu0 = 1, cu1 = 0, cv0 = 1, cv1 = 0, vlo = 0, vhi = -1;
                         if (act) {
                             const uint32_t id = __ldg(a.entries + item.start + b0 + r);
@@ -126,22 +120,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                                                   ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
                                                       (int64_t)(S + 6) * SP;
                             // padded index of the tile origin relative to this record
-                            sm.rec[buf][r] = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                            const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
-                            float2 v[NPOL];
-#pragma unroll
-                            for (int p = 0; p < NPOL; ++p) v[p] = __ldg(a.vis + (int64_t)id * NPOL + p);
-                            if (a.weight) {
-#pragma unroll
-                                for (int p = 0; p < NPOL; ++p) {
-                                    const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
-                                    v[p].x *= w;
-                                    v[p].y *= w;
-                                }
-                            }
-#pragma unroll
-                            for (int p = 0; p < NPOL; ++p)
-                                sm.v[buf][r][p] = make_float4(v[p].x, -sg * v[p].y, v[p].y, sg * v[p].x);
+                            base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
+                            vidc = id | ((rc.flags & GW_FLAG_CONJ) ? 0x80000000u : 0u);
                             // footprint relative to the tile
                             const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
                             vlo = rc.kv - h - tv0;
@@ -150,26 +130,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                             cu1 = min(kTileU - 1, uhi) >> 3;
                             cv0 = 0;
                             cv1 = (vhi >= 0 && vlo <= kTileV - 1) ? 0 : -1;
-                            e = (uint32_t)r;
                         }
                         // warp-aggregated appends: one shared atomic per target warp
-                        {
-                            const bool in_v = act && cv0 <= cv1;
-                            const int j0 = max(0, vlo) >> 2;
-                            const int j1 = min(kTileV - 1, vhi) >> 2;
-                            const uint32_t jr = in_v ? ((uint32_t)j0 | ((uint32_t)j1 << 3)) : 0u;
-                            for (int cu = 0; cu < kTileU / 8; ++cu) {
-                                const bool want = in_v && cu >= cu0 && cu <= cu1;
-                                const uint32_t bal = __ballot_sync(0xffffffffu, want);
-                                if (!bal) continue;
-                                const int w = cu;
-                                int base = 0;
-                                const int leader = __ffs(bal) - 1;
-                                if (lane == leader) base = atomicAdd(&sm.cnt[buf][w], __popc(bal));
-                                base = __shfl_sync(0xffffffffu, base, leader);
-                                if (want)
-                                    sm.list[buf][w][base + __popc(bal & ((1u << lane) - 1u))] = e | (jr << 8);
-                            }
+                        const int j0 = max(0, vlo) >> 2, j1 = min(kTileV - 1, vhi) >> 2;
+                        for (int w = 0; w < kComputeWarps; ++w) {
+                            const int cu = w % kColBlocks, j = w / kColBlocks;
+                            const bool want = act && cv0 <= cv1 && cu >= cu0 && cu <= cu1 &&
+                                              j >= j0 && j <= j1;
+                            const uint32_t bal = __ballot_sync(0xffffffffu, want);
+                            if (!bal) continue;
+                            int pos0 = 0;
+                            const int leader = __ffs(bal) - 1;
+                            if (lane == leader) pos0 = atomicAdd(&sm.cnt[buf][w], __popc(bal));
+                            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+                            if (want) sm.list[buf][w][pos0 + __popc(bal & ((1u << lane) - 1u))] = make_int2(base, (int)vidc);
                         }
                     }
                     if (pw == 0 && lane == 0) {
@@ -197,60 +171,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     }
 
     // ---------------------------------------------------------------- consumers
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
-    const int bu = warp * 8;
+    const int bu = (warp % kColBlocks) * 8, bv = (warp / kColBlocks) * 4;
     const int lu = lane & 7, lv = lane >> 3;
-    const float2* __restrict__ tab = a.ptable + lv * SP + bu + lu;
+    const float2* __restrict__ tab = a.ptable + (bv + lv) * SP + bu + lu;
     const int N = a.N;
-    // P = sum K (.) (V.x, -s V.y), Q = sum K (.) (V.y, s V.x):
-    // re = P.x + P.y, im = Q.x + Q.y  (s = -1 for the conjugate kernel)
-    float2 P[kSlots][NPOL], Q[kSlots][NPOL];
+    // Separate accumulators for records with the kernel (n) and with its
+    // conjugate (c, w < 0), with P = sum K (.) V and Q = sum (K.y, K.x) (.) V:
+    //   K V       : re = P.x - P.y,  im = Q.x + Q.y
+    //   conj(K) V : re = P.x + P.y,  im = Q.y - Q.x
+    float2 Pn[NPOL], Qn[NPOL], Pc[NPOL], Qc[NPOL];
 #pragma unroll
-    for (int j = 0; j < kSlots; ++j)
-#pragma unroll
-        for (int p = 0; p < NPOL; ++p) P[j][p] = Q[j][p] = make_float2(0.f, 0.f);
+    for (int p = 0; p < NPOL; ++p) Pn[p] = Qn[p] = Pc[p] = Qc[p] = make_float2(0.f, 0.f);
 
-    // Active slots of an entry are the contiguous range [j0, j1]: a switch on
-    // j0 falls through the slots and breaks after j1, so inactive slots issue
-    // nothing (no predicated-off work).
-#define GW_LOAD_SLOT(K, p_, j) K[j] = __ldg((p_) + (j) * 4 * SP)
-#define GW_LOAD(K, e)                                                          \
-    do {                                                                       \
-        const float2* p_ = tab + sm.rec[buf][(e) & 0xff];                      \
-        const int j0_ = ((e) >> 8) & 7, j1_ = ((e) >> 11) & 7;                 \
-        switch (j0_) {                                                         \
-            case 0: GW_LOAD_SLOT(K, p_, 0); if (j1_ == 0) break;               \
-            case 1: GW_LOAD_SLOT(K, p_, 1); if (j1_ == 1) break;               \
-            case 2: GW_LOAD_SLOT(K, p_, 2); if (j1_ == 2) break;               \
-            case 3: GW_LOAD_SLOT(K, p_, 3); if (j1_ == 3) break;               \
-            case 4: GW_LOAD_SLOT(K, p_, 4); if (j1_ == 4) break;               \
-            case 5: GW_LOAD_SLOT(K, p_, 5); if (j1_ == 5) break;               \
-            case 6: GW_LOAD_SLOT(K, p_, 6); if (j1_ == 6) break;               \
-            default: GW_LOAD_SLOT(K, p_, 7);                                    \
-        }                                                                      \
-    } while (0)
-#define GW_FMA_SLOT(K, j)                                                      \
-    _Pragma("unroll") for (int p = 0; p < NPOL; ++p) {                         \
-        P[j][p] = __ffma2_rn(K[j], make_float2(V[p].x, V[p].y), P[j][p]);      \
-        Q[j][p] = __ffma2_rn(K[j], make_float2(V[p].z, V[p].w), Q[j][p]);      \
-    }
-#define GW_FMA(K, e)                                                           \
-    do {                                                                       \
-        const float4* v_ = sm.v[buf][(e) & 0xff];                              \
-        float4 V[NPOL];                                                        \
-        _Pragma("unroll") for (int p = 0; p < NPOL; ++p) V[p] = v_[p];         \
-        const int j0_ = ((e) >> 8) & 7, j1_ = ((e) >> 11) & 7;                 \
-        switch (j0_) {                                                         \
-            case 0: GW_FMA_SLOT(K, 0) if (j1_ == 0) break;                     \
-            case 1: GW_FMA_SLOT(K, 1) if (j1_ == 1) break;                     \
-            case 2: GW_FMA_SLOT(K, 2) if (j1_ == 2) break;                     \
-            case 3: GW_FMA_SLOT(K, 3) if (j1_ == 3) break;                     \
-            case 4: GW_FMA_SLOT(K, 4) if (j1_ == 4) break;                     \
-            case 5: GW_FMA_SLOT(K, 5) if (j1_ == 5) break;                     \
-            case 6: GW_FMA_SLOT(K, 6) if (j1_ == 6) break;                     \
-            default: GW_FMA_SLOT(K, 7)                                          \
-        }                                                                      \
-    } while (0)
+    struct Stage {
+        float2 K;
+        float2 V[NPOL];
+        uint32_t conj;
+    };
+    auto load_stage = [&](Stage& st, int2 e) {
+        st.K = __ldg(tab + e.x);
+        const uint32_t vid = (uint32_t)e.y & 0x7fffffffu;
+        st.conj = (uint32_t)e.y >> 31;
+        const float2* vp = a.vis + (size_t)vid * NPOL;
+        if constexpr (NPOL % 2 == 0) {
+#pragma unroll
+            for (int p = 0; p < NPOL; p += 2) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(vp + p));
+                st.V[p] = make_float2(q.x, q.y);
+                st.V[p + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) st.V[p] = __ldg(vp + p);
+        }
+    };
+    auto fma_stage = [&](const Stage& st) {
+        const float2 Ks = make_float2(st.K.y, st.K.x);
+        if (st.conj) {
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) {
+                Pc[p] = __ffma2_rn(st.K, st.V[p], Pc[p]);
+                Qc[p] = __ffma2_rn(Ks, st.V[p], Qc[p]);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) {
+                Pn[p] = __ffma2_rn(st.K, st.V[p], Pn[p]);
+                Qn[p] = __ffma2_rn(Ks, st.V[p], Qn[p]);
+            }
+        }
+    };
 
     int buf = 0;
     for (;;) {
@@ -259,48 +229,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
         if (tile < 0) break;
         const int last = sm.last[buf];
         const int n = sm.cnt[buf][warp];
-        const uint32_t* lst = sm.list[buf][warp];
-        // three-stage pipeline over the warp's entries: kernel values of the
-        // next two entries are in flight while one entry's multiply-adds issue
-        float2 KA[kSlots], KB[kSlots], KC[kSlots];
-        uint32_t eA = 0, eB = 0, eC = 0;
-        if (n > 0) { eA = lst[0]; GW_LOAD(KA, eA); }
-        if (n > 1) { eB = lst[1]; GW_LOAD(KB, eB); }
+        const int2* lst = sm.list[buf][warp];
+        // three-stage pipeline: kernel values and visibilities of the next two
+        // entries are in flight while one entry's multiply-adds issue
+        Stage A, B, C;
+        if (n > 0) load_stage(A, lst[0]);
+        if (n > 1) load_stage(B, lst[1]);
         int i = 0;
         for (; i + 2 < n; i += 3) {
-            eC = lst[i + 2];
-            GW_LOAD(KC, eC);
-            GW_FMA(KA, eA);
-            if (i + 3 < n) { eA = lst[i + 3]; GW_LOAD(KA, eA); }
-            GW_FMA(KB, eB);
-            if (i + 4 < n) { eB = lst[i + 4]; GW_LOAD(KB, eB); }
-            GW_FMA(KC, eC);
+            load_stage(C, lst[i + 2]);
+            fma_stage(A);
+            if (i + 3 < n) load_stage(A, lst[i + 3]);
+            fma_stage(B);
+            if (i + 4 < n) load_stage(B, lst[i + 4]);
+            fma_stage(C);
         }
-        if (i < n) GW_FMA(KA, eA);
-        if (i + 1 < n) GW_FMA(KB, eB);
+        if (i < n) fma_stage(A);
+        if (i + 1 < n) fma_stage(B);
         if (last) {
-            // commit the tile's accumulators of this work item
+            // commit the block's accumulators of this work item
             const int u = (tile % side_u) * kTileU + bu + lu;
-            const int v0 = (tile / side_u) * kTileV + lv;
+            const int v = (tile / side_u) * kTileV + bv + lv;
 #pragma unroll
-            for (int j = 0; j < kSlots; ++j) {
-                const int v = v0 + 4 * j;
-#pragma unroll
-                for (int p = 0; p < NPOL; ++p) {
-                    const float re = P[j][p].x + P[j][p].y, im = Q[j][p].x + Q[j][p].y;
-                    if (u < N && v < N && (re != 0.f || im != 0.f))
-                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, make_float2(re, im));
-                    P[j][p] = Q[j][p] = make_float2(0.f, 0.f);
-                }
+            for (int p = 0; p < NPOL; ++p) {
+                const float re = (Pn[p].x - Pn[p].y) + (Pc[p].x + Pc[p].y);
+                const float im = (Qn[p].x + Qn[p].y) + (Qc[p].y - Qc[p].x);
+                if (u < N && v < N && (re != 0.f || im != 0.f))
+                    atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, make_float2(re, im));
+                Pn[p] = Qn[p] = Pc[p] = Qc[p] = make_float2(0.f, 0.f);
             }
         }
         bar_arrive(1 + kBufs + buf, kSyncThreads);  // buffer free
         buf = (buf + 1) % kBufs;
     }
-#undef GW_LOAD
-#undef GW_LOAD_SLOT
-#undef GW_FMA
-#undef GW_FMA_SLOT
 }
 
 template <int NPOL, int SP>
@@ -348,7 +309,25 @@ __global__ void k_pad_tables(const float2* __restrict__ tab, const int64_t* __re
     }
 }
 
+__global__ void k_weight_vis(const float2* __restrict__ vis, const float* __restrict__ w,
+                             int64_t n, float2* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = vis[e];
+        const float s = w[e];
+        out[e] = make_float2(v.x * s, v.y * s);
+    }
+}
+
 }  // namespace
+
+void launch_weight_vis(const float2* vis, const float* w, int64_t n, float2* out, cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_weight_vis<<<(unsigned)blocks, 256, 0, s>>>(vis, w, n, out);
+    note_launch();
+}
 
 int padded_stride(int smax) {
     const int need = smax + 14;

@@ -13,8 +13,8 @@ namespace gw {
 
 constexpr double kC0 = 299792458.0;   // speed of light, m/s
 constexpr int kTile = 32;             // grid tile side of the degridding binner
-constexpr int kGridTileU = 64;        // gridder tile: 64 (u) x 32 (v)
-constexpr int kGridTileV = 32;
+constexpr int kGridTileU = 32;        // gridder tile: 32 (u) x 16 (v)
+constexpr int kGridTileV = 16;
 constexpr int kItemMax = 1024;        // max bin entries per gridder work item
 constexpr double kQLimit = 1073741824.0;  // 2^30: |q| bound for a representable record
 
@@ -59,6 +59,7 @@ struct Scratch {
     uint32_t* counters = nullptr;     // [4]: 0 = item queue head, 1..3 spare
     unsigned long long* dropped = nullptr;  // [1]
     unsigned long long* work = nullptr;     // [2]: valid visibilities, sum of S_p^2
+    float2* wvis = nullptr;                 // [chunk * npol] weighted visibilities (lazy)
     int64_t entries_cap = 0;
     int64_t items_cap = 0;
 };
@@ -116,6 +117,8 @@ struct GridArgs {
     int pad_stride;              // padded row stride (padded_stride(S_max))
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
+// out[e] = vis[e] * w[e] (weights applied before gridding).
+void launch_weight_vis(const float2* vis, const float* w, int64_t n, float2* out, cudaStream_t s);
 // Zero-padded slice layout used by the gridder: (S + 6) rows x SP columns,
 // SP = padded_stride(S_max) >= S_max + 14, one of a few compile-time strides.
 int padded_stride(int smax);
