@@ -246,7 +246,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 
     const int N = desc->grid_n, P = desc->n_wplanes, beta = desc->oversample;
     p->field = (double)N * desc->cell_rad;
-    p->geom_grid = BinGeom{0, 5, 4, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
+    p->geom_grid = BinGeom{0, 5, 5, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
     p->geom_degrid = BinGeom{1, 5, 5, (N + kTile - 1) / kTile, (N + kTile - 1) / kTile};
     p->ntiles = std::max(p->geom_grid.ntu * p->geom_grid.ntv, p->geom_degrid.ntu * p->geom_degrid.ntv);
     p->support.resize(P);

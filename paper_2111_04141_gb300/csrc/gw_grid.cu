@@ -5,45 +5,39 @@
 //     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
 //
 // Design (GB300):
-// * A CTA owns one 32 (u) x 16 (v) tile of the grid for a work item (a run of
-//   that tile's bin).  Sixteen consumer warps each own one 8 x 4 block of the
-//   tile (lane (lu, lv) holds point (lu, lv) for every polarisation) and keep
-//   its accumulators in registers for the whole work item, so each grid point
-//   is committed once per work item (vector atomics, red.global).
-// * A warpgroup of four producer warps walks the work item in batches and
-//   appends, for every record, one 8-byte entry (table index of the tile
-//   origin relative to the record, visibility id, conjugation bit) to the
-//   list of every consumer warp whose block the record's footprint meets
-//   (warp-aggregated shared atomics; four batches in flight, handed over with
-//   named barriers).  A consumer reads one entry per record that touches its
-//   block and runs no other per-record control: wasted multiply-adds are
-//   limited to the parts of an 8 x 4 block outside a footprint.
+// * A CTA owns one 32 x 32 tile of the grid for a work item (a run of that
+//   tile's bin) and keeps the tile's accumulators in registers, so each grid
+//   point is committed once per work item (vector atomics, red.global).
+//   Two CTAs run per SM.
+// * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
+//   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
+//   polarisation.  Four slots per warp amortise each record's staged
+//   visibility over up to 4 x 32 points.
+// * A ninth, producer warp stages batches of records into shared memory
+//   (double-buffered, handed over with named barriers) and, for every record,
+//   appends it to the list of each compute warp whose block its footprint
+//   meets, together with the range of slots its rows meet.  Compute warps
+//   therefore only see records that touch them.
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
 //   rows around each S x S slice, one compile-time row stride per plan), so
-//   lanes outside the footprint read zeros without predication.  Visibilities
-//   are read straight from the visibility array with broadcast loads (the
-//   shared-memory path is the scarce one).  Kernel values and visibilities of
-//   the next two entries are in flight while one entry's multiply-adds issue.
-// * Per tap and polarisation the complex update costs two packed FP32x2 FMAs
-//   (Blackwell FFMA2: two multiply-adds per issued instruction), accumulated
-//   as P = sum K (.) V and Q = sum (K.y, K.x) (.) V, separately for records
-//   that use the kernel and for those that use its conjugate (w < 0); the
-//   real and imaginary parts are formed at commit.
+//   lanes outside the footprint read zeros and slot addresses are immediate
+//   offsets; loads for the next record are issued before the multiply-adds
+//   of the current one.
+// * Per tap and polarisation the update is two packed FP32x2 FMAs (Blackwell
+//   FFMA2) on the (re, im) accumulator pair:
+//     acc += (K.re, K.re) (.) A + (K.im, K.im) (.) B
+//   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
+//   kernel (w < 0), precomputed per record.
 #include "gw_internal.cuh"
 
 namespace gw {
 
 namespace {
 
-constexpr int kColBlocks = 4, kRowBlocks = 4;            // 8 x 4 blocks per tile
-constexpr int kComputeWarps = kColBlocks * kRowBlocks;   // one 8 x 4 block per warp
-constexpr int kThreads = (kComputeWarps + 4) * 32;       // + one producer warpgroup
-constexpr int kSyncThreads = kThreads;                   // threads in the batch barriers
-constexpr int kProducerThreads = 4 * 32;                 // producer-only barrier (id 9)
+constexpr int kComputeWarps = 8;
+constexpr int kThreads = (kComputeWarps + 1) * 32;
 constexpr int kBatch = 256;
-constexpr int kBufs = 4;             // batches in flight (barriers 1..4 full, 5..8 empty)
-constexpr int kTileU = 8 * kColBlocks, kTileV = 4 * kRowBlocks;
-static_assert(kTileU == kGridTileU && kTileV == kGridTileV, "tile shape");
+constexpr int kBufs = 2;
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
     int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
@@ -59,111 +53,101 @@ __device__ __forceinline__ void bar_arrive(int id, int n) {
 
 template <int NPOL>
 struct Smem {
-    // per consumer warp: (padded-table index of the tile origin for the record,
-    // visibility id | conj << 31) of every record meeting the warp's block
-    int2 list[kBufs][kComputeWarps][kBatch];
+    int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
+    float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
     int cnt[kBufs][kComputeWarps];
     int tile[kBufs];                       // tile of the batch; -1 = end of work
     int last[kBufs];                       // batch ends its work item
-    uint32_t item;                         // work item fetched by the first producer warp
 };
 
 template <int NPOL, int SP>
-__global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int side_u = a.ntiles_u;
+    const int side = a.ntiles_u;
     const int hb = a.beta / 2;
 
-    if (warp >= kComputeWarps) {
-        // ------------------------------------------------------------ producers
-        // The four warps of this warpgroup stage each batch together: warp pw
-        // takes records pw, pw + 4, ... of every 128-record group.
-        const int pw = warp - kComputeWarps;
+    if (warp == kComputeWarps) {
+        // ------------------------------------------------------------ producer
         const uint32_t nitems = *a.item_count;
         int buf = 0, uses = 0;
         for (;;) {
-            if (warp == kComputeWarps && lane == 0) sm.item = atomicAdd(a.queue, 1u);
-            bar_sync(9, kProducerThreads);
-            const uint32_t it = sm.item;
-            bar_sync(9, kProducerThreads);   // everyone has read sm.item
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(a.queue, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
             const bool done = it >= nitems;
             Item item{};
             if (!done) item = a.items[it];
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
-                if (uses >= kBufs) bar_sync(1 + kBufs + buf, kSyncThreads);  // wait until consumed
-                if (pw == 0 && lane < kComputeWarps) sm.cnt[buf][lane] = 0;
-                bar_sync(9, kProducerThreads);   // counters cleared before any append
+                if (uses >= kBufs) bar_sync(3 + buf, kThreads);  // wait until consumed
+                if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
+                __syncwarp();
                 if (done) {
-                    if (pw == 0 && lane == 0) {
+                    if (lane == 0) {
                         sm.tile[buf] = -1;
                         sm.last[buf] = 1;
                     }
                 } else {
-                    const int tu0 = (item.tile % side_u) * kTileU;
-                    const int tv0 = (item.tile / side_u) * kTileV;
+                    const int tu0 = (item.tile % side) * kTile;
+                    const int tv0 = (item.tile / side) * kTile;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
-                    for (int g = 0; g < nb; g += 128) {
-                        const int r = g + lane * 4 + pw;
-                        const bool act = r < nb;
-                        int base = 0;
-                        uint32_t vidc = 0;
-                        int cu0 = 1, cu1 = 0, cv0 = 1, cv1 = 0, vlo = 0, vhi = -1;
-                        if (act) {
-                            const uint32_t id = __ldg(a.entries + item.start + b0 + r);
-                            const gw_index_rec rc = load_rec(a.rec, id);
-                            const int S = __ldg(a.support + rc.plane), h = S >> 1;
-                            const int64_t slice = __ldg(a.pplane_off + rc.plane) +
-                                                  ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
-                                                      (int64_t)(S + 6) * SP;
-                            // padded index of the tile origin relative to this record
-                            base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                            vidc = id | ((rc.flags & GW_FLAG_CONJ) ? 0x80000000u : 0u);
-                            // footprint relative to the tile
-                            const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
-                            vlo = rc.kv - h - tv0;
-                            vhi = rc.kv + h - tv0;
-                            cu0 = max(0, ulo) >> 3;
-                            cu1 = min(kTileU - 1, uhi) >> 3;
-                            cv0 = 0;
-                            cv1 = (vhi >= 0 && vlo <= kTileV - 1) ? 0 : -1;
+                    for (int r = lane; r < nb; r += 32) {
+                        const uint32_t id = __ldg(a.entries + item.start + b0 + r);
+                        const gw_index_rec rc = load_rec(a.rec, id);
+                        const int S = __ldg(a.support + rc.plane), h = S >> 1;
+                        const int64_t slice = __ldg(a.pplane_off + rc.plane) +
+                                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
+                                                  (int64_t)(S + 6) * SP;
+                        // padded index of the tile origin relative to this record
+                        const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
+                        sm.rec[buf][r] = base;
+                        const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
+#pragma unroll
+                        for (int p = 0; p < NPOL; ++p) {
+                            float2 v = __ldg(a.vis + (int64_t)id * NPOL + p);
+                            if (a.weight) {
+                                const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
+                                v.x *= w;
+                                v.y *= w;
+                            }
+                            sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
+                                                   : make_float4(v.x, v.y, -v.y, v.x);
                         }
-                        // warp-aggregated appends: one shared atomic per target warp
-                        const int j0 = max(0, vlo) >> 2, j1 = min(kTileV - 1, vhi) >> 2;
-                        for (int w = 0; w < kComputeWarps; ++w) {
-                            const int cu = w % kColBlocks, j = w / kColBlocks;
-                            const bool want = act && cv0 <= cv1 && cu >= cu0 && cu <= cu1 &&
-                                              j >= j0 && j <= j1;
-                            const uint32_t bal = __ballot_sync(0xffffffffu, want);
-                            if (!bal) continue;
-                            int pos0 = 0;
-                            const int leader = __ffs(bal) - 1;
-                            if (lane == leader) pos0 = atomicAdd(&sm.cnt[buf][w], __popc(bal));
-                            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
-                            if (want) sm.list[buf][w][pos0 + __popc(bal & ((1u << lane) - 1u))] = make_int2(base, (int)vidc);
+                        // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
+                        const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
+                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
+                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTile - 1, uhi) >> 3;
+                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTile - 1, vhi) >> 4;
+                        for (int cv = cv0; cv <= cv1; ++cv) {
+                            const int j0 = max(0, vlo - 16 * cv) >> 2;
+                            const int j1 = min(15, vhi - 16 * cv) >> 2;
+                            const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
+                            for (int cu = cu0; cu <= cu1; ++cu) {
+                                const int w = cv * 4 + cu;
+                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
+                                sm.list[buf][w][pos] = e;
+                            }
                         }
                     }
-                    if (pw == 0 && lane == 0) {
+                    if (lane == 0) {
                         sm.tile[buf] = item.tile;
                         sm.last[buf] = (b == nb_total - 1);
                     }
                 }
                 __syncwarp();
                 __threadfence_block();
-                bar_arrive(1 + buf, kSyncThreads);  // this warp's part of the batch is ready
-                buf = (buf + 1) % kBufs;
+                bar_arrive(1 + buf, kThreads);  // batch ready
+                buf ^= 1;
                 ++uses;
             }
             if (done) {
-                // complete the consumers' last releases of the other buffers so
+                // complete the consumers' last release of the other buffer so
                 // that every barrier generation is balanced before exit
-                // (batch k was released by the consumers for k < E = uses - 1;
-                // the producer already waited on releases of k <= E - kBufs)
-                for (int k = max(0, uses - kBufs); k <= uses - 2; ++k)
-                    bar_sync(1 + kBufs + (k % kBufs), kSyncThreads);
+                if (uses >= 2) bar_sync(3 + buf, kThreads);
                 break;
             }
         }
@@ -171,96 +155,89 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     }
 
     // ---------------------------------------------------------------- consumers
-    const int bu = (warp % kColBlocks) * 8, bv = (warp / kColBlocks) * 4;
+    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
     const int lu = lane & 7, lv = lane >> 3;
     const float2* __restrict__ tab = a.ptable + (bv + lv) * SP + bu + lu;
     const int N = a.N;
-    // Separate accumulators for records with the kernel (n) and with its
-    // conjugate (c, w < 0), with P = sum K (.) V and Q = sum (K.y, K.x) (.) V:
-    //   K V       : re = P.x - P.y,  im = Q.x + Q.y
-    //   conj(K) V : re = P.x + P.y,  im = Q.y - Q.x
-    float2 Pn[NPOL], Qn[NPOL], Pc[NPOL], Qc[NPOL];
+    float2 acc[4][NPOL];   // (re, im)
 #pragma unroll
-    for (int p = 0; p < NPOL; ++p) Pn[p] = Qn[p] = Pc[p] = Qc[p] = make_float2(0.f, 0.f);
-
-    struct Stage {
-        float2 K;
-        float2 V[NPOL];
-        uint32_t conj;
-    };
-    auto load_stage = [&](Stage& st, int2 e) {
-        st.K = __ldg(tab + e.x);
-        const uint32_t vid = (uint32_t)e.y & 0x7fffffffu;
-        st.conj = (uint32_t)e.y >> 31;
-        const float2* vp = a.vis + (size_t)vid * NPOL;
-        if constexpr (NPOL % 2 == 0) {
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int p = 0; p < NPOL; p += 2) {
-                const float4 q = __ldg(reinterpret_cast<const float4*>(vp + p));
-                st.V[p] = make_float2(q.x, q.y);
-                st.V[p + 1] = make_float2(q.z, q.w);
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) st.V[p] = __ldg(vp + p);
-        }
-    };
-    auto fma_stage = [&](const Stage& st) {
-        const float2 Ks = make_float2(st.K.y, st.K.x);
-        if (st.conj) {
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) {
-                Pc[p] = __ffma2_rn(st.K, st.V[p], Pc[p]);
-                Qc[p] = __ffma2_rn(Ks, st.V[p], Qc[p]);
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) {
-                Pn[p] = __ffma2_rn(st.K, st.V[p], Pn[p]);
-                Qn[p] = __ffma2_rn(Ks, st.V[p], Qn[p]);
-            }
-        }
-    };
+        for (int p = 0; p < NPOL; ++p) acc[j][p] = make_float2(0.f, 0.f);
 
     int buf = 0;
     for (;;) {
-        bar_sync(1 + buf, kSyncThreads);  // wait for the batch
+        bar_sync(1 + buf, kThreads);  // wait for the batch
         const int tile = sm.tile[buf];
         if (tile < 0) break;
         const int last = sm.last[buf];
         const int n = sm.cnt[buf][warp];
-        const int2* lst = sm.list[buf][warp];
-        // three-stage pipeline: kernel values and visibilities of the next two
-        // entries are in flight while one entry's multiply-adds issue
-        Stage A, B, C;
-        if (n > 0) load_stage(A, lst[0]);
-        if (n > 1) load_stage(B, lst[1]);
-        int i = 0;
-        for (; i + 2 < n; i += 3) {
-            load_stage(C, lst[i + 2]);
-            fma_stage(A);
-            if (i + 3 < n) load_stage(A, lst[i + 3]);
-            fma_stage(B);
-            if (i + 4 < n) load_stage(B, lst[i + 4]);
-            fma_stage(C);
+        const uint32_t* lst = sm.list[buf][warp];
+
+        // software pipeline: kernel values of entry i+1 load during entry i's FMAs
+        float2 Kc0, Kc1, Kc2, Kc3, Kn0 = {}, Kn1 = {}, Kn2 = {}, Kn3 = {};
+        uint32_t ec = 0, en = 0;
+#define GW_LOAD_K(e, K0, K1, K2, K3)                                                  \
+        do {                                                                          \
+            const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
+            const float2* p_ = tab + sm.rec[buf][r_];                                  \
+            K0 = K1 = K2 = K3 = make_float2(0.f, 0.f);                                 \
+            if (0 >= j0_ && 0 <= j1_) K0 = __ldg(p_);                                  \
+            if (1 >= j0_ && 1 <= j1_) K1 = __ldg(p_ + 4 * SP);                         \
+            if (2 >= j0_ && 2 <= j1_) K2 = __ldg(p_ + 8 * SP);                         \
+            if (3 >= j0_ && 3 <= j1_) K3 = __ldg(p_ + 12 * SP);                        \
+        } while (0)
+        if (n > 0) {
+            ec = lst[0];
+            GW_LOAD_K(ec, Kc0, Kc1, Kc2, Kc3);
         }
-        if (i < n) fma_stage(A);
-        if (i + 1 < n) fma_stage(B);
-        if (last) {
-            // commit the block's accumulators of this work item
-            const int u = (tile % side_u) * kTileU + bu + lu;
-            const int v = (tile / side_u) * kTileV + bv + lv;
+        for (int i = 0; i < n; ++i) {
+            if (i + 1 < n) {
+                en = lst[i + 1];
+                GW_LOAD_K(en, Kn0, Kn1, Kn2, Kn3);
+            }
+            const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
+            float4 V[NPOL];
 #pragma unroll
-            for (int p = 0; p < NPOL; ++p) {
-                const float re = (Pn[p].x - Pn[p].y) + (Pc[p].x + Pc[p].y);
-                const float im = (Qn[p].x + Qn[p].y) + (Qc[p].y - Qc[p].x);
-                if (u < N && v < N && (re != 0.f || im != 0.f))
-                    atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, make_float2(re, im));
-                Pn[p] = Qn[p] = Pc[p] = Qc[p] = make_float2(0.f, 0.f);
+            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
+            const float2 Kc[4] = {Kc0, Kc1, Kc2, Kc3};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= j0 && j <= j1) {
+                    // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
+                    const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
+                    const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+#pragma unroll
+                    for (int p = 0; p < NPOL; ++p) {
+                        acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
+                        acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+                    }
+                }
+            }
+            ec = en;
+            Kc0 = Kn0;
+            Kc1 = Kn1;
+            Kc2 = Kn2;
+            Kc3 = Kn3;
+        }
+#undef GW_LOAD_K
+        if (last) {
+            // commit the tile's accumulators of this work item
+            const int u = (tile % a.ntiles_u) * kTile + bu + lu;
+            const int v0 = (tile / a.ntiles_u) * kTile + bv + lv;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int v = v0 + 4 * j;
+#pragma unroll
+                for (int p = 0; p < NPOL; ++p) {
+                    if (u < N && v < N && (acc[j][p].x != 0.f || acc[j][p].y != 0.f))
+                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, acc[j][p]);
+                    acc[j][p] = make_float2(0.f, 0.f);
+                }
             }
         }
-        bar_arrive(1 + kBufs + buf, kSyncThreads);  // buffer free
-        buf = (buf + 1) % kBufs;
+        bar_arrive(3 + buf, kThreads);  // buffer free
+        buf ^= 1;
     }
 }
 

@@ -13,8 +13,8 @@ namespace gw {
 
 constexpr double kC0 = 299792458.0;   // speed of light, m/s
 constexpr int kTile = 32;             // grid tile side of the degridding binner
-constexpr int kGridTileU = 32;        // gridder tile: 32 (u) x 16 (v)
-constexpr int kGridTileV = 16;
+constexpr int kGridTileU = 32;        // gridder tile: 32 (u) x 32 (v)
+constexpr int kGridTileV = 32;
 constexpr int kItemMax = 1024;        // max bin entries per gridder work item
 constexpr double kQLimit = 1073741824.0;  // 2^30: |q| bound for a representable record
 

@@ -157,7 +157,7 @@ def test_tables_match_oracle(gw, case):
 def test_bins(gw, case, mode):
     name, obs, prm = case
     ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
-    tu_, tv_ = (32, 16) if mode == 0 else (32, 32)
+    tu_, tv_ = (32, 32) if mode == 0 else (32, 32)
     ntu = (prm.grid_n + tu_ - 1) // tu_
     ntv = (prm.grid_n + tv_ - 1) // tv_
     S = plane_support(prm)
