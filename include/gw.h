@@ -163,6 +163,23 @@ gw_status gw_degrid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz
                         int32_t nchan, const void* grid, void* vis_out, int64_t* n_dropped,
                         void* cuda_stream);
 
+/* Degridding without any allocation.  The thesis has no counterpart; this
+ * exists for callers that cannot call cudaMalloc once they are running (a
+ * process whose device memory is all handed to another allocator at
+ * start-up, or a loop that must not take the driver's allocation lock).
+ * Same contract and result as gw_degrid_vis, but its scratch (index records
+ * and centre-tile bins) lives in one file-scope device array of about 2.5 MiB
+ * that every GPU loading the library holds until exit; nothing is allocated.
+ * Limits: nrow * nchan <= 65536 and grid_n <= 8192, else GW_EINVAL with the
+ * limit in gw_last_error().  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls share the one array and each call overwrites
+ * it: calls whose GPU work overlaps (different streams, or different plans
+ * on the same device) race; serialise them. */
+gw_status gw_degrid_vis_static(gw_plan plan, const double* uvw_m, const double* freq_hz,
+                               int64_t nrow, int32_t nchan, const void* grid, void* vis_out,
+                               int64_t* n_dropped, void* cuda_stream);
+
 /* Grid correction (Correction Step, Section 2.3 / 3.3.8), in place on
  * image (device, [npol][N][N] c64):
  *     image[pol][i][j] *= s(i, j) * h(m_i) * h(l_j),

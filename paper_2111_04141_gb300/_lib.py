@@ -55,6 +55,8 @@ _SIGS = {
                             ctypes.POINTER(c_i64), c_vp]),
     "gw_degrid_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
                               ctypes.POINTER(c_i64), c_vp]),
+    "gw_degrid_vis_static": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
+                                     ctypes.POINTER(c_i64), c_vp]),
     "gw_grid_correct": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
     "gw_grid_shift": (c_i32, [c_vp, c_vp, c_vp]),
     "gw_index_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, ctypes.POINTER(c_i64), c_vp]),

@@ -473,6 +473,61 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
     return finish_dropped(p, n_dropped, s);
 }
 
+gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                               int32_t nchan, const void* grid, void* vis_out, int64_t* n_dropped,
+                               void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!grid) return fail(GW_EINVAL, "null grid");
+    if (nrow > 0 && nchan > 0 && !vis_out) return fail(GW_EINVAL, "null vis_out");
+    const int64_t nvis = nrow * (int64_t)nchan;
+    if (nvis > static_scratch_max_vis())
+        return fail(GW_EINVAL, "gw_degrid_vis_static: %lld visibilities exceed the static scratch "
+                    "limit of %lld per call", (long long)nvis, (long long)static_scratch_max_vis());
+    const BinGeom& g = p->geom_degrid;
+    if (g.ntu * g.ntv > static_scratch_max_tiles())
+        return fail(GW_EINVAL, "gw_degrid_vis_static: grid_n %d needs %d tiles, the static scratch "
+                    "holds %d (grid_n <= 8192)", p->desc.grid_n, g.ntu * g.ntv,
+                    static_scratch_max_tiles());
+    Scratch sc;
+    cudaError_t e = static_scratch_view(p->device, &sc);
+    if (e != cudaSuccess) return cuda_fail(e, "locating the static scratch (cudaGetSymbolAddress)");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the array keeps the previous call's contents: reset what must start at zero
+    e = cudaMemsetAsync(sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc.work, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && nvis > 0)
+        e = cudaMemsetAsync(vis_out, 0, sizeof(float2) * nvis * p->desc.npol, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (nvis > 0) {
+        launch_index(uvw_m, freq_hz, nrow, nchan, p->ip, sc.rec, sc.dropped, s);
+        launch_bin(sc.rec, nvis, g, p->desc.n_wplanes, p->desc.support_min, p->desc.support_max,
+                   sc, s);
+        DegridArgs a;
+        a.rec = sc.rec;
+        a.grid = reinterpret_cast<const float2*>(grid);
+        a.table = p->table;
+        a.plane_off = p->d_plane_off;
+        a.support = p->d_support;
+        a.entries = sc.entries;
+        a.n_entries = sc.offsets + g.ntu * g.ntv;
+        a.vis_out = reinterpret_cast<float2*>(vis_out);
+        a.N = p->desc.grid_n;
+        a.npol = p->desc.npol;
+        a.beta = p->desc.oversample;
+        launch_degrid(a, nvis, p->num_sms, s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "static degrid launch");
+    }
+    if (!n_dropped) return GW_OK;
+    unsigned long long h = 0;
+    e = cudaMemcpyAsync(&h, sc.dropped, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the drop count");
+    *n_dropped = (int64_t)h;
+    return GW_OK;
+}
+
 gw_status gw_grid_correct(gw_plan p, void* image, int32_t direction, void* cuda_stream) {
     if (!p) return fail(GW_EINVAL, "null plan");
     gw_status st = check_device(p);

@@ -139,6 +139,13 @@ struct DegridArgs {
 };
 void launch_degrid(const DegridArgs& a, int64_t nvis_upper, int num_sms, cudaStream_t s);
 
+// ---- allocation-free scratch (gw_noalloc.cu) ------------------------------
+// View of the file-scope static scratch on `device` (current); looks up the
+// symbol's device address on first use per device.
+cudaError_t static_scratch_view(int device, Scratch* sc);
+int64_t static_scratch_max_vis();
+int static_scratch_max_tiles();
+
 // ---- correction (gw_correct.cu) -------------------------------------------
 void launch_correct(float2* image, const float* h, int N, int npol, int mode, cudaStream_t s);
 void launch_shift(float2* grid, int N, int npol, cudaStream_t s);

@@ -138,6 +138,28 @@ class Plan:
                                           _stream_ptr(stream, self.device)), "gw_degrid_vis")
         return (out, int(dropped.value)) if return_dropped else out
 
+    def degrid_static(self, uvw, freq, grid, out=None, stream=None, return_dropped=False):
+        """Degrid without allocating device memory (gw_degrid_vis_static).
+
+        For callers that cannot allocate while running: scratch comes from a
+        fixed device array inside the library (<= 65536 visibilities per call,
+        grid_n <= 8192).  ``out`` must be supplied by such callers; calls that
+        overlap on the GPU race on the shared array.
+        """
+        nrow, nchan = self._coords(uvw, freq)
+        _need(grid, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        if out is None:
+            out = torch.empty((nrow, nchan, self.npol), dtype=torch.complex64, device=self.device)
+        _need(out, "vis_out", torch.complex64, self.device, (nrow, nchan, self.npol))
+        dropped = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_degrid_vis_static(self._h, _ptr(uvw), _ptr(freq), nrow, nchan,
+                                                 _ptr(grid), _ptr(out),
+                                                 ctypes.byref(dropped) if return_dropped else None,
+                                                 _stream_ptr(stream, self.device)),
+                  "gw_degrid_vis_static")
+        return (out, int(dropped.value)) if return_dropped else out
+
     def correct(self, image, direction: int = 1, stream=None):
         _need(image, "image", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
         with torch.cuda.device(self.device):
