@@ -40,7 +40,8 @@ struct gw_plan_s {
     gw_plan_desc desc{};
     int device = -1;
     int num_sms = 0;
-    BinGeom geom_grid{}, geom_degrid{};
+    BinGeom geom_grid{}, geom_degrid{}, geom_staged{};
+    int hmax = 0;        // largest half-support over the planes
     int ntiles = 0;      // bins allocated (max over both geometries)
     int pad_stride = 0;
     double field = 0, table_scale = 0;
@@ -166,15 +167,15 @@ struct StageTimer {
 
 // Index + bin one chunk of rows; leaves records and bins in the plan scratch.
 gw_status index_and_bin(gw_plan p, const double* uvw, const double* freq, int64_t nrow, int nchan,
-                        int mode, cudaStream_t s) {
+                        const BinGeom& geom, cudaStream_t s) {
     {
         StageTimer t(p, kStIndex, s);
         launch_index(uvw, freq, nrow, nchan, p->ip, p->sc.rec, p->sc.dropped, s);
     }
     {
         StageTimer t(p, kStBin, s);
-        launch_bin(p->sc.rec, nrow * (int64_t)nchan, mode == 0 ? p->geom_grid : p->geom_degrid,
-                   p->desc.n_wplanes, p->desc.support_min, p->desc.support_max, p->sc, s);
+        launch_bin(p->sc.rec, nrow * (int64_t)nchan, geom, p->desc.n_wplanes,
+                   p->desc.support_min, p->desc.support_max, p->sc, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "index/bin launch");
@@ -248,7 +249,13 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     p->field = (double)N * desc->cell_rad;
     p->geom_grid = BinGeom{0, 5, 5, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
     p->geom_degrid = BinGeom{1, 5, 5, (N + kTile - 1) / kTile, (N + kTile - 1) / kTile};
-    p->ntiles = std::max(p->geom_grid.ntu * p->geom_grid.ntv, p->geom_degrid.ntu * p->geom_degrid.ntv);
+    {
+        const int st = degrid_staged_tile();
+        p->geom_staged = BinGeom{1, 4, 4, (N + st - 1) / st, (N + st - 1) / st};
+    }
+    p->ntiles = std::max({p->geom_grid.ntu * p->geom_grid.ntv,
+                          p->geom_degrid.ntu * p->geom_degrid.ntv,
+                          p->geom_staged.ntu * p->geom_staged.ntv});
     p->support.resize(P);
     p->wplane.resize(P);
     p->plane_off.resize(P + 1);
@@ -261,6 +268,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
         smax_real = std::max(smax_real, p->support[q]);
     }
     p->pad_stride = padded_stride(smax_real);
+    p->hmax = smax_real / 2;
     for (int q = 0; q < P; ++q) {
         const double r = P > 1 ? (double)q / (double)(P - 1) : 0.0;
         p->wplane[q] = P > 1 ? desc->w_max_lambda * (r * r) : 0.0;
@@ -389,7 +397,7 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
     for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
         const int64_t nr = std::min(rpc, nrow - r0);
         const int64_t v0 = r0 * nchan;
-        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, 0, s);
+        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, p->geom_grid, s);
         if (st != GW_OK) return st;
         GridArgs a;
         a.rec = p->sc.rec;
@@ -449,7 +457,9 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         float2* out = reinterpret_cast<float2*>(vis_out) + v0 * npol;
         e = cudaMemsetAsync(out, 0, sizeof(float2) * nr * nchan * npol, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, 1, s);
+        const bool staged = degrid_staged_fits(p->hmax, npol);
+        const BinGeom& geom = staged ? p->geom_staged : p->geom_degrid;
+        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, geom, s);
         if (st != GW_OK) return st;
         DegridArgs a;
         a.rec = p->sc.rec;
@@ -458,14 +468,19 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = p->sc.entries;
-        a.n_entries = p->sc.offsets + p->geom_degrid.ntu * p->geom_degrid.ntv;
+        a.n_entries = p->sc.offsets + geom.ntu * geom.ntv;
         a.vis_out = out;
         a.N = p->desc.grid_n;
         a.npol = npol;
         a.beta = p->desc.oversample;
+        a.items = p->sc.items;
+        a.item_count = p->sc.item_off + geom.ntu * geom.ntv;
+        a.queue = p->sc.counters;
+        a.ntiles_u = geom.ntu;
         {
             StageTimer t(p, kStDegrid, s);
-            launch_degrid(a, nr * nchan, p->num_sms, s);
+            if (!(staged && launch_degrid_staged(a, p->hmax, p->num_sms, s)))
+                launch_degrid(a, nr * nchan, p->num_sms, s);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "degrid launch");
@@ -630,9 +645,9 @@ gw_status gw_debug_bins(gw_plan p, const double* uvw_m, const double* freq_hz, i
     if (!tile_offsets || (mode != 0 && mode != 1)) return fail(GW_EINVAL, "bad arguments");
     if (nrow * (int64_t)nchan > p->chunk) return fail(GW_EINVAL, "input exceeds one chunk");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    st = index_and_bin(p, uvw_m, freq_hz, nrow, nchan, mode, s);
-    if (st != GW_OK) return st;
     const BinGeom& g = mode == 0 ? p->geom_grid : p->geom_degrid;
+    st = index_and_bin(p, uvw_m, freq_hz, nrow, nchan, g, s);
+    if (st != GW_OK) return st;
     std::vector<uint32_t> offs(g.ntu * g.ntv + 1);
     cudaError_t e = cudaMemcpyAsync(offs.data(), p->sc.offsets, sizeof(uint32_t) * offs.size(),
                                     cudaMemcpyDeviceToHost, s);

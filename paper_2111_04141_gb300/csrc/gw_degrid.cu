@@ -3,10 +3,19 @@
 //     V[pol] = sum_{tv, tu} conj(K_i(tv, tu)) * G[pol][kv + tv][ku + tu],
 // K_i the record's kernel (K_p[ov][ou], or its conjugate when w < 0).
 //
-// One warp per visibility: lanes stride over the taps of each footprint
-// row, multiply-accumulate all polarisations, and reduce with warp
-// shuffles.  Visibilities are visited in centre-tile order so that
-// neighbouring warps read overlapping grid footprints from L1/L2.
+// Two kernels:
+// * k_degrid_staged (used by gw_degrid_vis): a CTA takes a work item of one
+//   16 x 16 centre tile, copies the tile's grid region (the tile plus the
+//   plan's largest half-support on every side, polarisations interleaved) into
+//   shared memory once, and serves all records of the item from it, so the
+//   grid is read from L2/HBM about once per tile instead of once per tap.
+//   One warp per record: lanes take consecutive taps of the S x S footprint
+//   (flattened, so every lane is busy), multiply-accumulate all polarisations
+//   against the kernel slice (read coalesced from the table) and reduce with
+//   warp shuffles.
+// * k_degrid (the fallback when the region does not fit in shared memory,
+//   and the allocation-free entry point): the same per-record warp, reading
+//   the grid through L1/L2, records visited in 32 x 32 centre-tile order.
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -81,7 +90,127 @@ void launch_t(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
     note_launch();
 }
 
+constexpr int kStagedThreads = 512;
+constexpr int kStagedTile = 16;
+
+template <int NPOL>
+__global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, int hmax) {
+    extern __shared__ __align__(16) float2 reg[];          // [RS][RS][NPOL]
+    __shared__ uint32_t s_item;
+    const int RS = kStagedTile + 2 * hmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = kStagedThreads / 32;
+    const int N = a.N, hb = a.beta / 2;
+    const uint32_t nitems = *a.item_count;
+    for (;;) {
+        __syncthreads();                       // previous item fully consumed
+        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= nitems) break;
+        const Item item = a.items[it];
+        const int rx0 = (item.tile % a.ntiles_u) * kStagedTile - hmax;
+        const int ry0 = (item.tile / a.ntiles_u) * kStagedTile - hmax;
+        // stage the region, polarisations interleaved
+        for (int e = threadIdx.x; e < RS * RS; e += kStagedThreads) {
+            const int y = e / RS, x = e - y * RS;
+            const int gy = ry0 + y, gx = rx0 + x;
+            const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p)
+                reg[(size_t)e * NPOL + p] =
+                    in ? __ldg(a.grid + ((int64_t)p * N + gy) * N + gx) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int r = warp; r < item.len; r += nwarps) {
+            const uint32_t id = __ldg(a.entries + item.start + r);
+            int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
+            const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
+            const int S = __ldg(a.support + rc.plane), h = S >> 1;
+            const float2* K = a.table + __ldg(a.plane_off + rc.plane) +
+                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+            const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
+            // region index of tap (0, 0)
+            const int base = (rc.kv - h - ry0) * RS + (rc.ku - h - rx0);
+            float acc[NPOL][2];
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) acc[p][0] = acc[p][1] = 0.f;
+            const int n = S * S;
+            // flattened taps t = lane + 32 i, (tv, tu) advanced incrementally
+            const int dq = 32 / S, dr = 32 - dq * S;
+            int tv = lane / S, tu = lane - (lane / S) * S;
+            for (int t = lane; t < n; t += 32) {
+                const float2 k = __ldg(K + t);
+                const float ki = sg * k.y;
+                const float2* g = reg + (size_t)(base + tv * RS + tu) * NPOL;
+#pragma unroll
+                for (int p = 0; p < NPOL; ++p) {
+                    const float2 gv = g[p];
+                    // conj(K_i) G with K_i = K (w >= 0) or conj K (w < 0)
+                    acc[p][0] = fmaf(k.x, gv.x, acc[p][0]);
+                    acc[p][0] = fmaf(ki, gv.y, acc[p][0]);
+                    acc[p][1] = fmaf(k.x, gv.y, acc[p][1]);
+                    acc[p][1] = fmaf(-ki, gv.x, acc[p][1]);
+                }
+                tu += dr;
+                tv += dq;
+                if (tu >= S) {
+                    tu -= S;
+                    ++tv;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p)
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    acc[p][0] += __shfl_xor_sync(0xffffffffu, acc[p][0], d);
+                    acc[p][1] += __shfl_xor_sync(0xffffffffu, acc[p][1], d);
+                }
+            if (lane < NPOL) {
+                float re = acc[0][0], im = acc[0][1];
+#pragma unroll
+                for (int p = 1; p < NPOL; ++p)
+                    if (lane == p) { re = acc[p][0]; im = acc[p][1]; }
+                a.vis_out[(int64_t)id * NPOL + lane] = make_float2(re, im);
+            }
+        }
+    }
+}
+
+template <int NPOL>
+bool launch_staged_t(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s) {
+    const int RS = kStagedTile + 2 * hmax;
+    const size_t smem = (size_t)RS * RS * NPOL * sizeof(float2);
+    if (smem > kStagedSmemMax) return false;
+    cudaFuncSetAttribute(k_degrid_staged<NPOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_staged<NPOL>, kStagedThreads,
+                                                  smem);
+    if (per_sm < 1) return false;
+    k_degrid_staged<NPOL><<<num_sms * per_sm, kStagedThreads, smem, s>>>(a, hmax);
+    note_launch();
+    return true;
+}
+
 }  // namespace
+
+int degrid_staged_tile() { return kStagedTile; }
+
+bool degrid_staged_fits(int hmax, int npol) {
+    const int RS = kStagedTile + 2 * hmax;
+    return (size_t)RS * RS * npol * sizeof(float2) <= kStagedSmemMax;
+}
+
+bool launch_degrid_staged(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s) {
+    cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
+    switch (a.npol) {
+        case 1: return launch_staged_t<1>(a, hmax, num_sms, s);
+        case 2: return launch_staged_t<2>(a, hmax, num_sms, s);
+        case 3: return launch_staged_t<3>(a, hmax, num_sms, s);
+        default: return launch_staged_t<4>(a, hmax, num_sms, s);
+    }
+}
 
 void launch_degrid(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
     switch (a.npol) {

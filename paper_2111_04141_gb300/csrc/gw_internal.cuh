@@ -136,8 +136,18 @@ struct DegridArgs {
     const uint32_t* n_entries;  // device scalar
     float2* vis_out;            // [nvis][npol]
     int N, npol, beta;
+    // staged kernel only: work items over 16 x 16 centre tiles
+    const Item* items = nullptr;
+    const uint32_t* item_count = nullptr;
+    uint32_t* queue = nullptr;
+    int ntiles_u = 0;
 };
 void launch_degrid(const DegridArgs& a, int64_t nvis_upper, int num_sms, cudaStream_t s);
+constexpr size_t kStagedSmemMax = 200 * 1024;   // staged-degrid region budget (bytes)
+int degrid_staged_tile();
+bool degrid_staged_fits(int hmax, int npol);
+// Returns false (nothing launched) if the region does not fit.
+bool launch_degrid_staged(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s);
 
 // ---- allocation-free scratch (gw_noalloc.cu) ------------------------------
 // View of the file-scope static scratch on `device` (current); looks up the

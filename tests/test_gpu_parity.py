@@ -65,6 +65,10 @@ CASES = {
                                            beta=16, seed=5),
     "bigS": lambda: syn.small_case(n_ant=6, n_times=12, n_chan=2, npol=1, grid_n=256,
                                    s_min=15, s_max=63, n_w=6, diameter_m=1500.0, seed=9),
+    # staged degridding region (16 + 70)^2 x 4 pols > shared-memory budget:
+    # exercises the global-gather fallback
+    "wide-4pol": lambda: syn.small_case(n_ant=5, n_times=6, n_chan=2, npol=4, grid_n=256,
+                                        s_min=15, s_max=71, n_w=4, diameter_m=1000.0, seed=13),
 }
 
 
