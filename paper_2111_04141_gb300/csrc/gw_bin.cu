@@ -166,7 +166,7 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
                                                        sc.cursor, sc.entries);
         note_launch();
     }
-    {
+    if (sc.items) {   // work items (the allocation-free degrid path has none)
         const int tb = (ntiles + 255) / 256;
         k_items<<<tb, 256, 0, s>>>(sc.count, sc.offsets, sc.item_off, ntiles, sc.items);
         note_launch();

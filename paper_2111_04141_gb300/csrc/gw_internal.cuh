@@ -80,6 +80,7 @@ struct BinGeom {
     int mode, su, sv, ntu, ntv;
 };
 // Also accumulates sc.work[0] += valid records, sc.work[1] += sum of S_p^2.
+// Work items are written only when sc.items is non-null.
 void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
                 Scratch& sc, cudaStream_t s);
 
