@@ -40,7 +40,9 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid.cu); null otherwise.
-GRID_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "capture": None}
+GRID_TRAFFIC = {"sha256": "79742d88160e95f056fe985c4c2db419d1e05ed026e3677d48e0f8ab1bc9d9b0",
+                "bytes_per_launch": 1.014889e9 + 0.266981e9,
+                "capture": "profiles/k_grid_wproj4096.md"}
 
 
 def parse():
@@ -55,8 +57,10 @@ def parse():
                     help="rows of the workload in the CPU-baseline sample (0 = 1/8 of rows)")
     ap.add_argument("--times", type=int, default=256,
                     help="time steps of the workload (256 = the full workload)")
-    ap.add_argument("--profile-only", action="store_true",
-                    help="plan + warm-up + one gridding call, no timing or JSON (for ncu)")
+    ap.add_argument("--profile-only", nargs="?", const="grid", default=None,
+                    choices=["grid", "degrid"],
+                    help="plan + warm-up + one gridding (or degridding) call, no timing or "
+                         "JSON (for ncu)")
     return ap.parse_args()
 
 
@@ -226,7 +230,12 @@ def main():
         plan.grid(uvw, freq, vis, out=grid)
     torch.cuda.synchronize(dev)
     if args.profile_only:
-        plan.grid(uvw, freq, vis, out=grid)
+        if args.profile_only == "degrid":
+            out_vis = torch.empty_like(vis)
+            for _ in range(4):
+                plan.degrid(uvw, freq, grid, out=out_vis)
+        else:
+            plan.grid(uvw, freq, vis, out=grid)
         torch.cuda.synchronize(dev)
         plan.close()
         return
