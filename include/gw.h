@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 1
+#define GW_API_VERSION 2
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -57,10 +57,19 @@ typedef enum {
     GW_EDEVICE = -6        /* called with a different current device than the plan's */
 } gw_status;
 
+/* Storage type of visibilities and of the kernel tables.  The 16-bit kinds
+ * are pairs (re in the low 16 bits of a 32-bit word, im in the high 16 bits,
+ * little-endian: the memory layout of two consecutive 16-bit values re, im).
+ * They change storage only: visibilities and table entries are widened to
+ * FP32 on load and every sum is FP32; FP64 is kept for coordinates, index
+ * selection and table generation.  Degridded visibilities are rounded to
+ * the plan's vis_dtype (to nearest) when stored.  Float16 has a narrow
+ * range (|x| <= 65504): visibilities must lie in it, and float16 tables are
+ * stored scaled by 2^table_exp2 (gw_plan_info), undone in FP32. */
 typedef enum {
-    GW_C64 = 0,            /* complex float32 pairs */
-    GW_BF16X2 = 1,         /* complex bfloat16 pairs */
-    GW_F16X2 = 2           /* complex float16 pairs */
+    GW_C64 = 0,            /* complex float32 pairs, 8 bytes */
+    GW_BF16X2 = 1,         /* complex bfloat16 pairs, 4 bytes */
+    GW_F16X2 = 2           /* complex float16 pairs, 4 bytes */
 } gw_dtype;
 
 /* Plan descriptor.  Defines the imaging problem; see gw_plan_create. */
@@ -105,6 +114,11 @@ typedef struct {
     double field;             /* L = N * cell_rad */
     double taper_c;           /* PSWF bandwidth c = pi * support_min / 2 */
     double table_scale;       /* global kernel scale (w = 0, o = 0 slice sums to 1) */
+    int32_t vis_dtype, table_dtype;  /* gw_dtype of the plan */
+    int32_t table_exp2;       /* 16-bit tables store round(K * 2^table_exp2); 0 for
+                                 GW_C64 and GW_BF16X2; for GW_F16X2 chosen so the largest
+                                 entry (w = 0, o = 0 centre tap) lies in [2^14, 2^15) */
+    int32_t reserved;
 } gw_plan_info;
 
 /* ------------------------------------------------------------------------
@@ -143,8 +157,9 @@ gw_status gw_plan_info_get(gw_plan plan, gw_plan_info* out);
  * and chunked inputs add linearly; zero it first for a fresh image.
  *   uvw_m    device, [nrow][3] float64, metres
  *   freq_hz  device, [nchan] float64, Hz
- *   vis      device, [nrow][nchan][npol] complex of the plan's vis_dtype,
- *            16-byte aligned when npol is even (8-byte aligned otherwise)
+ *   vis      device, [nrow][nchan][npol] complex of the plan's vis_dtype;
+ *            GW_C64: 16-byte aligned when npol is even (8-byte otherwise);
+ *            16-bit kinds: 4-byte aligned
  *   weight   device, [nrow][nchan][npol] float32, or NULL for unit weights
  *   grid     device, [npol][N][N] c64, accumulated
  *   n_dropped host, optional: receives the number of visibilities dropped by
@@ -154,6 +169,27 @@ gw_status gw_plan_info_get(gw_plan plan, gw_plan_info* out);
 gw_status gw_grid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
                       int32_t nchan, const void* vis, const float* weight, void* grid,
                       int64_t* n_dropped, void* cuda_stream);
+
+/* Gridding with compensated commits (the Kahan-style variant of
+ * gw_grid_vis; same arguments plus grid_err).  Each grid point's partial
+ * sum over a work item is committed with an atomic add that returns the
+ * previous value; the exact rounding error of that FP32 addition
+ * (Knuth's TwoSum) is accumulated into grid_err.  grid + grid_err is then
+ * the sum of the commits with the FP32 commit rounding removed to first
+ * order; gw_grid_fold forms it.
+ *   grid_err device, [npol][N][N] c64, 8-byte aligned, caller-owned;
+ *            zero it together with the grid, pass the same buffer to every
+ *            call that accumulates into that grid, then call gw_grid_fold.
+ * Errors as gw_grid_vis, and GW_EINVAL for a null grid_err. */
+gw_status gw_grid_vis_compensated(gw_plan plan, const double* uvw_m, const double* freq_hz,
+                                  int64_t nrow, int32_t nchan, const void* vis,
+                                  const float* weight, void* grid, void* grid_err,
+                                  int64_t* n_dropped, void* cuda_stream);
+
+/* grid += grid_err, then grid_err = 0 (device, both [npol][N][N] c64):
+ * ends a sequence of gw_grid_vis_compensated calls.  Asynchronous on the
+ * stream.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */
+gw_status gw_grid_fold(gw_plan plan, void* grid, void* grid_err, void* cuda_stream);
 
 /* Degridding, the adjoint of gw_grid_vis with unit weights:
  *     vis_out[r][c][pol] = sum_{tv,tu} conj(K(tv, tu)) * grid[pol][kv + tv][ku + tu]
@@ -223,6 +259,11 @@ gw_status gw_index_vis(gw_plan plan, const double* uvw_m, const double* freq_hz,
  * plane_offsets (host, may be NULL) receives n_wplanes + 1 element offsets;
  * supports (host, may be NULL) receives n_wplanes supports.  Synchronous. */
 gw_status gw_plan_copy_tables(gw_plan plan, float* out, int64_t* plane_offsets, int32_t* supports);
+
+/* Copy the tables as stored (table_dtype elements: 8 bytes for GW_C64, 4
+ * for the 16-bit kinds, scaled by 2^table_exp2), same layout and element
+ * count as gw_plan_copy_tables.  Synchronous. */
+gw_status gw_plan_copy_stored_tables(gw_plan plan, void* out);
 
 /* Copy the corrector h(l_i), i = 0..N-1, to host memory (float64).  Synchronous. */
 gw_status gw_plan_copy_corrector(gw_plan plan, double* out);

@@ -34,7 +34,9 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("grid_n", c_i32), ("npol", c_i32), ("oversample", c_i32), ("n_wplanes", c_i32),
                 ("grid_tile_u", c_i32), ("grid_tile_v", c_i32), ("degrid_tile", c_i32),
                 ("device", c_i32), ("table_elems", c_i64), ("chunk_vis", c_i64),
-                ("field", c_f64), ("taper_c", c_f64), ("table_scale", c_f64)]
+                ("field", c_f64), ("taper_c", c_f64), ("table_scale", c_f64),
+                ("vis_dtype", c_i32), ("table_dtype", c_i32), ("table_exp2", c_i32),
+                ("reserved", c_i32)]
 
 
 class Timing(ctypes.Structure):
@@ -53,6 +55,9 @@ _SIGS = {
     "gw_plan_info_get": (c_i32, [c_vp, ctypes.POINTER(PlanInfo)]),
     "gw_grid_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp,
                             ctypes.POINTER(c_i64), c_vp]),
+    "gw_grid_vis_compensated": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                        ctypes.POINTER(c_i64), c_vp]),
+    "gw_grid_fold": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "gw_degrid_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
                               ctypes.POINTER(c_i64), c_vp]),
     "gw_degrid_vis_static": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
@@ -61,6 +66,7 @@ _SIGS = {
     "gw_grid_shift": (c_i32, [c_vp, c_vp, c_vp]),
     "gw_index_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, ctypes.POINTER(c_i64), c_vp]),
     "gw_plan_copy_tables": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "gw_plan_copy_stored_tables": (c_i32, [c_vp, c_vp]),
     "gw_plan_copy_corrector": (c_i32, [c_vp, c_vp]),
     "gw_plan_timing_enable": (c_i32, [c_vp, c_i32]),
     "gw_plan_timing_get": (c_i32, [c_vp, ctypes.POINTER(Timing)]),

@@ -51,8 +51,11 @@ struct gw_plan_s {
     int max_tiles_per_vis = 0;
     int64_t chunk = 0;
     // device state
-    float2* table = nullptr;
-    float2* ptable = nullptr;
+    float2* table = nullptr;      // FP32 tables (always built)
+    uint32_t* table16 = nullptr;  // 16-bit-pair tables (table_dtype != GW_C64)
+    void* ptable = nullptr;       // zero-padded gridder tables of kind table_dtype
+    int table_exp2 = 0;           // 16-bit tables hold K * 2^table_exp2
+    float table_inv = 1.f;        // 2^-table_exp2
     std::vector<int64_t> pplane_off;
     int64_t* d_pplane_off = nullptr;
     int64_t* d_plane_off = nullptr;
@@ -77,6 +80,7 @@ void plan_free(gw_plan p) {
     cudaFree(p->sc.work);
     cudaFree(p->sc.wvis);
     cudaFree(p->table);
+    cudaFree(p->table16);
     cudaFree(p->ptable);
     cudaFree(p->d_pplane_off);
     cudaFree(p->d_plane_off);
@@ -114,8 +118,10 @@ gw_status check_desc(const gw_plan_desc* d) {
     const double half = 0.5 * d->grid_n * d->cell_rad;
     if (d->n_wplanes > 1 && 2.0 * half * half >= 1.0)
         return fail(GW_EINVAL, "field of view too wide: corners reach l^2 + m^2 >= 1");
-    if (d->vis_dtype != GW_C64 || d->table_dtype != GW_C64)
-        return fail(GW_EUNSUPPORTED, "only GW_C64 visibilities and tables are implemented");
+    if (d->vis_dtype < GW_C64 || d->vis_dtype > GW_F16X2)
+        return fail(GW_EINVAL, "vis_dtype must be GW_C64, GW_BF16X2 or GW_F16X2");
+    if (d->table_dtype < GW_C64 || d->table_dtype > GW_F16X2)
+        return fail(GW_EINVAL, "table_dtype must be GW_C64, GW_BF16X2 or GW_F16X2");
     if (d->max_vis_per_call < 0) return fail(GW_EINVAL, "max_vis_per_call must be >= 0");
     return GW_OK;
 }
@@ -303,7 +309,16 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 #define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { plan_free(p); \
         return fail(GW_ENOMEM, "device allocation of %s failed", #x); } } while (0)
     GW_ALLOC(p->table, (size_t)p->plane_off[P]);
-    GW_ALLOC(p->ptable, (size_t)p->pplane_off[P]);
+    if (desc->table_dtype == GW_C64) {
+        float2* pt = nullptr;
+        GW_ALLOC(pt, (size_t)p->pplane_off[P]);
+        p->ptable = pt;
+    } else {
+        uint32_t* pt = nullptr;
+        GW_ALLOC(p->table16, (size_t)p->plane_off[P]);
+        GW_ALLOC(pt, (size_t)p->pplane_off[P]);
+        p->ptable = pt;
+    }
     GW_ALLOC(p->d_pplane_off, (size_t)P + 1);
     GW_ALLOC(p->d_plane_off, (size_t)P + 1);
     GW_ALLOC(p->d_support, (size_t)P);
@@ -344,10 +359,16 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     tb.wplane = p->wplane.data();
     tb.plane_off = p->plane_off.data();
     tb.num_sms = p->num_sms;
-    e = build_tables(tb, p->table, p->d_h, p->d_hf, &p->table_scale, s);
+    e = build_tables(tb, p->table, p->table16, desc->table_dtype, p->d_h, p->d_hf,
+                     &p->table_scale, &p->table_exp2, s);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "building kernel tables"); }
-    launch_pad_tables(p->table, p->d_plane_off, p->d_pplane_off, p->d_support, P, beta,
-                      p->pad_stride, p->ptable, s);
+    p->table_inv = std::ldexp(1.0f, -p->table_exp2);
+    if (desc->table_dtype == GW_C64)
+        launch_pad_tables(p->table, GW_C64, p->d_plane_off, p->d_pplane_off, p->d_support, P,
+                          beta, p->pad_stride, p->ptable, s);
+    else
+        launch_pad_tables(p->table16, desc->table_dtype, p->d_plane_off, p->d_pplane_off,
+                          p->d_support, P, beta, p->pad_stride, p->ptable, s);
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "padding kernel tables"); }
@@ -375,20 +396,28 @@ gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
     out->field = p->field;
     out->taper_c = M_PI * p->desc.support_min / 2.0;
     out->table_scale = p->table_scale;
+    out->vis_dtype = p->desc.vis_dtype;
+    out->table_dtype = p->desc.table_dtype;
+    out->table_exp2 = p->table_exp2;
+    out->reserved = 0;
     return GW_OK;
 }
 
-gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
-                      int32_t nchan, const void* vis, const float* weight, void* grid,
-                      int64_t* n_dropped, void* cuda_stream) {
+static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                           int32_t nchan, const void* vis, const float* weight, void* grid,
+                           void* grid_err, int64_t* n_dropped, void* cuda_stream) {
     gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
     if (st != GW_OK) return st;
     if (!grid) return fail(GW_EINVAL, "null grid");
     if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
-    if ((p->desc.npol % 2 == 0) && (reinterpret_cast<uintptr_t>(vis) % 16 != 0))
+    const int vk = p->desc.vis_dtype;
+    const size_t vb = dtype_bytes(vk);
+    if (vk == GW_C64 && (p->desc.npol % 2 == 0) && (reinterpret_cast<uintptr_t>(vis) % 16 != 0))
         return fail(GW_EINVAL, "vis must be 16-byte aligned when npol is even");
-    if ((reinterpret_cast<uintptr_t>(grid) % 8 != 0) || (reinterpret_cast<uintptr_t>(vis) % 8 != 0))
-        return fail(GW_EINVAL, "vis and grid must be 8-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(grid) % 8 != 0) || (reinterpret_cast<uintptr_t>(vis) % vb != 0))
+        return fail(GW_EINVAL, "grid must be 8-byte aligned and vis aligned to its element size");
+    if (grid_err && reinterpret_cast<uintptr_t>(grid_err) % 8 != 0)
+        return fail(GW_EINVAL, "grid_err must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -403,7 +432,8 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
         a.rec = p->sc.rec;
         a.ptable = p->ptable;
         a.pplane_off = p->d_pplane_off;
-        a.vis = reinterpret_cast<const float2*>(vis) + v0 * npol;
+        a.vis = static_cast<const char*>(vis) + (size_t)v0 * npol * vb;
+        a.vis_kind = vk;
         a.weight = nullptr;
         if (weight) {
             if (!p->sc.wvis) {
@@ -413,10 +443,13 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
                     return fail(GW_ENOMEM, "allocating weighted-visibility scratch");
                 }
             }
-            launch_weight_vis(a.vis, weight + v0 * npol, nr * nchan * npol, p->sc.wvis, s);
+            // weighted visibilities are formed in FP32
+            launch_weight_vis(a.vis, vk, weight + v0 * npol, nr * nchan * npol, p->sc.wvis, s);
             a.vis = p->sc.wvis;
+            a.vis_kind = GW_C64;
         }
-        a.table = p->table;
+        a.table_kind = p->desc.table_dtype;
+        a.table_inv = p->table_inv;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = p->sc.entries;
@@ -424,6 +457,7 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
         a.item_count = p->sc.item_off + p->geom_grid.ntu * p->geom_grid.ntv;
         a.queue = p->sc.counters;
         a.grid = reinterpret_cast<float2*>(grid);
+        a.grid_err = reinterpret_cast<float2*>(grid_err);
         a.N = p->desc.grid_n;
         a.npol = npol;
         a.beta = p->desc.oversample;
@@ -439,6 +473,34 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
     return finish_dropped(p, n_dropped, s);
 }
 
+gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                      int32_t nchan, const void* vis, const float* weight, void* grid,
+                      int64_t* n_dropped, void* cuda_stream) {
+    return grid_impl(p, uvw_m, freq_hz, nrow, nchan, vis, weight, grid, nullptr, n_dropped,
+                     cuda_stream);
+}
+
+gw_status gw_grid_vis_compensated(gw_plan p, const double* uvw_m, const double* freq_hz,
+                                  int64_t nrow, int32_t nchan, const void* vis,
+                                  const float* weight, void* grid, void* grid_err,
+                                  int64_t* n_dropped, void* cuda_stream) {
+    if (!grid_err) return fail(GW_EINVAL, "null grid_err");
+    return grid_impl(p, uvw_m, freq_hz, nrow, nchan, vis, weight, grid, grid_err, n_dropped,
+                     cuda_stream);
+}
+
+gw_status gw_grid_fold(gw_plan p, void* grid, void* grid_err, void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    if (!grid || !grid_err) return fail(GW_EINVAL, "null grid or grid_err");
+    const int64_t n = (int64_t)p->desc.npol * p->desc.grid_n * p->desc.grid_n;
+    launch_fold(reinterpret_cast<float2*>(grid), reinterpret_cast<float2*>(grid_err), n,
+                (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "fold launch");
+}
+
 gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
                         int32_t nchan, const void* grid, void* vis_out, int64_t* n_dropped,
                         void* cuda_stream) {
@@ -450,12 +512,15 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
     cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     const int npol = p->desc.npol;
+    const size_t vb = dtype_bytes(p->desc.vis_dtype);
+    if (reinterpret_cast<uintptr_t>(vis_out) % vb != 0)
+        return fail(GW_EINVAL, "vis_out must be aligned to its element size");
     const int64_t rpc = rows_per_chunk(p, nchan);
     for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
         const int64_t nr = std::min(rpc, nrow - r0);
         const int64_t v0 = r0 * nchan;
-        float2* out = reinterpret_cast<float2*>(vis_out) + v0 * npol;
-        e = cudaMemsetAsync(out, 0, sizeof(float2) * nr * nchan * npol, s);
+        void* out = static_cast<char*>(vis_out) + (size_t)v0 * npol * vb;
+        e = cudaMemsetAsync(out, 0, vb * nr * nchan * npol, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
         const bool staged = degrid_staged_fits(p->hmax, npol);
         const BinGeom& geom = staged ? p->geom_staged : p->geom_degrid;
@@ -464,7 +529,10 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         DegridArgs a;
         a.rec = p->sc.rec;
         a.grid = reinterpret_cast<const float2*>(grid);
-        a.table = p->table;
+        a.table = p->table16 ? (const void*)p->table16 : (const void*)p->table;
+        a.table_kind = p->desc.table_dtype;
+        a.vis_kind = p->desc.vis_dtype;
+        a.table_inv = p->table_inv;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = p->sc.entries;
@@ -496,6 +564,8 @@ gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* fre
     if (!grid) return fail(GW_EINVAL, "null grid");
     if (nrow > 0 && nchan > 0 && !vis_out) return fail(GW_EINVAL, "null vis_out");
     const int64_t nvis = nrow * (int64_t)nchan;
+    if (reinterpret_cast<uintptr_t>(vis_out) % dtype_bytes(p->desc.vis_dtype) != 0)
+        return fail(GW_EINVAL, "vis_out must be aligned to its element size");
     if (nvis > static_scratch_max_vis())
         return fail(GW_EINVAL, "gw_degrid_vis_static: %lld visibilities exceed the static scratch "
                     "limit of %lld per call", (long long)nvis, (long long)static_scratch_max_vis());
@@ -512,7 +582,7 @@ gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* fre
     e = cudaMemsetAsync(sc.dropped, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc.work, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess && nvis > 0)
-        e = cudaMemsetAsync(vis_out, 0, sizeof(float2) * nvis * p->desc.npol, s);
+        e = cudaMemsetAsync(vis_out, 0, (size_t)dtype_bytes(p->desc.vis_dtype) * nvis * p->desc.npol, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (nvis > 0) {
         launch_index(uvw_m, freq_hz, nrow, nchan, p->ip, sc.rec, sc.dropped, s);
@@ -521,12 +591,15 @@ gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* fre
         DegridArgs a;
         a.rec = sc.rec;
         a.grid = reinterpret_cast<const float2*>(grid);
-        a.table = p->table;
+        a.table = p->table16 ? (const void*)p->table16 : (const void*)p->table;
+        a.table_kind = p->desc.table_dtype;
+        a.vis_kind = p->desc.vis_dtype;
+        a.table_inv = p->table_inv;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = sc.entries;
         a.n_entries = sc.offsets + g.ntu * g.ntv;
-        a.vis_out = reinterpret_cast<float2*>(vis_out);
+        a.vis_out = vis_out;
         a.N = p->desc.grid_n;
         a.npol = p->desc.npol;
         a.beta = p->desc.oversample;
@@ -592,6 +665,16 @@ gw_status gw_plan_copy_tables(gw_plan p, float* out, int64_t* plane_offsets, int
     if (supports)
         for (size_t i = 0; i < p->support.size(); ++i) supports[i] = p->support[i];
     return GW_OK;
+}
+
+gw_status gw_plan_copy_stored_tables(gw_plan p, void* out) {
+    if (!p || !out) return fail(GW_EINVAL, "null argument");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    const void* src = p->table16 ? (const void*)p->table16 : (const void*)p->table;
+    cudaError_t e = cudaMemcpy(out, src, (size_t)dtype_bytes(p->desc.table_dtype) * p->plane_off.back(),
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "copying stored tables");
 }
 
 gw_status gw_plan_timing_enable(gw_plan p, int32_t enable) {

@@ -4,6 +4,7 @@
 //   correct: image[pol][i][j] *= s(i, j) h(m_i) h(l_j), s = (-1)^(i+j) when the
 //            image comes from (or goes to) an FFT of a shifted grid, else 1.
 //   shift:   grid[pol][kv][ku] *= (-1)^(kv+ku).
+//   fold:    grid += err, err = 0 (ends a compensated gridding sequence).
 // For even N, (-1)^(k) before and (-1)^(i) after an unnormalised FFT turn it
 // into the transform with both origins at pixel N/2.
 #include "gw_internal.cuh"
@@ -42,6 +43,19 @@ __global__ void k_shift(float2* __restrict__ g, int N, int npol) {
     }
 }
 
+__global__ void k_fold(float2* __restrict__ g, float2* __restrict__ err, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 d = err[e];
+        if (d.x == 0.f && d.y == 0.f) continue;
+        float2 v = g[e];
+        v.x += d.x;
+        v.y += d.y;
+        g[e] = v;
+        err[e] = make_float2(0.f, 0.f);
+    }
+}
+
 unsigned blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     if (b > 152 * 32) b = 152 * 32;
@@ -57,6 +71,11 @@ void launch_correct(float2* image, const float* h, int N, int npol, int mode, cu
 
 void launch_shift(float2* grid, int N, int npol, cudaStream_t s) {
     k_shift<<<blocks_for((int64_t)N * N), 256, 0, s>>>(grid, N, npol);
+    note_launch();
+}
+
+void launch_fold(float2* grid, float2* err, int64_t n, cudaStream_t s) {
+    k_fold<<<blocks_for(n), 256, 0, s>>>(grid, err, n);
     note_launch();
 }
 

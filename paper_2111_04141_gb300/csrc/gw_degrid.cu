@@ -2,6 +2,8 @@
 // (residualcalc), Section 1.6):
 //     V[pol] = sum_{tv, tu} conj(K_i(tv, tu)) * G[pol][kv + tv][ku + tu],
 // K_i the record's kernel (K_p[ov][ou], or its conjugate when w < 0).
+// Tables of any storage kind are widened to FP32 on load, the sum is FP32,
+// and the result is written in the plan's visibility kind.
 //
 // Two kernels:
 // * k_degrid_staged (used by gw_degrid_vis): a CTA takes a work item of one
@@ -24,8 +26,9 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <int NPOL>
+template <int NPOL, int TK>
 __global__ void __launch_bounds__(kThreads) k_degrid(DegridArgs a) {
+    using TE = TabElem<TK>;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -37,8 +40,9 @@ __global__ void __launch_bounds__(kThreads) k_degrid(DegridArgs a) {
         int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
         const gw_index_rec r = *reinterpret_cast<gw_index_rec*>(&rv);
         const int S = __ldg(a.support + r.plane), h = S >> 1;
-        const float2* K = a.table + __ldg(a.plane_off + r.plane) +
-                          ((int64_t)(r.ov + hb) * a.beta + (r.ou + hb)) * S * S;
+        const typename TE::T* K = reinterpret_cast<const typename TE::T*>(a.table) +
+                                  __ldg(a.plane_off + r.plane) +
+                                  ((int64_t)(r.ov + hb) * a.beta + (r.ou + hb)) * S * S;
         // conj(K_i): K_i = K for w >= 0 (use conj K), K_i = conj K for w < 0 (use K)
         const float s = (r.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
         float acc[NPOL][2];
@@ -47,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_degrid(DegridArgs a) {
         for (int tv = 0; tv < S; ++tv) {
             const int64_t row = r.kv - h + tv;
             for (int tu = lane; tu < S; tu += 32) {
-                const float2 k = __ldg(K + tv * S + tu);
+                const float2 k = TE::load(K + tv * S + tu);
                 const float ki = s * k.y;
                 const int64_t col = r.ku - h + tu;
 #pragma unroll
@@ -73,28 +77,30 @@ __global__ void __launch_bounds__(kThreads) k_degrid(DegridArgs a) {
 #pragma unroll
             for (int p = 1; p < NPOL; ++p)
                 if (lane == p) { re = acc[p][0]; im = acc[p][1]; }
-            a.vis_out[(int64_t)id * NPOL + lane] = make_float2(re, im);
+            store_vis(a.vis_out, a.vis_kind, (int64_t)id * NPOL + lane, re * a.table_inv,
+                      im * a.table_inv);
         }
     }
 }
 
-template <int NPOL>
+template <int NPOL, int TK>
 void launch_t(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<NPOL>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<NPOL, TK>, kThreads, 0);
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (nvis * 32 + kThreads - 1) / kThreads;
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms * per_sm);
     if (blocks < 1) blocks = 1;
-    k_degrid<NPOL><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    k_degrid<NPOL, TK><<<(unsigned)blocks, kThreads, 0, s>>>(a);
     note_launch();
 }
 
 constexpr int kStagedThreads = 512;
 constexpr int kStagedTile = 16;
 
-template <int NPOL>
+template <int NPOL, int TK>
 __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, int hmax) {
+    using TE = TabElem<TK>;
     extern __shared__ __align__(16) float2 reg[];          // [RS][RS][NPOL]
     __shared__ uint32_t s_item;
     const int RS = kStagedTile + 2 * hmax;
@@ -127,8 +133,9 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
             const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
             const int S = __ldg(a.support + rc.plane), h = S >> 1;
-            const float2* K = a.table + __ldg(a.plane_off + rc.plane) +
-                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+            const typename TE::T* K = reinterpret_cast<const typename TE::T*>(a.table) +
+                                      __ldg(a.plane_off + rc.plane) +
+                                      ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
             const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
             // region index of tap (0, 0)
             const int base = (rc.kv - h - ry0) * RS + (rc.ku - h - rx0);
@@ -140,7 +147,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             const int dq = 32 / S, dr = 32 - dq * S;
             int tv = lane / S, tu = lane - (lane / S) * S;
             for (int t = lane; t < n; t += 32) {
-                const float2 k = __ldg(K + t);
+                const float2 k = TE::load(K + t);
                 const float ki = sg * k.y;
                 const float2* g = reg + (size_t)(base + tv * RS + tu) * NPOL;
 #pragma unroll
@@ -171,26 +178,47 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
 #pragma unroll
                 for (int p = 1; p < NPOL; ++p)
                     if (lane == p) { re = acc[p][0]; im = acc[p][1]; }
-                a.vis_out[(int64_t)id * NPOL + lane] = make_float2(re, im);
+                store_vis(a.vis_out, a.vis_kind, (int64_t)id * NPOL + lane, re * a.table_inv,
+                          im * a.table_inv);
             }
         }
     }
 }
 
-template <int NPOL>
+template <int NPOL, int TK>
 bool launch_staged_t(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s) {
     const int RS = kStagedTile + 2 * hmax;
     const size_t smem = (size_t)RS * RS * NPOL * sizeof(float2);
     if (smem > kStagedSmemMax) return false;
-    cudaFuncSetAttribute(k_degrid_staged<NPOL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_degrid_staged<NPOL, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_staged<NPOL>, kStagedThreads,
-                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid_staged<NPOL, TK>,
+                                                  kStagedThreads, smem);
     if (per_sm < 1) return false;
-    k_degrid_staged<NPOL><<<num_sms * per_sm, kStagedThreads, smem, s>>>(a, hmax);
+    k_degrid_staged<NPOL, TK><<<num_sms * per_sm, kStagedThreads, smem, s>>>(a, hmax);
     note_launch();
     return true;
+}
+
+template <int TK>
+bool launch_staged_k(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s) {
+    switch (a.npol) {
+        case 1: return launch_staged_t<1, TK>(a, hmax, num_sms, s);
+        case 2: return launch_staged_t<2, TK>(a, hmax, num_sms, s);
+        case 3: return launch_staged_t<3, TK>(a, hmax, num_sms, s);
+        default: return launch_staged_t<4, TK>(a, hmax, num_sms, s);
+    }
+}
+
+template <int TK>
+void launch_k(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
+    switch (a.npol) {
+        case 1: launch_t<1, TK>(a, nvis, num_sms, s); break;
+        case 2: launch_t<2, TK>(a, nvis, num_sms, s); break;
+        case 3: launch_t<3, TK>(a, nvis, num_sms, s); break;
+        default: launch_t<4, TK>(a, nvis, num_sms, s); break;
+    }
 }
 
 }  // namespace
@@ -204,20 +232,18 @@ bool degrid_staged_fits(int hmax, int npol) {
 
 bool launch_degrid_staged(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s) {
     cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
-    switch (a.npol) {
-        case 1: return launch_staged_t<1>(a, hmax, num_sms, s);
-        case 2: return launch_staged_t<2>(a, hmax, num_sms, s);
-        case 3: return launch_staged_t<3>(a, hmax, num_sms, s);
-        default: return launch_staged_t<4>(a, hmax, num_sms, s);
+    switch (a.table_kind) {
+        case GW_BF16X2: return launch_staged_k<GW_BF16X2>(a, hmax, num_sms, s);
+        case GW_F16X2: return launch_staged_k<GW_F16X2>(a, hmax, num_sms, s);
+        default: return launch_staged_k<GW_C64>(a, hmax, num_sms, s);
     }
 }
 
 void launch_degrid(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
-    switch (a.npol) {
-        case 1: launch_t<1>(a, nvis, num_sms, s); break;
-        case 2: launch_t<2>(a, nvis, num_sms, s); break;
-        case 3: launch_t<3>(a, nvis, num_sms, s); break;
-        default: launch_t<4>(a, nvis, num_sms, s); break;
+    switch (a.table_kind) {
+        case GW_BF16X2: launch_k<GW_BF16X2>(a, nvis, num_sms, s); break;
+        case GW_F16X2: launch_k<GW_F16X2>(a, nvis, num_sms, s); break;
+        default: launch_k<GW_C64>(a, nvis, num_sms, s); break;
     }
 }
 

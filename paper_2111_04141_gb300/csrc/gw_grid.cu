@@ -1,274 +1,17 @@
-// Gridding kernel: w-projection convolutional gridding onto a complex grid.
-//
-// Computes the Gridding Step of Algorithm convgriddingoversampling
-// (Section 2.4.5) with the w-projection GCF (Section 1.7.1):
-//     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
-//
-// Design (GB300):
-// * A CTA owns one 32 x 32 tile of the grid for a work item (a run of that
-//   tile's bin) and keeps the tile's accumulators in registers, so each grid
-//   point is committed once per work item (vector atomics, red.global).
-//   Two CTAs run per SM.
-// * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
-//   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
-//   polarisation.  Four slots per warp amortise each record's staged
-//   visibility over up to 4 x 32 points.
-// * A ninth, producer warp stages batches of records into shared memory
-//   (double-buffered, handed over with named barriers) and, for every record,
-//   appends it to the list of each compute warp whose block its footprint
-//   meets, together with the range of slots its rows meet.  Compute warps
-//   therefore only see records that touch them.
-// * Kernel values come from zero-padded slices (7 zero columns and 3 zero
-//   rows around each S x S slice, one compile-time row stride per plan), so
-//   lanes outside the footprint read zeros and slot addresses are immediate
-//   offsets; loads for the next record are issued before the multiply-adds
-//   of the current one.
-// * Per tap and polarisation the update is two packed FP32x2 FMAs (Blackwell
-//   FFMA2) on the (re, im) accumulator pair:
-//     acc += (K.re, K.re) (.) A + (K.im, K.im) (.) B
-//   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
-//   kernel (w < 0), precomputed per record.
+// Gridding: table padding, visibility weighting and the dispatch to the
+// gridding kernel instantiated per table kind (gw_grid_kernel.cuh).
 #include "gw_internal.cuh"
 
 namespace gw {
 
 namespace {
 
-constexpr int kComputeWarps = 8;
-constexpr int kThreads = (kComputeWarps + 1) * 32;
-constexpr int kBatch = 256;
-constexpr int kBufs = 2;
-
-__device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
-    int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
-    return *reinterpret_cast<gw_index_rec*>(&v);
-}
-
-__device__ __forceinline__ void bar_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(int id, int n) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-template <int NPOL>
-struct Smem {
-    int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
-    float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
-    uint32_t list[kBufs][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
-    int cnt[kBufs][kComputeWarps];
-    int tile[kBufs];                       // tile of the batch; -1 = end of work
-    int last[kBufs];                       // batch ends its work item
-};
-
-template <int NPOL, int SP>
-__global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int side = a.ntiles_u;
-    const int hb = a.beta / 2;
-
-    if (warp == kComputeWarps) {
-        // ------------------------------------------------------------ producer
-        const uint32_t nitems = *a.item_count;
-        int buf = 0, uses = 0;
-        for (;;) {
-            uint32_t it = 0;
-            if (lane == 0) it = atomicAdd(a.queue, 1u);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            const bool done = it >= nitems;
-            Item item{};
-            if (!done) item = a.items[it];
-            const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
-            for (int b = 0; b < nb_total; ++b) {
-                if (uses >= kBufs) bar_sync(3 + buf, kThreads);  // wait until consumed
-                if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
-                __syncwarp();
-                if (done) {
-                    if (lane == 0) {
-                        sm.tile[buf] = -1;
-                        sm.last[buf] = 1;
-                    }
-                } else {
-                    const int tu0 = (item.tile % side) * kTile;
-                    const int tv0 = (item.tile / side) * kTile;
-                    const int b0 = b * kBatch;
-                    const int nb = min(kBatch, item.len - b0);
-                    for (int r = lane; r < nb; r += 32) {
-                        const uint32_t id = __ldg(a.entries + item.start + b0 + r);
-                        const gw_index_rec rc = load_rec(a.rec, id);
-                        const int S = __ldg(a.support + rc.plane), h = S >> 1;
-                        const int64_t slice = __ldg(a.pplane_off + rc.plane) +
-                                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
-                                                  (int64_t)(S + 6) * SP;
-                        // padded index of the tile origin relative to this record
-                        const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                        sm.rec[buf][r] = base;
-                        const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
-#pragma unroll
-                        for (int p = 0; p < NPOL; ++p) {
-                            float2 v = __ldg(a.vis + (int64_t)id * NPOL + p);
-                            if (a.weight) {
-                                const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
-                                v.x *= w;
-                                v.y *= w;
-                            }
-                            sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
-                                                   : make_float4(v.x, v.y, -v.y, v.x);
-                        }
-                        // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
-                        const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
-                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
-                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTile - 1, uhi) >> 3;
-                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTile - 1, vhi) >> 4;
-                        for (int cv = cv0; cv <= cv1; ++cv) {
-                            const int j0 = max(0, vlo - 16 * cv) >> 2;
-                            const int j1 = min(15, vhi - 16 * cv) >> 2;
-                            const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
-                            for (int cu = cu0; cu <= cu1; ++cu) {
-                                const int w = cv * 4 + cu;
-                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
-                                sm.list[buf][w][pos] = e;
-                            }
-                        }
-                    }
-                    if (lane == 0) {
-                        sm.tile[buf] = item.tile;
-                        sm.last[buf] = (b == nb_total - 1);
-                    }
-                }
-                __syncwarp();
-                __threadfence_block();
-                bar_arrive(1 + buf, kThreads);  // batch ready
-                buf ^= 1;
-                ++uses;
-            }
-            if (done) {
-                // complete the consumers' last release of the other buffer so
-                // that every barrier generation is balanced before exit
-                if (uses >= 2) bar_sync(3 + buf, kThreads);
-                break;
-            }
-        }
-        return;
-    }
-
-    // ---------------------------------------------------------------- consumers
-    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
-    const int lu = lane & 7, lv = lane >> 3;
-    const float2* __restrict__ tab = a.ptable + (bv + lv) * SP + bu + lu;
-    const int N = a.N;
-    float2 acc[4][NPOL];   // (re, im)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int p = 0; p < NPOL; ++p) acc[j][p] = make_float2(0.f, 0.f);
-
-    int buf = 0;
-    for (;;) {
-        bar_sync(1 + buf, kThreads);  // wait for the batch
-        const int tile = sm.tile[buf];
-        if (tile < 0) break;
-        const int last = sm.last[buf];
-        const int n = sm.cnt[buf][warp];
-        const uint32_t* lst = sm.list[buf][warp];
-
-        // software pipeline: kernel values of entry i+1 load during entry i's FMAs
-        float2 Kc0, Kc1, Kc2, Kc3, Kn0 = {}, Kn1 = {}, Kn2 = {}, Kn3 = {};
-        uint32_t ec = 0, en = 0;
-#define GW_LOAD_K(e, K0, K1, K2, K3)                                                  \
-        do {                                                                          \
-            const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
-            const float2* p_ = tab + sm.rec[buf][r_];                                  \
-            K0 = K1 = K2 = K3 = make_float2(0.f, 0.f);                                 \
-            if (0 >= j0_ && 0 <= j1_) K0 = __ldg(p_);                                  \
-            if (1 >= j0_ && 1 <= j1_) K1 = __ldg(p_ + 4 * SP);                         \
-            if (2 >= j0_ && 2 <= j1_) K2 = __ldg(p_ + 8 * SP);                         \
-            if (3 >= j0_ && 3 <= j1_) K3 = __ldg(p_ + 12 * SP);                        \
-        } while (0)
-        if (n > 0) {
-            ec = lst[0];
-            GW_LOAD_K(ec, Kc0, Kc1, Kc2, Kc3);
-        }
-        for (int i = 0; i < n; ++i) {
-            if (i + 1 < n) {
-                en = lst[i + 1];
-                GW_LOAD_K(en, Kn0, Kn1, Kn2, Kn3);
-            }
-            const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
-            float4 V[NPOL];
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
-            const float2 Kc[4] = {Kc0, Kc1, Kc2, Kc3};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j >= j0 && j <= j1) {
-                    // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
-                    const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
-                    const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
-#pragma unroll
-                    for (int p = 0; p < NPOL; ++p) {
-                        acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
-                        acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
-                    }
-                }
-            }
-            ec = en;
-            Kc0 = Kn0;
-            Kc1 = Kn1;
-            Kc2 = Kn2;
-            Kc3 = Kn3;
-        }
-#undef GW_LOAD_K
-        if (last) {
-            // commit the tile's accumulators of this work item
-            const int u = (tile % a.ntiles_u) * kTile + bu + lu;
-            const int v0 = (tile / a.ntiles_u) * kTile + bv + lv;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int v = v0 + 4 * j;
-#pragma unroll
-                for (int p = 0; p < NPOL; ++p) {
-                    if (u < N && v < N && (acc[j][p].x != 0.f || acc[j][p].y != 0.f))
-                        atomicAdd(a.grid + ((int64_t)p * N + v) * N + u, acc[j][p]);
-                    acc[j][p] = make_float2(0.f, 0.f);
-                }
-            }
-        }
-        bar_arrive(3 + buf, kThreads);  // buffer free
-        buf ^= 1;
-    }
-}
-
-template <int NPOL, int SP>
-void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
-    const size_t smem = sizeof(Smem<NPOL>);
-    cudaFuncSetAttribute(k_grid<NPOL, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP>, kThreads, smem);
-    if (per_sm < 1) per_sm = 1;
-    k_grid<NPOL, SP><<<num_sms * per_sm, kThreads, smem, s>>>(a);
-    note_launch();
-}
-
-template <int NPOL>
-void launch_t(const GridArgs& a, int num_sms, cudaStream_t s) {
-    switch (a.pad_stride) {
-        case 24: launch_sp<NPOL, 24>(a, num_sms, s); break;
-        case 32: launch_sp<NPOL, 32>(a, num_sms, s); break;
-        case 48: launch_sp<NPOL, 48>(a, num_sms, s); break;
-        case 80: launch_sp<NPOL, 80>(a, num_sms, s); break;
-        case 144: launch_sp<NPOL, 144>(a, num_sms, s); break;
-        default: launch_sp<NPOL, 272>(a, num_sms, s); break;
-    }
-}
-
 // Zero-padded copy of the tables: slice (p, o) becomes (S + 6) rows x SP
 // columns with the S x S values at row 3, column 7.
-__global__ void k_pad_tables(const float2* __restrict__ tab, const int64_t* __restrict__ plane_off,
+template <class T>
+__global__ void k_pad_tables(const T* __restrict__ tab, const int64_t* __restrict__ plane_off,
                              const int64_t* __restrict__ pplane_off, const int* __restrict__ support,
-                             int P, int beta, int SP, float2* __restrict__ ptab) {
+                             int P, int beta, int SP, T* __restrict__ ptab) {
     const int p = blockIdx.y;
     if (p >= P) return;
     const int S = support[p], SR = S + 6;
@@ -279,18 +22,18 @@ __global__ void k_pad_tables(const float2* __restrict__ tab, const int64_t* __re
         const int64_t o = e / per;
         const int rem = (int)(e - o * per);
         const int row = rem / SP - 3, col = rem % SP - 7;
-        float2 v = make_float2(0.f, 0.f);
+        T v{};
         if (row >= 0 && row < S && col >= 0 && col < S)
             v = tab[plane_off[p] + o * S * S + (int64_t)row * S + col];
         ptab[pplane_off[p] + e] = v;
     }
 }
 
-__global__ void k_weight_vis(const float2* __restrict__ vis, const float* __restrict__ w,
+__global__ void k_weight_vis(const void* __restrict__ vis, int kind, const float* __restrict__ w,
                              int64_t n, float2* __restrict__ out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = vis[e];
+        const float2 v = load_vis(vis, kind, e);
         const float s = w[e];
         out[e] = make_float2(v.x * s, v.y * s);
     }
@@ -298,11 +41,12 @@ __global__ void k_weight_vis(const float2* __restrict__ vis, const float* __rest
 
 }  // namespace
 
-void launch_weight_vis(const float2* vis, const float* w, int64_t n, float2* out, cudaStream_t s) {
+void launch_weight_vis(const void* vis, int kind, const float* w, int64_t n, float2* out,
+                       cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_weight_vis<<<(unsigned)blocks, 256, 0, s>>>(vis, w, n, out);
+    k_weight_vis<<<(unsigned)blocks, 256, 0, s>>>(vis, kind, w, n, out);
     note_launch();
 }
 
@@ -314,19 +58,26 @@ int padded_stride(int smax) {
 
 int64_t padded_table_elems(int S, int beta, int SP) { return (int64_t)beta * beta * (S + 6) * SP; }
 
-void launch_pad_tables(const float2* tab, const int64_t* plane_off, const int64_t* pplane_off,
-                       const int* support, int P, int beta, int SP, float2* ptab, cudaStream_t s) {
-    k_pad_tables<<<dim3(256, P), 256, 0, s>>>(tab, plane_off, pplane_off, support, P, beta, SP, ptab);
+void launch_pad_tables(const void* tab, int kind, const int64_t* plane_off,
+                       const int64_t* pplane_off, const int* support, int P, int beta, int SP,
+                       void* ptab, cudaStream_t s) {
+    if (kind == GW_C64)
+        k_pad_tables<float2><<<dim3(256, P), 256, 0, s>>>(
+            static_cast<const float2*>(tab), plane_off, pplane_off, support, P, beta, SP,
+            static_cast<float2*>(ptab));
+    else
+        k_pad_tables<uint32_t><<<dim3(256, P), 256, 0, s>>>(
+            static_cast<const uint32_t*>(tab), plane_off, pplane_off, support, P, beta, SP,
+            static_cast<uint32_t*>(ptab));
     note_launch();
 }
 
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s) {
     cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
-    switch (a.npol) {
-        case 1: launch_t<1>(a, num_sms, s); break;
-        case 2: launch_t<2>(a, num_sms, s); break;
-        case 3: launch_t<3>(a, num_sms, s); break;
-        default: launch_t<4>(a, num_sms, s); break;
+    switch (a.table_kind) {
+        case GW_BF16X2: launch_grid_bf16(a, num_sms, s); break;
+        case GW_F16X2: launch_grid_f16(a, num_sms, s); break;
+        default: launch_grid_c64(a, num_sms, s); break;
     }
 }
 

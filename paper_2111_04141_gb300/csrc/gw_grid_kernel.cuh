@@ -1,0 +1,323 @@
+// Gridding kernel: w-projection convolutional gridding onto a complex grid.
+// Included once per table kind by gw_grid_c64.cu, gw_grid_bf16.cu and
+// gw_grid_f16.cu.
+//
+// Computes the Gridding Step of Algorithm convgriddingoversampling
+// (Section 2.4.5) with the w-projection GCF (Section 1.7.1):
+//     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
+//
+// Design (GB300):
+// * A CTA owns one 32 x 32 tile of the grid for a work item (a run of that
+//   tile's bin) and keeps the tile's accumulators in registers, so each grid
+//   point is committed once per work item (vector atomics, red.global).
+//   Two CTAs run per SM.
+// * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
+//   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
+//   polarisation.  Four slots per warp amortise each record's staged
+//   visibility over up to 4 x 32 points.
+// * A ninth, producer warp stages batches of records into shared memory
+//   (double-buffered, handed over with named barriers) and, for every record,
+//   appends it to the list of each compute warp whose block its footprint
+//   meets, together with the range of slots its rows meet.  Compute warps
+//   therefore only see records that touch them.
+// * Kernel values come from zero-padded slices (7 zero columns and 3 zero
+//   rows around each S x S slice, one compile-time row stride per plan), so
+//   lanes outside the footprint read zeros and slot addresses are immediate
+//   offsets; loads for the next record are issued before the multiply-adds
+//   of the current one.
+// * Per tap and polarisation the update is two packed FP32x2 FMAs (Blackwell
+//   FFMA2) on the (re, im) accumulator pair:
+//     acc += (K.re, K.re) (.) A + (K.im, K.im) (.) B
+//   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
+//   kernel (w < 0), precomputed per record.
+// * Storage precision: the table element type is a template parameter
+//   (complex FP32, or bfloat16 / float16 pairs widened to FP32 on load);
+//   visibilities of any kind are widened to FP32 when staged; all
+//   accumulation is FP32.  With an error grid the commit is compensated
+//   (commit_compensated).
+#pragma once
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr int kComputeWarps = 8;
+constexpr int kThreads = (kComputeWarps + 1) * 32;
+constexpr int kBatch = 256;
+constexpr int kBufs = 2;
+
+__device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
+    int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
+    return *reinterpret_cast<gw_index_rec*>(&v);
+}
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Commit with the rounding error kept: the vector atomic returns the value
+// it added to, so the exact error of the (round-to-nearest) sum it stored is
+// recovered with Knuth's TwoSum and accumulated into a second grid.  The
+// compensated value is grid + err (a Kahan-style sum of the commits).
+__device__ __forceinline__ void commit_compensated(float2* g, float2* err, float2 val) {
+    const float2 old = atomicAdd(g, val);
+    float2 e;
+    {
+        const float s = __fadd_rn(old.x, val.x);
+        const float bv = __fsub_rn(s, old.x);
+        const float av = __fsub_rn(s, bv);
+        e.x = __fadd_rn(__fsub_rn(old.x, av), __fsub_rn(val.x, bv));
+    }
+    {
+        const float s = __fadd_rn(old.y, val.y);
+        const float bv = __fsub_rn(s, old.y);
+        const float av = __fsub_rn(s, bv);
+        e.y = __fadd_rn(__fsub_rn(old.y, av), __fsub_rn(val.y, bv));
+    }
+    if (e.x != 0.f || e.y != 0.f) atomicAdd(err, e);
+}
+
+template <int NPOL>
+struct Smem {
+    int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
+    float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
+    uint32_t list[kBufs][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
+    int cnt[kBufs][kComputeWarps];
+    int tile[kBufs];                       // tile of the batch; -1 = end of work
+    int last[kBufs];                       // batch ends its work item
+};
+
+template <int NPOL, int SP, int TK>
+__global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
+    using TE = TabElem<TK>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int side = a.ntiles_u;
+    const int hb = a.beta / 2;
+
+    if (warp == kComputeWarps) {
+        // ------------------------------------------------------------ producer
+        const uint32_t nitems = *a.item_count;
+        int buf = 0, uses = 0;
+        for (;;) {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(a.queue, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            const bool done = it >= nitems;
+            Item item{};
+            if (!done) item = a.items[it];
+            const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
+            for (int b = 0; b < nb_total; ++b) {
+                if (uses >= kBufs) bar_sync(3 + buf, kThreads);  // wait until consumed
+                if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
+                __syncwarp();
+                if (done) {
+                    if (lane == 0) {
+                        sm.tile[buf] = -1;
+                        sm.last[buf] = 1;
+                    }
+                } else {
+                    const int tu0 = (item.tile % side) * kTile;
+                    const int tv0 = (item.tile / side) * kTile;
+                    const int b0 = b * kBatch;
+                    const int nb = min(kBatch, item.len - b0);
+                    for (int r = lane; r < nb; r += 32) {
+                        const uint32_t id = __ldg(a.entries + item.start + b0 + r);
+                        const gw_index_rec rc = load_rec(a.rec, id);
+                        const int S = __ldg(a.support + rc.plane), h = S >> 1;
+                        const int64_t slice = __ldg(a.pplane_off + rc.plane) +
+                                              ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
+                                                  (int64_t)(S + 6) * SP;
+                        // padded index of the tile origin relative to this record
+                        const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
+                        sm.rec[buf][r] = base;
+                        const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
+#pragma unroll
+                        for (int p = 0; p < NPOL; ++p) {
+                            float2 v = load_vis(a.vis, a.vis_kind, (int64_t)id * NPOL + p);
+                            if (a.weight) {
+                                const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
+                                v.x *= w;
+                                v.y *= w;
+                            }
+                            sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
+                                                   : make_float4(v.x, v.y, -v.y, v.x);
+                        }
+                        // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
+                        const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
+                        const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
+                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTile - 1, uhi) >> 3;
+                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTile - 1, vhi) >> 4;
+                        for (int cv = cv0; cv <= cv1; ++cv) {
+                            const int j0 = max(0, vlo - 16 * cv) >> 2;
+                            const int j1 = min(15, vhi - 16 * cv) >> 2;
+                            const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
+                            for (int cu = cu0; cu <= cu1; ++cu) {
+                                const int w = cv * 4 + cu;
+                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
+                                sm.list[buf][w][pos] = e;
+                            }
+                        }
+                    }
+                    if (lane == 0) {
+                        sm.tile[buf] = item.tile;
+                        sm.last[buf] = (b == nb_total - 1);
+                    }
+                }
+                __syncwarp();
+                __threadfence_block();
+                bar_arrive(1 + buf, kThreads);  // batch ready
+                buf ^= 1;
+                ++uses;
+            }
+            if (done) {
+                // complete the consumers' last release of the other buffer so
+                // that every barrier generation is balanced before exit
+                if (uses >= 2) bar_sync(3 + buf, kThreads);
+                break;
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
+    const int lu = lane & 7, lv = lane >> 3;
+    const typename TE::T* __restrict__ tab =
+        reinterpret_cast<const typename TE::T*>(a.ptable) + (bv + lv) * SP + bu + lu;
+    const int N = a.N;
+    float2 acc[4][NPOL];   // (re, im)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int p = 0; p < NPOL; ++p) acc[j][p] = make_float2(0.f, 0.f);
+
+    int buf = 0;
+    for (;;) {
+        bar_sync(1 + buf, kThreads);  // wait for the batch
+        const int tile = sm.tile[buf];
+        if (tile < 0) break;
+        const int last = sm.last[buf];
+        const int n = sm.cnt[buf][warp];
+        const uint32_t* lst = sm.list[buf][warp];
+
+        // software pipeline: kernel values of entry i+1 load during entry i's FMAs
+        float2 Kc0, Kc1, Kc2, Kc3, Kn0 = {}, Kn1 = {}, Kn2 = {}, Kn3 = {};
+        uint32_t ec = 0, en = 0;
+#define GW_LOAD_K(e, K0, K1, K2, K3)                                                  \
+        do {                                                                          \
+            const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
+            const typename TE::T* p_ = tab + sm.rec[buf][r_];                          \
+            K0 = K1 = K2 = K3 = make_float2(0.f, 0.f);                                 \
+            if (0 >= j0_ && 0 <= j1_) K0 = TE::load(p_);                               \
+            if (1 >= j0_ && 1 <= j1_) K1 = TE::load(p_ + 4 * SP);                      \
+            if (2 >= j0_ && 2 <= j1_) K2 = TE::load(p_ + 8 * SP);                      \
+            if (3 >= j0_ && 3 <= j1_) K3 = TE::load(p_ + 12 * SP);                     \
+        } while (0)
+        if (n > 0) {
+            ec = lst[0];
+            GW_LOAD_K(ec, Kc0, Kc1, Kc2, Kc3);
+        }
+        for (int i = 0; i < n; ++i) {
+            if (i + 1 < n) {
+                en = lst[i + 1];
+                GW_LOAD_K(en, Kn0, Kn1, Kn2, Kn3);
+            }
+            const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
+            float4 V[NPOL];
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
+            const float2 Kc[4] = {Kc0, Kc1, Kc2, Kc3};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= j0 && j <= j1) {
+                    // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
+                    const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
+                    const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+#pragma unroll
+                    for (int p = 0; p < NPOL; ++p) {
+                        acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
+                        acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+                    }
+                }
+            }
+            ec = en;
+            Kc0 = Kn0;
+            Kc1 = Kn1;
+            Kc2 = Kn2;
+            Kc3 = Kn3;
+        }
+#undef GW_LOAD_K
+        if (last) {
+            // commit the tile's accumulators of this work item
+            const int u = (tile % a.ntiles_u) * kTile + bu + lu;
+            const int v0 = (tile / a.ntiles_u) * kTile + bv + lv;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int v = v0 + 4 * j;
+#pragma unroll
+                for (int p = 0; p < NPOL; ++p) {
+                    if (u < N && v < N && (acc[j][p].x != 0.f || acc[j][p].y != 0.f)) {
+                        const float2 val = make_float2(acc[j][p].x * a.table_inv,
+                                                       acc[j][p].y * a.table_inv);
+                        const int64_t off = ((int64_t)p * N + v) * N + u;
+                        if (a.grid_err) {
+                            commit_compensated(a.grid + off, a.grid_err + off, val);
+                        } else {
+                            atomicAdd(a.grid + off, val);
+                        }
+                    }
+                    acc[j][p] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        bar_arrive(3 + buf, kThreads);  // buffer free
+        buf ^= 1;
+    }
+}
+
+template <int NPOL, int SP, int TK>
+void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
+    const size_t smem = sizeof(Smem<NPOL>);
+    cudaFuncSetAttribute(k_grid<NPOL, SP, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP, TK>, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    k_grid<NPOL, SP, TK><<<num_sms * per_sm, kThreads, smem, s>>>(a);
+    note_launch();
+}
+
+template <int NPOL, int TK>
+void launch_t(const GridArgs& a, int num_sms, cudaStream_t s) {
+    switch (a.pad_stride) {
+        case 24: launch_sp<NPOL, 24, TK>(a, num_sms, s); break;
+        case 32: launch_sp<NPOL, 32, TK>(a, num_sms, s); break;
+        case 48: launch_sp<NPOL, 48, TK>(a, num_sms, s); break;
+        case 80: launch_sp<NPOL, 80, TK>(a, num_sms, s); break;
+        case 144: launch_sp<NPOL, 144, TK>(a, num_sms, s); break;
+        default: launch_sp<NPOL, 272, TK>(a, num_sms, s); break;
+    }
+}
+
+}  // namespace
+
+// All gridder instantiations for one table kind.
+template <int TK>
+void launch_grid_kind(const GridArgs& a, int num_sms, cudaStream_t s) {
+    switch (a.npol) {
+        case 1: launch_t<1, TK>(a, num_sms, s); break;
+        case 2: launch_t<2, TK>(a, num_sms, s); break;
+        case 3: launch_t<3, TK>(a, num_sms, s); break;
+        default: launch_t<4, TK>(a, num_sms, s); break;
+    }
+}
+
+
+}  // namespace gw

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <algorithm>
 #include <cstdarg>
 #include <cstdint>
@@ -29,6 +31,55 @@ __host__ __device__ inline int plane_support(int p, int P, int smin, int smax) {
 
 __host__ __device__ inline long long floor_div(long long a, long long b) {
     return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// ---- storage types ---------------------------------------------------------
+// Tables and visibilities are stored as complex FP32 (float2) or as pairs of
+// 16-bit floats (re in the low half of a 32-bit word, im in the high half);
+// arithmetic is always FP32.
+__host__ __device__ constexpr int dtype_bytes(int kind) { return kind == GW_C64 ? 8 : 4; }
+
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t u) {
+    // a bfloat16 is the upper half of the float32 with the same bits
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+__device__ __forceinline__ float2 unpack_f16x2(uint32_t u) {
+    __half2 h;
+    memcpy(&h, &u, sizeof u);
+    return __half22float2(h);
+}
+
+// Table element of kind TK and its load (read-only path).
+template <int TK> struct TabElem;
+template <> struct TabElem<GW_C64> {
+    using T = float2;
+    static __device__ __forceinline__ float2 load(const T* p) { return __ldg(p); }
+};
+template <> struct TabElem<GW_BF16X2> {
+    using T = uint32_t;
+    static __device__ __forceinline__ float2 load(const T* p) { return unpack_bf16x2(__ldg(p)); }
+};
+template <> struct TabElem<GW_F16X2> {
+    using T = uint32_t;
+    static __device__ __forceinline__ float2 load(const T* p) { return unpack_f16x2(__ldg(p)); }
+};
+
+// Visibility i of a buffer of kind `kind` (uniform runtime branch).
+__device__ __forceinline__ float2 load_vis(const void* vis, int kind, int64_t i) {
+    if (kind == GW_C64) return __ldg(reinterpret_cast<const float2*>(vis) + i);
+    const uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(vis) + i);
+    return kind == GW_BF16X2 ? unpack_bf16x2(u) : unpack_f16x2(u);
+}
+
+// Store (re, im) as element i of a buffer of kind `kind`, rounded to nearest.
+__device__ __forceinline__ void store_vis(void* vis, int kind, int64_t i, float re, float im) {
+    if (kind == GW_C64) {
+        reinterpret_cast<float2*>(vis)[i] = make_float2(re, im);
+    } else if (kind == GW_BF16X2) {
+        reinterpret_cast<__nv_bfloat162*>(vis)[i] = __floats2bfloat162_rn(re, im);
+    } else {
+        reinterpret_cast<__half2*>(vis)[i] = __floats2half2_rn(re, im);
+    }
 }
 
 struct IndexParams {
@@ -95,18 +146,22 @@ struct TableBuild {
 };
 // Builds float2 tables (device, plane_off[P] complex elements) and the
 // corrector h (device, N doubles and N floats).  Returns the global scale.
-cudaError_t build_tables(const TableBuild& tb, float2* d_table, double* d_h, float* d_hf,
-                         double* h_scale, cudaStream_t s);
+// With d_table16 non-null it also stores every entry, scaled by 2^exp2, as a
+// 16-bit pair of kind kind16 (GW_BF16X2 or GW_F16X2), rounded once from FP64;
+// exp2 is 0 for bfloat16 and, for float16, puts the largest entry (the
+// w = 0, o = 0 centre tap) in [2^14, 2^15) so no entry overflows and small
+// ones stay clear of the subnormal range.
+cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_table16, int kind16,
+                         double* d_h, float* d_hf, double* h_scale, int* h_exp2, cudaStream_t s);
 int quad_nodes(double field, double w, int support, int smin);
 
 // ---- gridding / degridding (gw_grid.cu, gw_degrid.cu) -----------------------
 struct GridArgs {
     const gw_index_rec* rec;
-    const float2* ptable;        // zero-padded tables (launch_pad_tables)
+    const void* ptable;          // zero-padded tables of kind table_kind (launch_pad_tables)
     const int64_t* pplane_off;   // device [P]: padded plane offsets
-    const float2* vis;         // [nvis][npol]
+    const void* vis;           // [nvis][npol] of kind vis_kind
     const float* weight;       // [nvis][npol] or null
-    const float2* table;
     const int64_t* plane_off;  // device [P]
     const int* support;        // device [P]
     const uint32_t* entries;
@@ -114,29 +169,41 @@ struct GridArgs {
     const uint32_t* item_count;  // device scalar: item_off[ntiles]
     uint32_t* queue;             // device scalar: work queue head (zeroed before launch)
     float2* grid;                // [npol][N][N]
+    float2* grid_err;            // [npol][N][N] commit rounding errors, or null (plain commits)
     int N, npol, beta, ntiles_u;  // ntiles_u: gridder tiles along u
     int pad_stride;              // padded row stride (padded_stride(S_max))
+    int vis_kind, table_kind;    // gw_dtype of vis and of the tables
+    float table_inv;             // 2^-exp2: undoes the table storage scale at the commit
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
-// out[e] = vis[e] * w[e] (weights applied before gridding).
-void launch_weight_vis(const float2* vis, const float* w, int64_t n, float2* out, cudaStream_t s);
+// One instantiation set per table kind (gw_grid_c64.cu, gw_grid_bf16.cu, gw_grid_f16.cu).
+void launch_grid_c64(const GridArgs& a, int num_sms, cudaStream_t s);
+void launch_grid_bf16(const GridArgs& a, int num_sms, cudaStream_t s);
+void launch_grid_f16(const GridArgs& a, int num_sms, cudaStream_t s);
+// out[e] = vis[e] * w[e] in FP32 (weights applied before gridding); vis of kind `kind`.
+void launch_weight_vis(const void* vis, int kind, const float* w, int64_t n, float2* out,
+                       cudaStream_t s);
 // Zero-padded slice layout used by the gridder: (S + 6) rows x SP columns,
 // SP = padded_stride(S_max) >= S_max + 14, one of a few compile-time strides.
 int padded_stride(int smax);
 int64_t padded_table_elems(int S, int beta, int SP);
-void launch_pad_tables(const float2* tab, const int64_t* plane_off, const int64_t* pplane_off,
-                       const int* support, int P, int beta, int SP, float2* ptab, cudaStream_t s);
+// tab/ptab hold elements of kind `kind` (8 bytes for GW_C64, else 4).
+void launch_pad_tables(const void* tab, int kind, const int64_t* plane_off,
+                       const int64_t* pplane_off, const int* support, int P, int beta, int SP,
+                       void* ptab, cudaStream_t s);
 
 struct DegridArgs {
     const gw_index_rec* rec;
     const float2* grid;
-    const float2* table;
+    const void* table;          // unpadded tables of kind table_kind
     const int64_t* plane_off;
     const int* support;
     const uint32_t* entries;    // centre-binned ids, offsets[ntiles] of them
     const uint32_t* n_entries;  // device scalar
-    float2* vis_out;            // [nvis][npol]
+    void* vis_out;              // [nvis][npol] of kind vis_kind
     int N, npol, beta;
+    int vis_kind = GW_C64, table_kind = GW_C64;
+    float table_inv = 1.f;      // 2^-exp2: undoes the table storage scale
     // staged kernel only: work items over 16 x 16 centre tiles
     const Item* items = nullptr;
     const uint32_t* item_count = nullptr;
@@ -160,5 +227,7 @@ int static_scratch_max_tiles();
 // ---- correction (gw_correct.cu) -------------------------------------------
 void launch_correct(float2* image, const float* h, int N, int npol, int mode, cudaStream_t s);
 void launch_shift(float2* grid, int N, int npol, cudaStream_t s);
+// grid[i] += err[i]; err[i] = 0 over n complex elements.
+void launch_fold(float2* grid, float2* err, int64_t n, cudaStream_t s);
 
 }  // namespace gw

@@ -16,7 +16,8 @@
 //   K_p(du, dv) = sum_{j, i >= 0} m_j m_i Tw_j Tw_i screen_ji cos(pi du a_i) cos(pi dv a_j)
 // (m = 2 for a node > 0, 1 for the centre node), computed as two dense FP64
 // products.  Entries are sampled at du = t_u - o_u / beta, dv = t_v - o_v / beta,
-// scaled once so that the w = 0, o = 0 slice sums to 1, and stored as float2.
+// scaled once so that the w = 0, o = 0 slice sums to 1, and stored as float2
+// (and, for 16-bit storage, rounded once from FP64 to bfloat16 or float16).
 //
 // psi_0 comes from its Legendre expansion: the smallest eigenpair of the
 // symmetric tridiagonal matrix of the prolate operator in the normalised
@@ -285,12 +286,20 @@ __global__ void k_scale(const double2* __restrict__ Kf0, int F, int fmin, int be
         if (threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *scale = 1.0 / red[0];
+    if (threadIdx.x == 0) {
+        scale[0] = 1.0 / red[0];
+        // the largest |K| of all planes: the w = 0, o = 0 centre tap (the
+        // integrand there is T(a) T(b) >= 0 with no phase)
+        scale[1] = scale[0] * Kf0[(int64_t)(-fmin) * F + (-fmin)].x;
+    }
 }
 
 // table[((ov' * beta + ou') * S + tv') * S + tu'] = scale * Kf[beta tv - ov - fmin][beta tu - ou - fmin]
+// Scaled FP64 entries -> FP32 table and, optionally, a 16-bit table holding
+// round(entry * 2^exp2) (one rounding from FP64, to nearest even).
 __global__ void k_slices(const double2* __restrict__ Kf, int F, int fmin, int beta, int S,
-                         const double* __restrict__ scale, float2* __restrict__ tab) {
+                         const double* __restrict__ scale, float2* __restrict__ tab,
+                         uint32_t* __restrict__ tab16, int kind16, int exp2) {
     const int64_t n = (int64_t)beta * beta * S * S;
     const double sc = *scale;
     const int h = S / 2;
@@ -301,7 +310,22 @@ __global__ void k_slices(const double2* __restrict__ Kf, int F, int fmin, int be
         const int ou = (int)((e / ((int64_t)S * S)) % beta) - beta / 2;
         const int ov = (int)(e / ((int64_t)S * S * beta)) - beta / 2;
         const double2 k = Kf[(int64_t)(beta * tv - ov - fmin) * F + (beta * tu - ou - fmin)];
-        tab[e] = make_float2((float)(sc * k.x), (float)(sc * k.y));
+        const double re = sc * k.x, im = sc * k.y;
+        tab[e] = make_float2((float)re, (float)im);
+        if (tab16) {
+            const double re2 = scalbn(re, exp2), im2 = scalbn(im, exp2);
+            uint16_t lo, hi;
+            if (kind16 == GW_BF16X2) {
+                const __nv_bfloat16 a = __double2bfloat16(re2), b = __double2bfloat16(im2);
+                memcpy(&lo, &a, 2);
+                memcpy(&hi, &b, 2);
+            } else {
+                const __half a = __double2half(re2), b = __double2half(im2);
+                memcpy(&lo, &a, 2);
+                memcpy(&hi, &b, 2);
+            }
+            tab16[e] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
     }
 }
 
@@ -338,8 +362,8 @@ __global__ void k_corrector(int N, int F, int fmin, int beta, int h0,
 
 }  // namespace
 
-cudaError_t build_tables(const TableBuild& tb, float2* d_table, double* d_h, float* d_hf,
-                         double* h_scale, cudaStream_t s) {
+cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_table16, int kind16,
+                         double* d_h, float* d_hf, double* h_scale, int* h_exp2, cudaStream_t s) {
     const double c = M_PI * tb.smin / 2.0;
     const int K = (int)std::ceil(0.5 * c) + 40;
     if (K > kMaxTerms) return cudaErrorInvalidValue;
@@ -354,6 +378,7 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, double* d_h, flo
     double *coef = nullptr, *chi = nullptr, *th = nullptr, *wm = nullptr, *tw = nullptr;
     double *Cm = nullptr, *scale = nullptr, *C1 = nullptr;
     double2 *A = nullptr, *Bt = nullptr, *Kf = nullptr, *Kf0 = nullptr;
+    int exp2 = 0;   // storage exponent of the 16-bit table
     cudaError_t err = cudaSuccess;
 #define GW_TRY(x) do { err = (x); if (err != cudaSuccess) goto done; } while (0)
     GW_TRY(cudaMalloc(&coef, sizeof(double) * K));
@@ -366,7 +391,7 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, double* d_h, flo
     GW_TRY(cudaMalloc(&Bt, sizeof(double2) * (size_t)Fmax * Qhmax));
     GW_TRY(cudaMalloc(&Kf, sizeof(double2) * (size_t)Fmax * Fmax));
     GW_TRY(cudaMalloc(&Kf0, sizeof(double2) * (size_t)(beta * tb.support[0]) * (beta * tb.support[0])));
-    GW_TRY(cudaMalloc(&scale, sizeof(double)));
+    GW_TRY(cudaMalloc(&scale, 2 * sizeof(double)));
     GW_TRY(cudaMalloc(&C1, sizeof(double) * (size_t)beta * tb.support[0]));
 
     k_pswf<<<1, 1, 0, s>>>(c, K, coef, chi);
@@ -397,10 +422,21 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, double* d_h, flo
                 k_c1<<<(F + 127) / 128, 128, 0, s>>>(F, fmin, beta, Qh, th, tw, C1);
                 k_corrector<<<(tb.N + 127) / 128, 128, 0, s>>>(tb.N, F, fmin, beta, h, C1, d_h, d_hf);
                 note_launch(3);
+                if (d_table16 && kind16 == GW_F16X2) {
+                    // storage exponent from the largest entry: peak * 2^exp2 in [2^14, 2^15)
+                    double sp[2];
+                    GW_TRY(cudaMemcpyAsync(sp, scale, sizeof sp, cudaMemcpyDeviceToHost, s));
+                    GW_TRY(cudaStreamSynchronize(s));
+                    int e2 = 0;
+                    std::frexp(sp[1], &e2);      // peak = m 2^e2, m in [0.5, 1)
+                    exp2 = 15 - e2;
+                }
             } else {
                 const int64_t n = (int64_t)beta * beta * S * S;
                 int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-                k_slices<<<blocks, 256, 0, s>>>(Kf, F, fmin, beta, S, scale, d_table + tb.plane_off[p]);
+                k_slices<<<blocks, 256, 0, s>>>(Kf, F, fmin, beta, S, scale, d_table + tb.plane_off[p],
+                                                d_table16 ? d_table16 + tb.plane_off[p] : nullptr,
+                                                kind16, exp2);
                 note_launch();
             }
             GW_TRY(cudaGetLastError());
@@ -408,6 +444,7 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, double* d_h, flo
     }
     GW_TRY(cudaMemcpyAsync(h_scale, scale, sizeof(double), cudaMemcpyDeviceToHost, s));
     GW_TRY(cudaStreamSynchronize(s));
+    *h_exp2 = exp2;
 done:
 #undef GW_TRY
     cudaFree(coef); cudaFree(chi); cudaFree(th); cudaFree(wm); cudaFree(tw); cudaFree(Cm);

@@ -16,6 +16,28 @@ from . import _lib
 from ._lib import GwError, PlanDesc, PlanInfo, check
 
 _DTYPES = {"c64": _lib.GW_C64, "bf16": _lib.GW_BF16X2, "f16": _lib.GW_F16X2}
+# torch storage of each kind: complex64 [..., npol], or 16-bit reals [..., npol, 2]
+_TORCH = {"c64": torch.complex64, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def vis_shape(kind: str, nrow: int, nchan: int, npol: int):
+    return (nrow, nchan, npol) if kind == "c64" else (nrow, nchan, npol, 2)
+
+
+def to_storage(vis: torch.Tensor, kind: str) -> torch.Tensor:
+    """complex64 visibilities -> the storage layout of ``kind`` (rounded to nearest)."""
+    if kind == "c64":
+        return vis.to(torch.complex64).contiguous()
+    return torch.view_as_real(vis.to(torch.complex64)).to(_TORCH[kind]).contiguous()
+
+
+def from_storage(vis: torch.Tensor) -> torch.Tensor:
+    """Visibilities in any storage layout -> complex64 (exact widening)."""
+    if vis.dtype == torch.complex64:
+        return vis
+    if vis.dtype == torch.complex32:
+        return vis.to(torch.complex64)
+    return torch.view_as_complex(vis.float().contiguous())
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -65,6 +87,8 @@ class Plan:
         self.info = info
         self.grid_n = int(grid_n)
         self.npol = int(npol)
+        self.vis_dtype = vis_dtype
+        self.table_dtype = table_dtype
 
     @classmethod
     def from_observation(cls, obs, **kw):
@@ -102,34 +126,70 @@ class Plan:
             raise ValueError("freq must be [nchan]")
         return int(uvw.shape[0]), int(freq.shape[0])
 
+    def _vis_arg(self, vis, name, nrow, nchan):
+        """Validate a visibility tensor in the plan's storage kind."""
+        k = self.vis_dtype
+        if k == "f16" and isinstance(vis, torch.Tensor) and vis.dtype == torch.complex32:
+            vis = torch.view_as_real(vis)
+        _need(vis, name, _TORCH[k], self.device, vis_shape(k, nrow, nchan, self.npol))
+        return vis
+
+    def new_vis(self, nrow: int, nchan: int) -> torch.Tensor:
+        return torch.empty(vis_shape(self.vis_dtype, nrow, nchan, self.npol),
+                           dtype=_TORCH[self.vis_dtype], device=self.device)
+
     def new_grid(self) -> torch.Tensor:
         return torch.zeros((self.npol, self.grid_n, self.grid_n), dtype=torch.complex64,
                            device=self.device)
 
-    def grid(self, uvw, freq, vis, weight=None, out=None, stream=None, return_dropped=False):
-        """Accumulate vis [nrow, nchan, npol] onto out (new zero grid if None)."""
+    def grid(self, uvw, freq, vis, weight=None, out=None, stream=None, return_dropped=False,
+             err=None):
+        """Accumulate vis (plan's storage kind, [nrow, nchan, npol] complex64 or
+        [nrow, nchan, npol, 2] 16-bit) onto out (new zero grid if None).
+
+        With ``err`` (a [npol, N, N] complex64 tensor, zeroed with the grid)
+        commits are compensated (gw_grid_vis_compensated); call ``fold`` once
+        all calls into the grid are done."""
         nrow, nchan = self._coords(uvw, freq)
-        _need(vis, "vis", torch.complex64, self.device, (nrow, nchan, self.npol))
+        vis = self._vis_arg(vis, "vis", nrow, nchan)
         if weight is not None:
             _need(weight, "weight", torch.float32, self.device, (nrow, nchan, self.npol))
         if out is None:
             out = self.new_grid()
-        _need(out, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        gshape = (self.npol, self.grid_n, self.grid_n)
+        _need(out, "grid", torch.complex64, self.device, gshape)
         dropped = ctypes.c_int64(-1)
+        dp = ctypes.byref(dropped) if return_dropped else None
         with torch.cuda.device(self.device):
-            check(self._lib.gw_grid_vis(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(vis),
-                                        _ptr(weight), _ptr(out),
-                                        ctypes.byref(dropped) if return_dropped else None,
-                                        _stream_ptr(stream, self.device)), "gw_grid_vis")
+            if err is None:
+                check(self._lib.gw_grid_vis(self._h, _ptr(uvw), _ptr(freq), nrow, nchan,
+                                            _ptr(vis), _ptr(weight), _ptr(out), dp,
+                                            _stream_ptr(stream, self.device)), "gw_grid_vis")
+            else:
+                _need(err, "err", torch.complex64, self.device, gshape)
+                check(self._lib.gw_grid_vis_compensated(
+                    self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(vis), _ptr(weight),
+                    _ptr(out), _ptr(err), dp, _stream_ptr(stream, self.device)),
+                    "gw_grid_vis_compensated")
         return (out, int(dropped.value)) if return_dropped else out
 
+    def fold(self, grid, err, stream=None):
+        """grid += err; err = 0 (ends a compensated gridding sequence)."""
+        gshape = (self.npol, self.grid_n, self.grid_n)
+        _need(grid, "grid", torch.complex64, self.device, gshape)
+        _need(err, "err", torch.complex64, self.device, gshape)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_fold(self._h, _ptr(grid), _ptr(err),
+                                         _stream_ptr(stream, self.device)), "gw_grid_fold")
+        return grid
+
     def degrid(self, uvw, freq, grid, out=None, stream=None, return_dropped=False):
-        """Visibilities [nrow, nchan, npol] from grid [npol, N, N] (overwrites out)."""
+        """Visibilities (plan's storage kind) from grid [npol, N, N] (overwrites out)."""
         nrow, nchan = self._coords(uvw, freq)
         _need(grid, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
         if out is None:
-            out = torch.empty((nrow, nchan, self.npol), dtype=torch.complex64, device=self.device)
-        _need(out, "vis_out", torch.complex64, self.device, (nrow, nchan, self.npol))
+            out = self.new_vis(nrow, nchan)
+        out = self._vis_arg(out, "vis_out", nrow, nchan)
         dropped = ctypes.c_int64(-1)
         with torch.cuda.device(self.device):
             check(self._lib.gw_degrid_vis(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(grid),
@@ -149,8 +209,8 @@ class Plan:
         nrow, nchan = self._coords(uvw, freq)
         _need(grid, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
         if out is None:
-            out = torch.empty((nrow, nchan, self.npol), dtype=torch.complex64, device=self.device)
-        _need(out, "vis_out", torch.complex64, self.device, (nrow, nchan, self.npol))
+            out = self.new_vis(nrow, nchan)
+        out = self._vis_arg(out, "vis_out", nrow, nchan)
         dropped = ctypes.c_int64(-1)
         with torch.cuda.device(self.device):
             check(self._lib.gw_degrid_vis_static(self._h, _ptr(uvw), _ptr(freq), nrow, nchan,
@@ -208,6 +268,19 @@ class Plan:
                                                 sup.ctypes.data_as(ctypes.c_void_p)),
                   "gw_plan_copy_tables")
         return buf.view(np.complex64), offs, sup
+
+    def stored_tables(self):
+        """The tables as stored: complex64 for c64 plans, else uint16 [..., 2]
+        raw 16-bit pairs (scaled by 2^info.table_exp2), flat like ``tables``."""
+        n = self.info.table_elems
+        if self.table_dtype == "c64":
+            buf = np.empty(n, dtype=np.complex64)
+        else:
+            buf = np.empty((n, 2), dtype=np.uint16)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_copy_stored_tables(self._h, buf.ctypes.data_as(ctypes.c_void_p)),
+                  "gw_plan_copy_stored_tables")
+        return buf
 
     def corrector(self):
         h = np.empty(self.grid_n, dtype=np.float64)
