@@ -39,7 +39,7 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
-# kernel source it was taken on (sha256 of gw_grid.cu); null otherwise.
+# kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
 GRID_TRAFFIC = {"sha256": "79742d88160e95f056fe985c4c2db419d1e05ed026e3677d48e0f8ab1bc9d9b0",
                 "bytes_per_launch": 1.014889e9 + 0.266981e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 16-bit-storage and compensated-commit measurements")
     ap.add_argument("--cpu-sample-rows", type=int, default=0,
                     help="rows of the workload in the CPU-baseline sample (0 = 1/8 of rows)")
     ap.add_argument("--times", type=int, default=256,
@@ -71,7 +73,7 @@ def dist_env():
     return world, rank, local
 
 
-def kernel_sha(name="gw_grid.cu"):
+def kernel_sha(name="gw_grid_kernel.cuh"):
     p = os.path.join(ROOT, "paper_2111_04141_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()
 
@@ -197,6 +199,62 @@ def run_reference(args, world, rank):
     }))
 
 
+def measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
+    """Gridding rate and error of each storage variant on the same batch:
+    bfloat16 / float16 tables + visibilities (FP32 sums), and FP32 with
+    compensated commits.  Errors are relative L2 against the plain FP32 grid
+    of the batch (the FP64-oracle errors are measured by the test suite)."""
+    import torch
+    from paper_2111_04141_gb300.plan import to_storage
+    ref = plan.grid(uvw, freq, vis)
+    nref = torch.linalg.vector_norm(ref)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"error_basis": "relative L2 vs the FP32 grid of the same batch"}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    plan.timing(True)
+    plan.timing()
+    for kind in ("bf16", "f16"):
+        p2 = gw.Plan.from_observation(obs, table_dtype=kind, vis_dtype=kind)
+        v2 = to_storage(vis, kind)
+        g2 = p2.new_grid()
+        p2.timing(True)
+        ms = timed(lambda: p2.grid(uvw, freq, v2, out=g2))
+        tm = p2.timing()
+        one = p2.grid(uvw, freq, v2)
+        taps = tm["taps"] / max(1, tm["grid_calls"])
+        out[kind] = {"value": taps * obs.npol / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "grid_kernel_ms": tm["grid_ms"] / max(1, tm["grid_calls"]),
+                     "rel_l2_vs_fp32": float(torch.linalg.vector_norm(one - ref) / nref),
+                     "vis_bytes": v2.numel() * v2.element_size()}
+        p2.close()
+        del v2, g2, one
+    g, e = plan.new_grid(), plan.new_grid()
+    plan.timing()
+    ms = timed(lambda: plan.grid(uvw, freq, vis, out=g, err=e))
+    tm = plan.timing()
+    plan.timing(False)
+    g.zero_()
+    e.zero_()
+    plan.grid(uvw, freq, vis, out=g, err=e)
+    plan.fold(g, e)
+    taps = tm["taps"] / max(1, tm["grid_calls"])
+    out["c64_compensated"] = {"value": taps * obs.npol / (ms * 1e-3), "unit": UNIT,
+                              "ms_per_step": ms,
+                              "grid_kernel_ms": tm["grid_ms"] / max(1, tm["grid_calls"]),
+                              "rel_l2_vs_fp32": float(torch.linalg.vector_norm(g - ref) / nref)}
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -280,7 +338,7 @@ def main():
                if GRID_TRAFFIC["sha256"] == kernel_sha() else None)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "k_grid (gw_grid.cu)",
+            "kernel": "k_grid (gw_grid_kernel.cuh)",
             "peak_basis": f"FP32 FFMA: {num_sms} SMs x {FFMA_PER_SM_PER_CLK} FFMA/clk x 2 FLOP x "
                           f"{sm_max:.0f} MHz",
             "frac_at_sampled_clock": (achieved / (num_sms * FFMA_PER_SM_PER_CLK * 2 *
@@ -343,6 +401,10 @@ def main():
               "achieved_tflops": dg["taps"] / nd * npol * FLOP_PER_UPDATE /
                                  (dg["degrid_ms"] / max(1, dg["degrid_calls"]) * 1e-3) / 1e12}
 
+    # ---- storage precision and compensated commits on the same batch -------
+    precision = measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
+        if not args.no_precision else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = args.cpu_sample_rows or obs.nrow // 8
@@ -368,7 +430,7 @@ def main():
                        "l2": "inputs larger than L2 (vis 264 MB, grid 512 MB); no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "degrid": degrid,
+            "clocks": clocks, "degrid": degrid, "precision": precision,
         }
         print(json.dumps(line))
     plan.close()
