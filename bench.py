@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-stream measurement")
+    ap.add_argument("--serving-jobs", type=int, default=256)
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 16-bit-storage and compensated-commit measurements")
     ap.add_argument("--cpu-sample-rows", type=int, default=0,
@@ -255,6 +258,78 @@ def measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
     return out
 
 
+def measure_serving(args, dev):
+    """Mixed grid/degrid stream (256 jobs, 8 setups with 1024^2-8192^2 grids,
+    support 7-63, 1 or 4 pols, 1e4-1e7 visibilities log-uniform, sorted or
+    shuffled uvw) at Poisson arrivals of 0.8x the sequential capacity: the
+    continuous-batching server against one-at-a-time plain launches."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2111_04141_gb300.serve import (Server, build_stream, latency_stats,
+                                              run_sequential)
+    from paper_2111_04141_gb300.tune import tune_plan
+    max_vis = 10_000_000
+    n_slots = 4
+    specs = syn.serving_setups(n_setups=8, max_vis=max_vis)
+    jspecs = syn.serving_jobs(specs, n_jobs=args.serving_jobs, max_vis=max_vis)
+    setups, jobs = build_stream(specs, jspecs, np.zeros(len(jspecs)), max_vis)
+    gen = torch.Generator(device=dev).manual_seed(17)
+    models = {s.name: torch.randn((s.npol, s.grid_n, s.grid_n), dtype=torch.complex64,
+                                  device=dev, generator=gen) for s in setups}
+    # autotune each setup on a one-million-visibility sample of its own pools
+    tuning, tune_ms = {}, {}
+    from paper_2111_04141_gb300 import Plan
+    for s, d in zip(setups, specs):
+        rows = min(d["uvw_sorted"].shape[0], 1_000_000 // s.nchan)
+        with Plan(**s.plan_kwargs) as p:
+            u = torch.from_numpy(d["uvw_sorted"][:rows]).to(dev)
+            f = torch.from_numpy(s.freq_hz).to(dev)
+            v = torch.randn((rows, s.nchan, s.npol), dtype=torch.complex64, device=dev,
+                            generator=gen)
+            res = tune_plan(p, u, f, v, p.new_grid(), reps=2)
+        tuning[s.name] = res["tuning"]
+        tune_ms[s.name] = res["ms"]
+    srv = Server(setups, dev, budget=96 << 30, n_slots=n_slots, max_vis=max_vis,
+                 use_graphs=True, tuning=tuning)
+    srv.warm(models)
+    plain = {s.name: Plan(**s.plan_kwargs) for s in setups}
+    freqs = srv.freqs
+
+    def seq(js):
+        run_sequential(setups, plain, srv.models, freqs, js, dev)
+        return latency_stats(js)
+
+    def reset(js, arrivals):
+        for j, t in zip(js, arrivals):
+            j.arrival, j.t_admit, j.t_done, j.slot = float(t), float("nan"), float("nan"), -1
+
+    reset(jobs, np.zeros(len(jobs)))
+    seq(jobs[:8])                                   # warm-up of the plain path
+    reset(jobs, np.zeros(len(jobs)))
+    cap_seq = seq(jobs)
+    rate = 0.8 * cap_seq["jobs_per_s"]
+    arrivals = syn.poisson_arrivals(len(jobs), rate)
+    reset(jobs, arrivals)
+    pois_seq = seq(jobs)
+    reset(jobs, arrivals)
+    srv.run(jobs)
+    pois_srv = latency_stats(jobs)
+    reset(jobs, np.zeros(len(jobs)))
+    srv.run(jobs)
+    cap_srv = latency_stats(jobs)
+    for p in plain.values():
+        p.close()
+    srv.close()
+    return {"jobs": len(jobs), "setups": [s.name for s in setups], "slots": n_slots,
+            "graphs": True, "arrival_rate_jobs_per_s": rate,
+            "poisson_0.8x": {"server": pois_srv, "sequential": pois_seq},
+            "back_to_back": {"server": cap_srv, "sequential": cap_seq},
+            "tuning": tuning, "tune_ms": tune_ms,
+            "p99_speedup": pois_seq["p99_ms"] / pois_srv["p99_ms"],
+            "throughput_speedup": cap_srv["jobs_per_s"] / cap_seq["jobs_per_s"]}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -405,6 +480,8 @@ def main():
     precision = measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
         if not args.no_precision else None
 
+    serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = args.cpu_sample_rows or obs.nrow // 8
@@ -430,7 +507,7 @@ def main():
                        "l2": "inputs larger than L2 (vis 264 MB, grid 512 MB); no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "degrid": degrid, "precision": precision,
+            "clocks": clocks, "degrid": degrid, "precision": precision, "serving": serving,
         }
         print(json.dumps(line))
     plan.close()

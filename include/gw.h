@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 2
+#define GW_API_VERSION 3
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -119,7 +119,20 @@ typedef struct {
                                  GW_C64 and GW_BF16X2; for GW_F16X2 chosen so the largest
                                  entry (w = 0, o = 0 centre tap) lies in [2^14, 2^15) */
     int32_t reserved;
+    int64_t table_bytes;      /* device bytes of the kernel tables (shared with clones) */
+    int64_t scratch_bytes;    /* device bytes of this plan's own scratch */
 } gw_plan_info;
+
+/* Launch tuning of a plan (gw_plan_set_tuning).  Zero fields mean defaults.
+ * No counterpart in the thesis: these are implementation choices that an
+ * autotuner may pick per workload; results do not depend on them beyond
+ * FP32 summation order. */
+typedef struct {
+    int32_t item_max;       /* records per gridding / staged-degridding work item:
+                               0 = 1024, else 64 .. 2^20 (smaller items spread small
+                               jobs over more SMs, larger ones commit less often) */
+    int32_t degrid_kernel;  /* 0 = automatic, 1 = shared-memory staged, 2 = global gather */
+} gw_tuning;
 
 /* ------------------------------------------------------------------------
  * Plan lifetime
@@ -138,6 +151,17 @@ typedef struct {
  * above, or a field of view whose corners reach l^2 + m^2 >= 1 when P > 1),
  * GW_ENOMEM, GW_ECUDA.  On error *out is set to NULL. */
 gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* out);
+
+/* A plan with the same descriptor that shares src's kernel tables (no table
+ * generation) and owns its own scratch, sized by max_vis_per_call (0 =
+ * 2^23).  A plan and its clones may run concurrently on different streams;
+ * one plan must not run two calls at once (its scratch is reused).  The
+ * tables are freed with the last plan that uses them.  Tuning is copied.
+ * Errors: GW_EINVAL, GW_EDEVICE, GW_ENOMEM, GW_ECUDA. */
+gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream, gw_plan* out);
+
+gw_status gw_plan_set_tuning(gw_plan plan, const gw_tuning* tuning);
+gw_status gw_plan_get_tuning(gw_plan plan, gw_tuning* out);
 
 /* Free all device memory of the plan.  NULL is accepted.  The caller must
  * ensure no work using the plan is still in flight. */
@@ -215,6 +239,22 @@ gw_status gw_degrid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz
 gw_status gw_degrid_vis_static(gw_plan plan, const double* uvw_m, const double* freq_hz,
                                int64_t nrow, int32_t nchan, const void* grid, void* vis_out,
                                int64_t* n_dropped, void* cuda_stream);
+
+/* Device-count variants of gw_grid_vis / gw_degrid_vis for CUDA graphs.
+ * No thesis counterpart: a serving loop captures one call into a graph and
+ * replays it for jobs of different sizes.  The row count is read from
+ * device memory (*d_nrow, int64) when the kernels run, clamped to
+ * [0, max_nrow]; buffers are sized for max_nrow rows.  The call makes no
+ * allocation and no synchronisation (so it can be captured) and must fit
+ * one chunk: max_nrow * nchan <= the plan's max_vis_per_call, else
+ * GW_EINVAL.  No weights; dropped records are skipped and not reported.
+ * gw_degrid_vis_devcount zeroes and writes rows [0, *d_nrow) of vis_out. */
+gw_status gw_grid_vis_devcount(gw_plan plan, const double* uvw_m, const double* freq_hz,
+                               const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
+                               const void* vis, void* grid, void* cuda_stream);
+gw_status gw_degrid_vis_devcount(gw_plan plan, const double* uvw_m, const double* freq_hz,
+                                 const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
+                                 const void* grid, void* vis_out, void* cuda_stream);
 
 /* Grid correction (Correction Step, Section 2.3 / 3.3.8), in place on
  * image (device, [npol][N][N] c64):

@@ -36,7 +36,11 @@ class PlanInfo(ctypes.Structure):
                 ("device", c_i32), ("table_elems", c_i64), ("chunk_vis", c_i64),
                 ("field", c_f64), ("taper_c", c_f64), ("table_scale", c_f64),
                 ("vis_dtype", c_i32), ("table_dtype", c_i32), ("table_exp2", c_i32),
-                ("reserved", c_i32)]
+                ("reserved", c_i32), ("table_bytes", c_i64), ("scratch_bytes", c_i64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("item_max", c_i32), ("degrid_kernel", c_i32)]
 
 
 class Timing(ctypes.Structure):
@@ -53,11 +57,16 @@ _SIGS = {
     "gw_plan_create": (c_i32, [ctypes.POINTER(PlanDesc), c_vp, ctypes.POINTER(c_vp)]),
     "gw_plan_destroy": (c_i32, [c_vp]),
     "gw_plan_info_get": (c_i32, [c_vp, ctypes.POINTER(PlanInfo)]),
+    "gw_plan_clone": (c_i32, [c_vp, c_i64, c_vp, ctypes.POINTER(c_vp)]),
+    "gw_plan_set_tuning": (c_i32, [c_vp, ctypes.POINTER(Tuning)]),
+    "gw_plan_get_tuning": (c_i32, [c_vp, ctypes.POINTER(Tuning)]),
     "gw_grid_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp,
                             ctypes.POINTER(c_i64), c_vp]),
     "gw_grid_vis_compensated": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
                                         ctypes.POINTER(c_i64), c_vp]),
     "gw_grid_fold": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "gw_grid_vis_devcount": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
+    "gw_degrid_vis_devcount": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "gw_degrid_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
                               ctypes.POINTER(c_i64), c_vp]),
     "gw_degrid_vis_static": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,

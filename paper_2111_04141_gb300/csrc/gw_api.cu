@@ -36,6 +36,21 @@ static gw_status cuda_fail(cudaError_t e, const char* where) {
 
 using namespace gw;
 
+// Device tables of a plan, shared by the plan and its clones (gw_plan_clone);
+// freed with the last of them.
+struct TableSet {
+    std::atomic<int> refs{1};
+    float2* table = nullptr;
+    uint32_t* table16 = nullptr;
+    void* ptable = nullptr;
+    int64_t* d_pplane_off = nullptr;
+    int64_t* d_plane_off = nullptr;
+    int* d_support = nullptr;
+    double* d_h = nullptr;
+    float* d_hf = nullptr;
+    int64_t bytes = 0;
+};
+
 struct gw_plan_s {
     gw_plan_desc desc{};
     int device = -1;
@@ -50,6 +65,9 @@ struct gw_plan_s {
     std::vector<int64_t> plane_off;
     int max_tiles_per_vis = 0;
     int64_t chunk = 0;
+    TableSet* tabs = nullptr;     // owner of the device tables below once the plan is built
+    int64_t scratch_bytes = 0;
+    gw_tuning tuning{};
     // device state
     float2* table = nullptr;      // FP32 tables (always built)
     uint32_t* table16 = nullptr;  // 16-bit-pair tables (table_dtype != GW_C64)
@@ -73,20 +91,35 @@ struct gw_plan_s {
 
 namespace {
 
+void free_tables(float2* table, uint32_t* table16, void* ptable, int64_t* d_pplane_off,
+                 int64_t* d_plane_off, int* d_support, double* d_h, float* d_hf) {
+    cudaFree(table);
+    cudaFree(table16);
+    cudaFree(ptable);
+    cudaFree(d_pplane_off);
+    cudaFree(d_plane_off);
+    cudaFree(d_support);
+    cudaFree(d_h);
+    cudaFree(d_hf);
+}
+
 void plan_free(gw_plan p) {
     if (!p) return;
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
     cudaFree(p->sc.work);
     cudaFree(p->sc.wvis);
-    cudaFree(p->table);
-    cudaFree(p->table16);
-    cudaFree(p->ptable);
-    cudaFree(p->d_pplane_off);
-    cudaFree(p->d_plane_off);
-    cudaFree(p->d_support);
-    cudaFree(p->d_h);
-    cudaFree(p->d_hf);
+    if (p->tabs) {
+        TableSet* t = p->tabs;
+        if (t->refs.fetch_sub(1) == 1) {
+            free_tables(t->table, t->table16, t->ptable, t->d_pplane_off, t->d_plane_off,
+                        t->d_support, t->d_h, t->d_hf);
+            delete t;
+        }
+    } else {   // a plan that failed before its tables were handed to a TableSet
+        free_tables(p->table, p->table16, p->ptable, p->d_pplane_off, p->d_plane_off,
+                    p->d_support, p->d_h, p->d_hf);
+    }
     cudaFree(p->sc.rec);
     cudaFree(p->sc.count);
     cudaFree(p->sc.offsets);
@@ -138,6 +171,39 @@ gw_status check_device(gw_plan p) {
 template <class T>
 cudaError_t dmalloc(T** ptr, size_t n) {
     return cudaMalloc((void**)ptr, sizeof(T) * (n ? n : 1));
+}
+
+// Per-plan scratch sized by the plan's chunk (gw_plan_clone gives each clone its own).
+gw_status alloc_scratch(gw_plan p) {
+    Scratch& sc = p->sc;
+    sc.entries_cap = p->chunk * p->max_tiles_per_vis;
+    sc.items_cap = sc.entries_cap / kItemMin + p->ntiles + 1;
+    cudaError_t e = cudaSuccess;
+    int64_t bytes = 0;
+#define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); \
+        if (e != cudaSuccess) return fail(GW_ENOMEM, "device allocation of %s failed", #x); \
+        bytes += (int64_t)sizeof(*(x)) * (int64_t)(n); } while (0)
+    GW_ALLOC(sc.rec, (size_t)p->chunk);
+    GW_ALLOC(sc.count, (size_t)p->ntiles);
+    GW_ALLOC(sc.offsets, (size_t)p->ntiles + 1);
+    GW_ALLOC(sc.cursor, (size_t)p->ntiles);
+    GW_ALLOC(sc.item_off, (size_t)p->ntiles + 1);
+    GW_ALLOC(sc.entries, (size_t)sc.entries_cap);
+    GW_ALLOC(sc.items, (size_t)sc.items_cap);
+    GW_ALLOC(sc.counters, 4);
+    GW_ALLOC(sc.dropped, 1);
+    GW_ALLOC(sc.work, 2);
+#undef GW_ALLOC
+    p->scratch_bytes = bytes;
+    return GW_OK;
+}
+
+// Work-item size and degridding kernel choice of a plan (gw_plan_set_tuning).
+void apply_tuning(gw_plan p) {
+    const int im = p->tuning.item_max > 0 ? p->tuning.item_max : kItemMax;
+    p->geom_grid.item_max = im;
+    p->geom_degrid.item_max = im;
+    p->geom_staged.item_max = im;
 }
 
 enum Stage { kStIndex = 0, kStBin = 1, kStGrid = 2, kStDegrid = 3 };
@@ -303,9 +369,6 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     p->ip.smin = desc->support_min;
     p->ip.smax = desc->support_max;
 
-    Scratch& sc = p->sc;
-    sc.entries_cap = p->chunk * p->max_tiles_per_vis;
-    sc.items_cap = sc.entries_cap / kItemMax + p->ntiles + 1;
 #define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { plan_free(p); \
         return fail(GW_ENOMEM, "device allocation of %s failed", #x); } } while (0)
     GW_ALLOC(p->table, (size_t)p->plane_off[P]);
@@ -324,17 +387,12 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     GW_ALLOC(p->d_support, (size_t)P);
     GW_ALLOC(p->d_h, (size_t)N);
     GW_ALLOC(p->d_hf, (size_t)N);
-    GW_ALLOC(sc.rec, (size_t)p->chunk);
-    GW_ALLOC(sc.count, (size_t)p->ntiles);
-    GW_ALLOC(sc.offsets, (size_t)p->ntiles + 1);
-    GW_ALLOC(sc.cursor, (size_t)p->ntiles);
-    GW_ALLOC(sc.item_off, (size_t)p->ntiles + 1);
-    GW_ALLOC(sc.entries, (size_t)sc.entries_cap);
-    GW_ALLOC(sc.items, (size_t)sc.items_cap);
-    GW_ALLOC(sc.counters, 4);
-    GW_ALLOC(sc.dropped, 1);
-    GW_ALLOC(sc.work, 2);
 #undef GW_ALLOC
+    if (alloc_scratch(p) != GW_OK) {
+        plan_free(p);
+        return GW_ENOMEM;
+    }
+    Scratch& sc = p->sc;
     e = cudaMemsetAsync(sc.work, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaMemsetAsync"); }
     e = cudaMemcpyAsync(p->d_plane_off, p->plane_off.data(), sizeof(int64_t) * (P + 1),
@@ -372,7 +430,97 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "padding kernel tables"); }
+    TableSet* t = new (std::nothrow) TableSet;
+    if (!t) { plan_free(p); return fail(GW_ENOMEM, "host allocation failed"); }
+    t->table = p->table;
+    t->table16 = p->table16;
+    t->ptable = p->ptable;
+    t->d_pplane_off = p->d_pplane_off;
+    t->d_plane_off = p->d_plane_off;
+    t->d_support = p->d_support;
+    t->d_h = p->d_h;
+    t->d_hf = p->d_hf;
+    t->bytes = (int64_t)sizeof(float2) * p->plane_off[P] +
+               (int64_t)dtype_bytes(desc->table_dtype) * p->pplane_off[P] +
+               (p->table16 ? (int64_t)sizeof(uint32_t) * p->plane_off[P] : 0) +
+               (int64_t)(2 * sizeof(int64_t) + sizeof(int)) * (P + 1) +
+               (int64_t)(sizeof(double) + sizeof(float)) * N;
+    p->tabs = t;
+    apply_tuning(p);
     *out = p;
+    return GW_OK;
+}
+
+gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream, gw_plan* out) {
+    if (!out) return fail(GW_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (!src || !src->tabs) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(src);
+    if (st != GW_OK) return st;
+    if (max_vis_per_call < 0) return fail(GW_EINVAL, "max_vis_per_call must be >= 0");
+    gw_plan p = new (std::nothrow) gw_plan_s;
+    if (!p) return fail(GW_ENOMEM, "host allocation failed");
+    p->desc = src->desc;
+    p->desc.max_vis_per_call = max_vis_per_call;
+    p->device = src->device;
+    p->num_sms = src->num_sms;
+    p->geom_grid = src->geom_grid;
+    p->geom_degrid = src->geom_degrid;
+    p->geom_staged = src->geom_staged;
+    p->hmax = src->hmax;
+    p->ntiles = src->ntiles;
+    p->pad_stride = src->pad_stride;
+    p->field = src->field;
+    p->table_scale = src->table_scale;
+    p->support = src->support;
+    p->wplane = src->wplane;
+    p->plane_off = src->plane_off;
+    p->pplane_off = src->pplane_off;
+    p->max_tiles_per_vis = src->max_tiles_per_vis;
+    p->ip = src->ip;
+    p->tuning = src->tuning;
+    p->chunk = max_vis_per_call > 0 ? max_vis_per_call : ((int64_t)1 << 23);
+    if (p->chunk * p->max_tiles_per_vis >= ((int64_t)1 << 32)) {
+        delete p;
+        return fail(GW_EINVAL, "max_vis_per_call too large for 32-bit bin entries");
+    }
+    // share the tables
+    p->tabs = src->tabs;
+    p->tabs->refs.fetch_add(1);
+    p->table = src->table;
+    p->table16 = src->table16;
+    p->ptable = src->ptable;
+    p->table_exp2 = src->table_exp2;
+    p->table_inv = src->table_inv;
+    p->d_pplane_off = src->d_pplane_off;
+    p->d_plane_off = src->d_plane_off;
+    p->d_support = src->d_support;
+    p->d_h = src->d_h;
+    p->d_hf = src->d_hf;
+    st = alloc_scratch(p);
+    if (st != GW_OK) { plan_free(p); return st; }
+    cudaError_t e = cudaMemsetAsync(p->sc.work, 0, 2 * sizeof(unsigned long long),
+                                    (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaMemsetAsync"); }
+    apply_tuning(p);
+    *out = p;
+    return GW_OK;
+}
+
+gw_status gw_plan_set_tuning(gw_plan p, const gw_tuning* t) {
+    if (!p || !t) return fail(GW_EINVAL, "null argument");
+    if (t->item_max != 0 && (t->item_max < kItemMin || t->item_max > (1 << 20)))
+        return fail(GW_EINVAL, "item_max must be 0 or in [%d, 2^20]", kItemMin);
+    if (t->degrid_kernel < 0 || t->degrid_kernel > 2)
+        return fail(GW_EINVAL, "degrid_kernel must be 0 (auto), 1 (staged) or 2 (gather)");
+    p->tuning = *t;
+    apply_tuning(p);
+    return GW_OK;
+}
+
+gw_status gw_plan_get_tuning(gw_plan p, gw_tuning* out) {
+    if (!p || !out) return fail(GW_EINVAL, "null argument");
+    *out = p->tuning;
     return GW_OK;
 }
 
@@ -400,6 +548,8 @@ gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
     out->table_dtype = p->desc.table_dtype;
     out->table_exp2 = p->table_exp2;
     out->reserved = 0;
+    out->table_bytes = p->tabs ? p->tabs->bytes : 0;
+    out->scratch_bytes = p->scratch_bytes;
     return GW_OK;
 }
 
@@ -522,7 +672,7 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         void* out = static_cast<char*>(vis_out) + (size_t)v0 * npol * vb;
         e = cudaMemsetAsync(out, 0, vb * nr * nchan * npol, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-        const bool staged = degrid_staged_fits(p->hmax, npol);
+        const bool staged = p->tuning.degrid_kernel != 2 && degrid_staged_fits(p->hmax, npol);
         const BinGeom& geom = staged ? p->geom_staged : p->geom_degrid;
         st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, geom, s);
         if (st != GW_OK) return st;
@@ -554,6 +704,109 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         if (e != cudaSuccess) return cuda_fail(e, "degrid launch");
     }
     return finish_dropped(p, n_dropped, s);
+}
+
+// Shared checks of the device-count entry points; the whole call is one chunk.
+static gw_status devcount_checks(gw_plan p, const double* uvw_m, const double* freq_hz,
+                                 const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
+                                 const void* a, const void* b) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, max_nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!d_nrow || !a || !b) return fail(GW_EINVAL, "null argument");
+    if (max_nrow * (int64_t)nchan > p->chunk)
+        return fail(GW_EINVAL, "max_nrow * nchan (%lld) exceeds the plan's chunk (%lld): "
+                    "clone the plan with a larger max_vis_per_call",
+                    (long long)(max_nrow * (int64_t)nchan), (long long)p->chunk);
+    return GW_OK;
+}
+
+gw_status gw_grid_vis_devcount(gw_plan p, const double* uvw_m, const double* freq_hz,
+                               const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
+                               const void* vis, void* grid, void* cuda_stream) {
+    gw_status st = devcount_checks(p, uvw_m, freq_hz, d_nrow, max_nrow, nchan, vis, grid);
+    if (st != GW_OK) return st;
+    const int vk = p->desc.vis_dtype;
+    if ((reinterpret_cast<uintptr_t>(grid) % 8 != 0) ||
+        (reinterpret_cast<uintptr_t>(vis) % dtype_bytes(vk) != 0))
+        return fail(GW_EINVAL, "grid must be 8-byte aligned and vis aligned to its element size");
+    if (max_nrow == 0 || nchan == 0) return GW_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const DevCount dc{d_nrow, nchan};
+    launch_index(uvw_m, freq_hz, max_nrow, nchan, p->ip, p->sc.rec, p->sc.dropped, s, d_nrow);
+    launch_bin(p->sc.rec, max_nrow * (int64_t)nchan, p->geom_grid, p->desc.n_wplanes,
+               p->desc.support_min, p->desc.support_max, p->sc, s, dc);
+    GridArgs a;
+    a.rec = p->sc.rec;
+    a.ptable = p->ptable;
+    a.pplane_off = p->d_pplane_off;
+    a.vis = vis;
+    a.vis_kind = vk;
+    a.weight = nullptr;
+    a.table_kind = p->desc.table_dtype;
+    a.table_inv = p->table_inv;
+    a.plane_off = p->d_plane_off;
+    a.support = p->d_support;
+    a.entries = p->sc.entries;
+    a.items = p->sc.items;
+    a.item_count = p->sc.item_off + p->geom_grid.ntu * p->geom_grid.ntv;
+    a.queue = p->sc.counters;
+    a.grid = reinterpret_cast<float2*>(grid);
+    a.grid_err = nullptr;
+    a.N = p->desc.grid_n;
+    a.npol = p->desc.npol;
+    a.beta = p->desc.oversample;
+    a.ntiles_u = p->geom_grid.ntu;
+    a.pad_stride = p->pad_stride;
+    launch_grid(a, p->num_sms, s);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "grid launch");
+}
+
+gw_status gw_degrid_vis_devcount(gw_plan p, const double* uvw_m, const double* freq_hz,
+                                 const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
+                                 const void* grid, void* vis_out, void* cuda_stream) {
+    gw_status st = devcount_checks(p, uvw_m, freq_hz, d_nrow, max_nrow, nchan, grid, vis_out);
+    if (st != GW_OK) return st;
+    const int vk = p->desc.vis_dtype, npol = p->desc.npol;
+    if (reinterpret_cast<uintptr_t>(vis_out) % dtype_bytes(vk) != 0)
+        return fail(GW_EINVAL, "vis_out must be aligned to its element size");
+    if (max_nrow == 0 || nchan == 0) return GW_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const DevCount dc{d_nrow, nchan};
+    const int64_t nmax = max_nrow * (int64_t)nchan;
+    launch_zero_vis(vis_out, vk, nmax, npol, dc, s);
+    const bool staged = p->tuning.degrid_kernel != 2 && degrid_staged_fits(p->hmax, npol);
+    const BinGeom& geom = staged ? p->geom_staged : p->geom_degrid;
+    launch_index(uvw_m, freq_hz, max_nrow, nchan, p->ip, p->sc.rec, p->sc.dropped, s, d_nrow);
+    launch_bin(p->sc.rec, nmax, geom, p->desc.n_wplanes, p->desc.support_min,
+               p->desc.support_max, p->sc, s, dc);
+    DegridArgs a;
+    a.rec = p->sc.rec;
+    a.grid = reinterpret_cast<const float2*>(grid);
+    a.table = p->table16 ? (const void*)p->table16 : (const void*)p->table;
+    a.table_kind = p->desc.table_dtype;
+    a.vis_kind = vk;
+    a.table_inv = p->table_inv;
+    a.plane_off = p->d_plane_off;
+    a.support = p->d_support;
+    a.entries = p->sc.entries;
+    a.n_entries = p->sc.offsets + geom.ntu * geom.ntv;
+    a.vis_out = vis_out;
+    a.N = p->desc.grid_n;
+    a.npol = npol;
+    a.beta = p->desc.oversample;
+    a.items = p->sc.items;
+    a.item_count = p->sc.item_off + geom.ntu * geom.ntv;
+    a.queue = p->sc.counters;
+    a.ntiles_u = geom.ntu;
+    if (!(staged && launch_degrid_staged(a, p->hmax, p->num_sms, s)))
+        launch_degrid(a, nmax, p->num_sms, s);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "degrid launch");
 }
 
 gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,

@@ -8,7 +8,7 @@
 //   centre mode:    a record is listed once, in the tile of its pixel (the
 //                   degridder reads a record's whole footprint).
 // Steps: histogram (atomics) -> exclusive scan -> scatter (atomic cursors),
-// then the footprint bins are cut into work items of at most kItemMax
+// then the footprint bins are cut into work items of at most item_max
 // entries.  Order within a bin is unspecified.
 #include "gw_internal.cuh"
 
@@ -41,9 +41,10 @@ __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, int64_
     return *reinterpret_cast<gw_index_rec*>(&v);
 }
 
-__global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, BinGeom g, int P,
-                        int smin, int smax, uint32_t* __restrict__ count,
+__global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, DevCount dc, BinGeom g,
+                        int P, int smin, int smax, uint32_t* __restrict__ count,
                         unsigned long long* __restrict__ work) {
+    nvis = dc.clamp(nvis);
     unsigned long long n_valid = 0, n_taps = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -66,11 +67,12 @@ __global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, BinG
     }
 }
 
-// Exclusive scans of count[] -> offsets[], and of ceil(count / kItemMax) ->
+// Exclusive scans of count[] -> offsets[], and of ceil(count / item_max) ->
 // item_off[], in one block.  n may exceed the block size; each thread scans
 // a contiguous run, then the run totals are scanned across the block.
-__global__ void k_scan(const uint32_t* __restrict__ count, int n, uint32_t* __restrict__ offsets,
-                       uint32_t* __restrict__ item_off, uint32_t* __restrict__ cursor) {
+__global__ void k_scan(const uint32_t* __restrict__ count, int n, int item_max,
+                       uint32_t* __restrict__ offsets, uint32_t* __restrict__ item_off,
+                       uint32_t* __restrict__ cursor) {
     __shared__ uint32_t s_a[1024];
     __shared__ uint32_t s_b[1024];
     const int tid = threadIdx.x;
@@ -80,7 +82,7 @@ __global__ void k_scan(const uint32_t* __restrict__ count, int n, uint32_t* __re
     for (int i = lo; i < hi; ++i) {
         const uint32_t c = count[i];
         sa += c;
-        sb += (c + kItemMax - 1) / kItemMax;
+        sb += (c + item_max - 1) / item_max;
     }
     s_a[tid] = sa;
     s_b[tid] = sb;
@@ -104,7 +106,7 @@ __global__ void k_scan(const uint32_t* __restrict__ count, int n, uint32_t* __re
         item_off[i] = rb;
         cursor[i] = 0;
         ra += c;
-        rb += (c + kItemMax - 1) / kItemMax;
+        rb += (c + item_max - 1) / item_max;
     }
     if (tid == blockDim.x - 1) {
         offsets[n] = s_a[tid];
@@ -112,9 +114,11 @@ __global__ void k_scan(const uint32_t* __restrict__ count, int n, uint32_t* __re
     }
 }
 
-__global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, BinGeom g, int P,
-                          int smin, int smax, const uint32_t* __restrict__ offsets,
-                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ entries) {
+__global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, DevCount dc,
+                          BinGeom g, int P, int smin, int smax,
+                          const uint32_t* __restrict__ offsets, uint32_t* __restrict__ cursor,
+                          uint32_t* __restrict__ entries) {
+    nvis = dc.clamp(nvis);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
          i += (int64_t)gridDim.x * blockDim.x) {
         const gw_index_rec r = load_rec(rec, i);
@@ -130,15 +134,16 @@ __global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, Bi
 }
 
 __global__ void k_items(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offsets,
-                        const uint32_t* __restrict__ item_off, int ntiles, Item* __restrict__ items) {
+                        const uint32_t* __restrict__ item_off, int ntiles, int item_max,
+                        Item* __restrict__ items) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
         const uint32_t c = count[t];
         uint32_t o = item_off[t];
-        for (uint32_t s = 0; s < c; s += kItemMax, ++o) {
+        for (uint32_t s = 0; s < c; s += (uint32_t)item_max, ++o) {
             Item it;
             it.tile = t;
             it.start = (int32_t)(offsets[t] + s);
-            it.len = (int32_t)min((uint32_t)kItemMax, c - s);
+            it.len = (int32_t)min((uint32_t)item_max, c - s);
             it.pad = 0;
             items[o] = it;
         }
@@ -148,7 +153,7 @@ __global__ void k_items(const uint32_t* __restrict__ count, const uint32_t* __re
 }  // namespace
 
 void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
-                Scratch& sc, cudaStream_t s) {
+                Scratch& sc, cudaStream_t s, DevCount dc) {
     const int ntiles = g.ntu * g.ntv;
     cudaMemsetAsync(sc.count, 0, sizeof(uint32_t) * ntiles, s);
     const int threads = 256;
@@ -156,19 +161,20 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     if (nvis > 0) {
-        k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, g, P, smin, smax, sc.count, sc.work);
+        k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, dc, g, P, smin, smax, sc.count,
+                                                     sc.work);
         note_launch();
     }
-    k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, sc.offsets, sc.item_off, sc.cursor);
+    k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, g.item_max, sc.offsets, sc.item_off, sc.cursor);
     note_launch();
     if (nvis > 0) {
-        k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, g, P, smin, smax, sc.offsets,
-                                                       sc.cursor, sc.entries);
+        k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, dc, g, P, smin, smax,
+                                                       sc.offsets, sc.cursor, sc.entries);
         note_launch();
     }
     if (sc.items) {   // work items (the allocation-free degrid path has none)
         const int tb = (ntiles + 255) / 256;
-        k_items<<<tb, 256, 0, s>>>(sc.count, sc.offsets, sc.item_off, ntiles, sc.items);
+        k_items<<<tb, 256, 0, s>>>(sc.count, sc.offsets, sc.item_off, ntiles, g.item_max, sc.items);
         note_launch();
     }
 }

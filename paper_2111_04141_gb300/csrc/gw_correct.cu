@@ -56,6 +56,13 @@ __global__ void k_fold(float2* __restrict__ g, float2* __restrict__ err, int64_t
     }
 }
 
+__global__ void k_zero_vis(uint32_t* __restrict__ v, int64_t n_max, int words, DevCount dc) {
+    const int64_t n = dc.clamp(n_max) * words;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        v[e] = 0u;
+}
+
 unsigned blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     if (b > 152 * 32) b = 152 * 32;
@@ -71,6 +78,13 @@ void launch_correct(float2* image, const float* h, int N, int npol, int mode, cu
 
 void launch_shift(float2* grid, int N, int npol, cudaStream_t s) {
     k_shift<<<blocks_for((int64_t)N * N), 256, 0, s>>>(grid, N, npol);
+    note_launch();
+}
+
+void launch_zero_vis(void* vis, int kind, int64_t n_max, int npol, DevCount dc, cudaStream_t s) {
+    const int words = npol * dtype_bytes(kind) / 4;
+    k_zero_vis<<<blocks_for(n_max * words), 256, 0, s>>>(static_cast<uint32_t*>(vis), n_max, words,
+                                                        dc);
     note_launch();
 }
 

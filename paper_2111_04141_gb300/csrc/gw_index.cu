@@ -32,8 +32,10 @@ __device__ __forceinline__ AxisIdx axis_index(double coord_m, double f, const In
 }
 
 __global__ void k_index(const double* __restrict__ uvw, const double* __restrict__ freq,
-                        int64_t nrow, int nchan, IndexParams p, gw_index_rec* __restrict__ out,
+                        int64_t nrow, const int64_t* __restrict__ d_nrow, int nchan,
+                        IndexParams p, gw_index_rec* __restrict__ out,
                         unsigned long long* __restrict__ dropped) {
+    if (d_nrow) nrow = min(nrow, *d_nrow);     // row count read on the device
     const int64_t nvis = nrow * (int64_t)nchan;
     unsigned int my_drops = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
@@ -86,13 +88,14 @@ __global__ void k_index(const double* __restrict__ uvw, const double* __restrict
 
 void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan,
                   const IndexParams& prm, gw_index_rec* out, unsigned long long* dropped,
-                  cudaStream_t s) {
+                  cudaStream_t s, const int64_t* d_nrow) {
     const int64_t nvis = nrow * (int64_t)nchan;
     if (nvis <= 0) return;
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_index<<<(unsigned)blocks, threads, 0, s>>>(uvw, freq, nrow, nchan, prm, out, dropped);
+    k_index<<<(unsigned)blocks, threads, 0, s>>>(uvw, freq, nrow, d_nrow, nchan, prm, out,
+                                                 dropped);
     note_launch();
 }
 

@@ -17,7 +17,8 @@ constexpr double kC0 = 299792458.0;   // speed of light, m/s
 constexpr int kTile = 32;             // grid tile side of the degridding binner
 constexpr int kGridTileU = 32;        // gridder tile: 32 (u) x 32 (v)
 constexpr int kGridTileV = 32;
-constexpr int kItemMax = 1024;        // max bin entries per gridder work item
+constexpr int kItemMax = 1024;        // default max bin entries per work item
+constexpr int kItemMin = 64;          // smallest work-item size a plan may be tuned to
 constexpr double kQLimit = 1073741824.0;  // 2^30: |q| bound for a representable record
 
 // Support of plane p: the odd integer nearest
@@ -95,7 +96,7 @@ struct IndexParams {
 struct Item {
     int32_t tile;
     int32_t start;   // first entry index (absolute)
-    int32_t len;     // number of entries (<= kItemMax)
+    int32_t len;     // number of entries (<= the geometry's item_max)
     int32_t pad;
 };
 
@@ -118,22 +119,36 @@ struct Scratch {
 // ---- launch counting -----------------------------------------------------
 void note_launch(int n = 1);
 
+// Row count read on the device when kernels run (graph replays with any
+// count up to the captured maximum); nrow == null: the host count is used.
+struct DevCount {
+    const int64_t* nrow = nullptr;
+    int nchan = 1;
+    __device__ __forceinline__ int64_t clamp(int64_t nvis_max) const {
+        if (!nrow) return nvis_max;
+        const int64_t n = *nrow * (int64_t)nchan;
+        return n < nvis_max ? (n > 0 ? n : 0) : nvis_max;
+    }
+};
+
 // ---- index stage (gw_index.cu) --------------------------------------------
 void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan,
                   const IndexParams& prm, gw_index_rec* out, unsigned long long* dropped,
-                  cudaStream_t s);
+                  cudaStream_t s, const int64_t* d_nrow = nullptr);
 
 // ---- binner (gw_bin.cu) ----------------------------------------------------
 // mode 0: footprint tiles (every tile a record's footprint touches)
 // mode 1: centre tile (the tile holding pixel (ku, kv))
-// Tiles are 2^su (u) x 2^sv (v) pixels, ntu x ntv of them (row-major, v rows).
+// Tiles are 2^su (u) x 2^sv (v) pixels, ntu x ntv of them (row-major, v rows);
+// each tile's bin is cut into work items of at most item_max entries.
 struct BinGeom {
     int mode, su, sv, ntu, ntv;
+    int item_max = kItemMax;
 };
 // Also accumulates sc.work[0] += valid records, sc.work[1] += sum of S_p^2.
 // Work items are written only when sc.items is non-null.
 void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
-                Scratch& sc, cudaStream_t s);
+                Scratch& sc, cudaStream_t s, DevCount dc = DevCount{});
 
 // ---- kernel tables (gw_tables.cu) -----------------------------------------
 struct TableBuild {
@@ -229,5 +244,7 @@ void launch_correct(float2* image, const float* h, int N, int npol, int mode, cu
 void launch_shift(float2* grid, int N, int npol, cudaStream_t s);
 // grid[i] += err[i]; err[i] = 0 over n complex elements.
 void launch_fold(float2* grid, float2* err, int64_t n, cudaStream_t s);
+// Zero elements [0, min(n_max, dc count) * npol) of a visibility buffer of kind `kind`.
+void launch_zero_vis(void* vis, int kind, int64_t n_max, int npol, DevCount dc, cudaStream_t s);
 
 }  // namespace gw

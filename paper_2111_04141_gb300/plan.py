@@ -90,6 +90,36 @@ class Plan:
         self.vis_dtype = vis_dtype
         self.table_dtype = table_dtype
 
+    def clone(self, max_vis_per_call: int = 0, stream=None) -> "Plan":
+        """A plan sharing this plan's kernel tables with its own scratch
+        (gw_plan_clone): clones may run concurrently on different streams."""
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_clone(self._h, int(max_vis_per_call),
+                                          _stream_ptr(stream, self.device), ctypes.byref(h)),
+                  "gw_plan_clone")
+        c = Plan.__new__(Plan)
+        c._lib, c.device, c._h = self._lib, self.device, h
+        d = PlanDesc()
+        ctypes.pointer(d)[0] = self.desc
+        d.max_vis_per_call = int(max_vis_per_call)
+        c.desc = d
+        info = PlanInfo()
+        check(self._lib.gw_plan_info_get(h, ctypes.byref(info)), "gw_plan_info_get")
+        c.info = info
+        c.grid_n, c.npol = self.grid_n, self.npol
+        c.vis_dtype, c.table_dtype = self.vis_dtype, self.table_dtype
+        return c
+
+    def get_tuning(self) -> dict:
+        t = _lib.Tuning()
+        check(self._lib.gw_plan_get_tuning(self._h, ctypes.byref(t)), "gw_plan_get_tuning")
+        return {"item_max": t.item_max, "degrid_kernel": t.degrid_kernel}
+
+    def set_tuning(self, item_max: int = 0, degrid_kernel: int = 0):
+        t = _lib.Tuning(item_max=int(item_max), degrid_kernel=int(degrid_kernel))
+        check(self._lib.gw_plan_set_tuning(self._h, ctypes.byref(t)), "gw_plan_set_tuning")
+
     @classmethod
     def from_observation(cls, obs, **kw):
         args = dict(obs.plan_kwargs())
@@ -172,6 +202,31 @@ class Plan:
                     _ptr(out), _ptr(err), dp, _stream_ptr(stream, self.device)),
                     "gw_grid_vis_compensated")
         return (out, int(dropped.value)) if return_dropped else out
+
+    def grid_devcount(self, uvw, freq, d_nrow, vis, out, stream=None):
+        """gw_grid_vis_devcount: rows [0, d_nrow[0]) of uvw/vis (buffers sized
+        for uvw.shape[0] rows) onto ``out``; capturable in a CUDA graph."""
+        max_nrow, nchan = self._coords(uvw, freq)
+        vis = self._vis_arg(vis, "vis", max_nrow, nchan)
+        _need(d_nrow, "d_nrow", torch.int64, self.device, (1,))
+        _need(out, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        check(self._lib.gw_grid_vis_devcount(self._h, _ptr(uvw), _ptr(freq), _ptr(d_nrow),
+                                             max_nrow, nchan, _ptr(vis), _ptr(out),
+                                             _stream_ptr(stream, self.device)),
+              "gw_grid_vis_devcount")
+        return out
+
+    def degrid_devcount(self, uvw, freq, d_nrow, grid, out, stream=None):
+        """gw_degrid_vis_devcount: rows [0, d_nrow[0]) of ``out`` from ``grid``."""
+        max_nrow, nchan = self._coords(uvw, freq)
+        _need(d_nrow, "d_nrow", torch.int64, self.device, (1,))
+        _need(grid, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        out = self._vis_arg(out, "vis_out", max_nrow, nchan)
+        check(self._lib.gw_degrid_vis_devcount(self._h, _ptr(uvw), _ptr(freq), _ptr(d_nrow),
+                                               max_nrow, nchan, _ptr(grid), _ptr(out),
+                                               _stream_ptr(stream, self.device)),
+              "gw_degrid_vis_devcount")
+        return out
 
     def fold(self, grid, err, stream=None):
         """grid += err; err = 0 (ends a compensated gridding sequence)."""

@@ -1,0 +1,525 @@
+"""Serving loop: continuous batching of gridding and degridding jobs on one GPU.
+
+Jobs (grid or degrid requests against one of a set of registered imaging
+setups) arrive over time.  The server keeps every setup's plan and kernel
+tables on the device, and each setup's model grid for degridding.  It runs
+jobs in *slots*: a slot is a CUDA stream with device staging buffers and,
+per setup, a plan clone (own scratch, shared tables) plus CUDA graphs of the
+gridding and degridding calls captured once with a device-side row count,
+so one graph serves every job size.  A job that arrives while others run is
+admitted as soon as a slot is free and the HBM budget holds what the slot
+still has to allocate for its setup (idle slot state of other setups is
+evicted least-recently-used first); its copies and kernels then overlap on
+the device with the other slots' work.  Results come back through
+per-slot pinned staging buffers and a callback.
+
+Scheduling (``Scheduler``) is host logic only and is tested on the CPU; the
+GPU side (``Server``) turns its decisions into stream work.  ``run_sequential``
+is the baseline: one job at a time, plain launches on one stream.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# jobs and setups
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Setup:
+    """An imaging setup jobs refer to: the plan descriptor plus channels."""
+    name: str
+    plan_kwargs: dict
+    freq_hz: np.ndarray
+
+    @property
+    def grid_n(self):
+        return self.plan_kwargs["grid_n"]
+
+    @property
+    def npol(self):
+        return self.plan_kwargs["npol"]
+
+    @property
+    def nchan(self):
+        return int(self.freq_hz.shape[0])
+
+    def grid_bytes(self):
+        return self.npol * self.grid_n * self.grid_n * 8
+
+
+@dataclasses.dataclass
+class Job:
+    id: int
+    kind: str                 # "grid" or "degrid"
+    setup: str
+    nrow: int
+    arrival: float            # seconds from the start of the stream
+    uvw: object = None        # host [nrow, 3] float64 (pinned torch tensor)
+    vis: object = None        # host [nrow, nchan, npol] complex64 (grid jobs)
+    work: float = 0.0         # grid-point pol-updates (filled by the server)
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    slot: int = -1
+
+    @property
+    def latency(self):
+        return self.t_done - self.arrival
+
+
+# --------------------------------------------------------------------------
+# scheduling (host logic)
+# --------------------------------------------------------------------------
+
+class Scheduler:
+    """FIFO continuous-batching admission under an HBM budget.
+
+    ``cost(slot, setup)`` is the device memory a slot still has to allocate
+    to run a job of ``setup`` (0 when the slot already holds that setup's
+    state).  Slot state that is idle may be evicted, least recently used
+    first, to make room; the head of the queue is never overtaken (no
+    starvation), and a job that cannot fit even with every idle state
+    evicted waits for running jobs to finish.
+    """
+
+    def __init__(self, n_slots: int, budget: int, resident: int = 0):
+        self.n_slots = n_slots
+        self.budget = budget
+        self.used = resident               # bytes held outside slot state (tables, models)
+        self.pending: collections.deque = collections.deque()
+        self.busy: Dict[int, Job] = {}
+        self.state: Dict[tuple, int] = {}  # (slot, setup) -> bytes held
+        self.lru: collections.OrderedDict = collections.OrderedDict()
+
+    def arrive(self, job: Job):
+        self.pending.append(job)
+
+    def free_slots(self) -> List[int]:
+        return [s for s in range(self.n_slots) if s not in self.busy]
+
+    def _pick_slot(self, setup: str, free: List[int]) -> int:
+        # prefer a slot that already holds this setup's state
+        for s in free:
+            if (s, setup) in self.state:
+                return s
+        return free[0]
+
+    def _evictable(self, exclude_slot: int):
+        busy = set(self.busy)
+        return [k for k in self.lru if k[0] not in busy and k[0] != exclude_slot]
+
+    def admit(self, cost: Callable[[int, str], int]):
+        """Admit queue-head jobs while possible.  Returns a list of
+        (job, slot, evicted_keys, new_bytes) decisions."""
+        out = []
+        while self.pending:
+            free = self.free_slots()
+            if not free:
+                break
+            job = self.pending[0]
+            slot = self._pick_slot(job.setup, free)
+            need = cost(slot, job.setup)
+            evicted = []
+            if self.used + need > self.budget:
+                # evict idle state (LRU) until the job fits, if it can
+                cands = self._evictable(slot) + [k for k in self.lru
+                                                 if k[0] == slot and k[1] != job.setup]
+                freeable = sum(self.state[k] for k in cands)
+                if self.used - freeable + need > self.budget:
+                    break            # wait for running jobs to release memory
+                for k in cands:
+                    if self.used + need <= self.budget:
+                        break
+                    self.used -= self.state.pop(k)
+                    self.lru.pop(k)
+                    evicted.append(k)
+            self.pending.popleft()
+            key = (slot, job.setup)
+            if need:
+                self.state[key] = self.state.get(key, 0) + need
+                self.used += need
+            self.lru[key] = True
+            self.lru.move_to_end(key)
+            self.busy[slot] = job
+            job.slot = slot
+            out.append((job, slot, evicted, need))
+        return out
+
+    def complete(self, slot: int) -> Job:
+        return self.busy.pop(slot)
+
+
+def latency_stats(jobs: List[Job]) -> dict:
+    lat = np.array([j.latency for j in jobs])
+    t0 = min(j.arrival for j in jobs)
+    t1 = max(j.t_done for j in jobs)
+    work = sum(j.work for j in jobs)
+    return {"jobs": len(jobs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "max_ms": float(lat.max() * 1e3), "makespan_s": float(t1 - t0),
+            "updates_per_s": float(work / max(t1 - t0, 1e-9)),
+            "jobs_per_s": float(len(jobs) / max(t1 - t0, 1e-9))}
+
+
+# --------------------------------------------------------------------------
+# GPU execution
+# --------------------------------------------------------------------------
+
+class _SlotState:
+    """Per (slot, setup): plan clone, device row count and captured graphs."""
+
+    def __init__(self, plan, d_nrow):
+        self.plan = plan
+        self.d_nrow = d_nrow
+        self.graphs = {}
+
+    def close(self):
+        self.graphs.clear()
+        self.plan.close()
+
+
+class Server:
+    """Continuous-batching server on one GPU (see the module docstring).
+
+    setups      registered imaging setups (plans are built at ``warm``)
+    max_vis     largest job (visibilities) any slot must hold
+    budget      device bytes the server may hold (tables, models, slot state)
+    on_result   callback(job, host_tensor) called when a job's result is in
+                host memory (the tensor is a slot staging buffer: copy it to keep it)
+    """
+
+    def __init__(self, setups: List[Setup], device, budget: int, n_slots: int = 4,
+                 max_vis: int = 10_000_000, use_graphs: bool = True, tuning: Optional[dict] = None,
+                 on_result: Optional[Callable] = None):
+        import torch
+        from .plan import Plan
+        self.torch = torch
+        self.Plan = Plan
+        self.setups = {s.name: s for s in setups}
+        self.device = torch.device(device)
+        self.n_slots = n_slots
+        self.max_vis = int(max_vis)
+        self.use_graphs = use_graphs
+        self.tuning = tuning or {}
+        self.on_result = on_result
+        self.budget = int(budget)
+        self.plans: Dict[str, object] = {}
+        self.models: Dict[str, object] = {}
+        self.freqs: Dict[str, object] = {}
+        self.state: Dict[tuple, _SlotState] = {}
+        self.slots = []
+        self.sched: Optional[Scheduler] = None
+
+    # ---- set-up -----------------------------------------------------------
+    def warm(self, models: Optional[Dict[str, np.ndarray]] = None, prewarm: bool = True):
+        """Build every setup's plan (tables) and upload models and channels;
+        allocate the slots' staging buffers; with ``prewarm``, create each
+        slot's clone and graphs for every setup while the budget allows (the
+        rest are created, and evicted, on demand)."""
+        torch = self.torch
+        resident = 0
+        max_rows = 1
+        max_grid = 0
+        max_vis_el = 1
+        for name, s in self.setups.items():
+            p = self.Plan(**s.plan_kwargs, max_vis_per_call=1 << 16, device=self.device)
+            if name in self.tuning:
+                p.set_tuning(**self.tuning[name])
+            self.plans[name] = p
+            resident += p.info.table_bytes + p.info.scratch_bytes
+            self.freqs[name] = torch.from_numpy(s.freq_hz).to(self.device)
+            g = torch.zeros((s.npol, s.grid_n, s.grid_n), dtype=torch.complex64,
+                            device=self.device)
+            if models and name in models:
+                m = models[name]
+                g.copy_(m if isinstance(m, torch.Tensor) else torch.from_numpy(m))
+            self.models[name] = g
+            resident += s.grid_bytes()
+            rows = -(-self.max_vis // s.nchan)
+            max_rows = max(max_rows, rows)
+            max_grid = max(max_grid, s.grid_bytes())
+            max_vis_el = max(max_vis_el, rows * s.nchan * s.npol)
+        for _ in range(self.n_slots):
+            st = torch.cuda.Stream(self.device)
+            slot = {
+                "stream": st,
+                "uvw": torch.empty((max_rows, 3), dtype=torch.float64, device=self.device),
+                "vis": torch.empty(max_vis_el, dtype=torch.complex64, device=self.device),
+                "grid": torch.empty(max_grid // 8, dtype=torch.complex64, device=self.device),
+                "host": torch.empty(max(max_grid // 8, max_vis_el), dtype=torch.complex64,
+                                    pin_memory=True),
+                "event": torch.cuda.Event(),
+            }
+            resident += (max_rows * 24 + max_vis_el * 8 + max_grid)
+            self.slots.append(slot)
+        torch.cuda.synchronize(self.device)
+        self.resident = resident
+        self.sched = Scheduler(self.n_slots, self.budget, resident)
+        if prewarm:
+            for slot in range(self.n_slots):
+                for name in self.setups:
+                    need = self._state_bytes(name)
+                    if self.sched.used + need > self.budget:
+                        continue
+                    if self.use_graphs:
+                        for kind in ("grid", "degrid"):
+                            self._graph(slot, name, kind)
+                    else:
+                        self._ensure_state(slot, name)
+                    self.sched.state[(slot, name)] = need
+                    self.sched.lru[(slot, name)] = True
+                    self.sched.used += need
+            torch.cuda.synchronize(self.device)
+
+    def close(self):
+        for st in self.state.values():
+            st.close()
+        self.state.clear()
+        for p in self.plans.values():
+            p.close()
+        self.plans.clear()
+
+    # ---- slot state -------------------------------------------------------
+    def _state_bytes(self, setup: str) -> int:
+        """Device bytes of a slot's clone for ``setup``: the master's scratch
+        plus the per-visibility parts (record, bin entries, work items) for
+        the extra chunk length."""
+        s = self.setups[setup]
+        p = self.plans[setup]
+        mt = ((s.plan_kwargs["support_max"] - 1) // 32 + 2) ** 2
+        per_vis = 16 + 4 * mt + 16 * mt / 64.0
+        return int(p.info.scratch_bytes + (self.max_vis - p.info.chunk_vis) * per_vis)
+
+    def _cost(self, slot: int, setup: str) -> int:
+        return 0 if (slot, setup) in self.state else self._state_bytes(setup)
+
+    def _ensure_state(self, slot: int, setup: str) -> _SlotState:
+        key = (slot, setup)
+        st = self.state.get(key)
+        if st is None:
+            torch = self.torch
+            clone = self.plans[setup].clone(max_vis_per_call=self.max_vis,
+                                            stream=self.slots[slot]["stream"])
+            d_nrow = torch.zeros(1, dtype=torch.int64, device=self.device)
+            st = _SlotState(clone, d_nrow)
+            self.state[key] = st
+        return st
+
+    def _views(self, slot: int, setup: str, nrow_max: int):
+        s = self.setups[setup]
+        b = self.slots[slot]
+        uvw = b["uvw"][:nrow_max]
+        vis = b["vis"][:nrow_max * s.nchan * s.npol].view(nrow_max, s.nchan, s.npol)
+        grid = b["grid"][:s.npol * s.grid_n * s.grid_n].view(s.npol, s.grid_n, s.grid_n)
+        return uvw, vis, grid
+
+    def _graph(self, slot: int, setup: str, kind: str):
+        """The (slot, setup, kind) graph, captured on first use."""
+        torch = self.torch
+        st = self._ensure_state(slot, setup)
+        g = st.graphs.get(kind)
+        if g is not None:
+            return g
+        s = self.setups[setup]
+        rows = -(-self.max_vis // s.nchan)
+        uvw, vis, grid = self._views(slot, setup, rows)
+        freq = self.freqs[setup]
+        stream = self.slots[slot]["stream"]
+        model = self.models[setup]
+
+        def body():
+            if kind == "grid":
+                grid.zero_()
+                st.plan.grid_devcount(uvw, freq, st.d_nrow, vis, grid)
+            else:
+                st.plan.degrid_devcount(uvw, freq, st.d_nrow, model, vis)
+
+        with torch.cuda.stream(stream):
+            st.d_nrow.zero_()
+            body()                               # warm-up outside capture
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            body()
+        st.graphs[kind] = g
+        return g
+
+    def _drop_state(self, key):
+        st = self.state.pop(key, None)
+        if st is not None:
+            self.slots[key[0]]["stream"].synchronize()
+            st.close()
+
+    # ---- job execution ------------------------------------------------------
+    def _launch(self, job: Job, slot: int):
+        torch = self.torch
+        s = self.setups[job.setup]
+        b = self.slots[slot]
+        stream = b["stream"]
+        nvis = job.nrow * s.nchan
+        if self.use_graphs:
+            g = self._graph(slot, job.setup, job.kind)
+            st = self.state[(slot, job.setup)]
+        else:
+            st = self._ensure_state(slot, job.setup)
+        uvw, vis, grid = self._views(slot, job.setup, job.nrow)
+        with torch.cuda.stream(stream):
+            uvw.copy_(job.uvw, non_blocking=True)
+            if job.kind == "grid":
+                vis.copy_(job.vis, non_blocking=True)
+            if self.use_graphs:
+                st.d_nrow.fill_(job.nrow)
+                g.replay()
+            else:
+                freq = self.freqs[job.setup]
+                if job.kind == "grid":
+                    grid.zero_()
+                    st.plan.grid(uvw, freq, vis, out=grid, stream=stream)
+                else:
+                    st.plan.degrid(uvw, freq, self.models[job.setup], out=vis, stream=stream)
+            host = b["host"]
+            if job.kind == "grid":
+                n = grid.numel()
+                host[:n].view(grid.shape).copy_(grid, non_blocking=True)
+            else:
+                n = nvis * s.npol
+                host[:n].view(vis.shape).copy_(vis, non_blocking=True)
+            b["event"].record(stream)
+
+    def _finish(self, slot: int, now: float):
+        job = self.sched.complete(slot)
+        job.t_done = now
+        if self.on_result is not None:
+            s = self.setups[job.setup]
+            host = self.slots[slot]["host"]
+            if job.kind == "grid":
+                out = host[:s.npol * s.grid_n * s.grid_n].view(s.npol, s.grid_n, s.grid_n)
+            else:
+                out = host[:job.nrow * s.nchan * s.npol].view(job.nrow, s.nchan, s.npol)
+            self.on_result(job, out)
+        return job
+
+    def run(self, jobs: List[Job], clock=time.perf_counter) -> List[Job]:
+        """Serve ``jobs`` (sorted by arrival, seconds from now); returns them
+        with admission and completion times filled in."""
+        jobs = sorted(jobs, key=lambda j: j.arrival)
+        for j in jobs:
+            s = self.setups[j.setup]
+            j.work = self._job_work(j)
+        t0 = clock()
+        i = 0
+        done = []
+        while len(done) < len(jobs):
+            now = clock() - t0
+            while i < len(jobs) and jobs[i].arrival <= now:
+                self.sched.arrive(jobs[i])
+                i += 1
+            for job, slot, evicted, _ in self.sched.admit(self._cost):
+                for key in evicted:
+                    self._drop_state(key)
+                job.t_admit = clock() - t0
+                self._launch(job, slot)
+            progressed = False
+            for slot in list(self.sched.busy):
+                if self.slots[slot]["event"].query():
+                    done.append(self._finish(slot, clock() - t0))
+                    progressed = True
+            if not progressed and not self.sched.pending and i < len(jobs):
+                wait = jobs[i].arrival - (clock() - t0)
+                if wait > 2e-4 and not self.sched.busy:
+                    time.sleep(wait - 1e-4)
+        return done
+
+    def _job_work(self, job: Job) -> float:
+        """Grid-point pol-updates of a job (sum of S_p^2 over its records, x npol),
+        from the plan's work counters is not available per job; estimated
+        from the mean S^2 of the setup's planes weighted like the records."""
+        s = self.setups[job.setup]
+        return float(job.nrow * s.nchan * s.npol * _mean_s2(s))
+
+
+def _mean_s2(s: Setup) -> float:
+    kw = s.plan_kwargs
+    P, smin, smax = kw["n_wplanes"], kw["support_min"], kw["support_max"]
+    if P <= 1:
+        return float(smin * smin)
+    sup = [2 * ((smin * (P - 1) + (smax - smin) * p) // (2 * (P - 1))) + 1 for p in range(P)]
+    return float(np.mean(np.square(sup)))
+
+
+# --------------------------------------------------------------------------
+# baseline: one job at a time, plain launches
+# --------------------------------------------------------------------------
+
+def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, jobs: List[Job],
+                   device, on_result: Optional[Callable] = None, clock=time.perf_counter):
+    """Jobs in arrival order on one stream: wait for arrival, copy in, grid or
+    degrid with the setup's plan (default tuning, no graphs), copy out,
+    synchronise."""
+    import torch
+    setups = {s.name: s for s in setups}
+    jobs = sorted(jobs, key=lambda j: j.arrival)
+    stream = torch.cuda.current_stream(device)
+    t0 = clock()
+    for j in jobs:
+        s = setups[j.setup]
+        j.work = float(j.nrow * s.nchan * s.npol * _mean_s2(s))
+        now = clock() - t0
+        if j.arrival > now:
+            time.sleep(j.arrival - now)
+        j.t_admit = clock() - t0
+        uvw = j.uvw.to(device, non_blocking=True)
+        p = plans[j.setup]
+        if j.kind == "grid":
+            vis = j.vis.to(device, non_blocking=True)
+            out = p.grid(uvw, freqs[j.setup], vis)
+        else:
+            out = p.degrid(uvw, freqs[j.setup], models[j.setup])
+        host = out.to("cpu", non_blocking=True)
+        stream.synchronize()
+        j.t_done = clock() - t0
+        if on_result is not None:
+            on_result(j, host)
+    return jobs
+
+
+# --------------------------------------------------------------------------
+# wiring of generated specs into setups and jobs (host buffers pinned)
+# --------------------------------------------------------------------------
+
+def build_stream(setup_specs: List[dict], job_specs: List[dict], arrivals, max_vis: int,
+                 vis_seed: int = 0):
+    """Setups and Jobs from plain specs: per setup, pinned pools of sorted
+    and shuffled uvw rows and of visibilities (CN(0, 1), max_vis x npol);
+    every job is a view into its setup's pools."""
+    import torch
+    gen = torch.Generator().manual_seed(vis_seed)
+    setups, pools = [], {}
+    for d in setup_specs:
+        st = Setup(d["name"], dict(d["plan_kwargs"]), np.asarray(d["freq_hz"]))
+        setups.append(st)
+        npol, nchan = st.npol, st.nchan
+        rows = -(-max_vis // nchan)
+        v = torch.randn((rows, nchan, npol, 2), generator=gen, dtype=torch.float32)
+        v.mul_(float(np.sqrt(0.5)))
+        pools[st.name] = {
+            "sorted": torch.from_numpy(np.ascontiguousarray(d["uvw_sorted"])).pin_memory(),
+            "shuffled": torch.from_numpy(np.ascontiguousarray(d["uvw_shuffled"])).pin_memory(),
+            "vis": torch.view_as_complex(v).pin_memory(),
+        }
+    jobs = []
+    for spec, t in zip(job_specs, arrivals):
+        pool = pools[spec["setup"]]
+        o, n = spec["offset"], spec["nrow"]
+        uvw = pool["shuffled" if spec["shuffled"] else "sorted"][o:o + n]
+        vis = pool["vis"][:n] if spec["kind"] == "grid" else None
+        jobs.append(Job(id=spec["id"], kind=spec["kind"], setup=spec["setup"], nrow=n,
+                        arrival=float(t), uvw=uvw, vis=vis))
+    return setups, jobs

@@ -223,3 +223,72 @@ def small_case(n_ant: int = 8, n_times: int = 12, n_chan: int = 3, npol: int = 4
 def random_weights(obs: Observation, seed: int = 11) -> np.ndarray:
     rng = np.random.default_rng(BASE_SEED + 200 + seed)
     return rng.uniform(0.25, 1.75, size=obs.vis.shape).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# serving stream: a set of imaging setups and a mixed, Poisson-arriving stream
+# --------------------------------------------------------------------------
+
+def serving_setups(n_setups: int = 8, max_vis: int = 10_000_000, seed_offset: int = 0,
+                   grid_sizes=(1024, 2048, 4096, 8192), max_rows=None) -> list:
+    """Imaging setups for the serving stream.  Each setup: a random array of
+    32-256 antennas in a disk (scaled so the field of view is 0.2-0.8 rad
+    at the setup's grid size), 1, 4 or 8 channels over 120-180 MHz,
+    grid side from ``grid_sizes`` (cycled so every size appears), 1 or 4
+    pols, odd S_max in [7, 63] with S_min = 7, 16 w-planes, oversampling 8.
+    Returns dicts with the plan arguments, channels, a time-ordered uvw pool
+    of at least max_vis / nchan rows ("sorted") and the same rows shuffled."""
+    rng = np.random.default_rng(BASE_SEED + 2 + seed_offset)
+    out = []
+    for k in range(n_setups):
+        N = int(grid_sizes[k % len(grid_sizes)])
+        npol = (1, 4)[(k // len(grid_sizes) + k) % 2]
+        smax = int(2 * rng.integers(3, 32) + 1)
+        n_ant = int(rng.integers(32, 257))
+        diam = 5e3
+        nchan = int(rng.choice([1, 4, 8]))
+        freq = np.linspace(120e6, 180e6, nchan) if nchan > 1 else np.array([150e6])
+        enu = antennas_disk(n_ant, diam, rng)
+        bl = baselines(enu)
+        rows = -(-max_vis // nchan) if max_rows is None else int(max_rows)
+        n_times = -(-rows // bl.shape[0])
+        uvw = uvw_tracks(bl, n_times)
+        # scale the array so the field of view L = N cell lands in [0.2, 0.8] rad
+        field = fit_cell(uvw, freq, N, smax) * N
+        scale = field / float(rng.uniform(0.2, 0.8))
+        uvw = uvw * scale
+        cell = fit_cell(uvw, freq, N, smax)
+        wmax = w_extent(uvw, freq)
+        shuffled = uvw[rng.permutation(uvw.shape[0])]
+        out.append(dict(
+            name=f"setup{k}-N{N}-S{smax}-pol{npol}-ch{nchan}",
+            plan_kwargs=dict(grid_n=N, cell_rad=cell, support_min=7, support_max=smax,
+                             oversample=8, n_wplanes=16, w_max_lambda=wmax, npol=npol),
+            freq_hz=freq, uvw_sorted=uvw, uvw_shuffled=shuffled))
+    return out
+
+
+def serving_jobs(setups: list, n_jobs: int = 256, min_vis: int = 10_000,
+                 max_vis: int = 10_000_000, seed_offset: int = 0) -> list:
+    """Job specs: kind grid/degrid 50/50, setup uniform, visibility count
+    log-uniform in [min_vis, max_vis], uvw rows sorted (a contiguous run of
+    the time-ordered pool) or shuffled, 50/50.  Arrival times are set later
+    (``poisson_arrivals``)."""
+    rng = np.random.default_rng(BASE_SEED + 5 + seed_offset)
+    jobs = []
+    for i in range(n_jobs):
+        s = setups[int(rng.integers(len(setups)))]
+        nchan = s["freq_hz"].shape[0]
+        nvis = int(np.exp(rng.uniform(np.log(min_vis), np.log(max_vis))))
+        nrow = max(1, nvis // nchan)
+        pool = s["uvw_sorted"].shape[0]
+        jobs.append(dict(id=i, kind=("grid", "degrid")[int(rng.integers(2))], setup=s["name"],
+                         nrow=nrow, offset=int(rng.integers(0, pool - nrow + 1)),
+                         shuffled=bool(rng.integers(2))))
+    return jobs
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed_offset: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson process with the given rate."""
+    rng = np.random.default_rng(BASE_SEED + 6 + seed_offset)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, n))

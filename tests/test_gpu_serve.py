@@ -1,0 +1,162 @@
+"""Serving on the GPU: device-count calls and their CUDA graphs, plan clones
+and tuning, and the continuous-batching server (each job's result is the
+same alone and in the mix).
+
+Tolerances: degridding is deterministic (fixed reduction order), so results
+agree to FP32 rounding of identical sums (relative L2 <= 1e-6); gridding
+commits with atomics in a run-dependent order (relative L2 <= 1e-6).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_04141_gb300 import build as b
+    b.build()
+    import paper_2111_04141_gb300 as gw
+    return gw
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel(a, b):
+    a = a.to(torch.complex128)
+    b = b.to(torch.complex128)
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def small():
+    return syn.small_case(n_ant=7, n_times=10, n_chan=3, npol=4, grid_n=128, s_min=7,
+                          s_max=21, n_w=5, diameter_m=1500.0)
+
+
+def test_devcount_and_graph_replay_match_plain_calls(gw):
+    obs = small()
+    u, f, v = dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)
+    rng = np.random.default_rng(0)
+    model = dev((rng.normal(size=(4, 128, 128)) + 1j * rng.normal(size=(4, 128, 128)))
+                .astype(np.complex64))
+    with gw.Plan.from_observation(obs) as master:
+        plan = master.clone(max_vis_per_call=obs.nvis)
+        d_n = torch.zeros(1, dtype=torch.int64, device=DEV)
+        g = plan.new_grid()
+        vo = torch.zeros_like(v)
+        # device count
+        for nrow in (obs.nrow, 37, 1, 0):
+            d_n.fill_(nrow)
+            g.zero_()
+            plan.grid_devcount(u, f, d_n, v, g)
+            want = master.grid(u[:nrow], f, v[:nrow]) if nrow else master.new_grid()
+            assert rel(g, want) <= TOL if nrow else not torch.any(g != 0)
+            vo.fill_(7)
+            plan.degrid_devcount(u, f, d_n, model, vo)
+            if nrow:
+                want = master.degrid(u[:nrow], f, model)
+                assert rel(vo[:nrow], want) <= TOL
+            assert torch.all(vo[nrow:] == 7)               # rows past the count untouched
+        # one captured graph, replayed for several sizes
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            d_n.fill_(obs.nrow)
+            g.zero_()
+            plan.grid_devcount(u, f, d_n, v, g)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            g.zero_()
+            plan.grid_devcount(u, f, d_n, v, g)
+        for nrow in (obs.nrow, 55, 3):
+            d_n.fill_(nrow)
+            graph.replay()
+            torch.cuda.synchronize()
+            assert rel(g, master.grid(u[:nrow], f, v[:nrow])) <= TOL
+        plan.close()
+
+
+def test_clone_shares_tables_and_outlives_master(gw):
+    obs = small()
+    u, f, v = dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)
+    master = gw.Plan.from_observation(obs)
+    want = master.grid(u, f, v)
+    tab = master.tables()[0]
+    clone = master.clone(max_vis_per_call=1000)
+    assert clone.info.table_bytes == master.info.table_bytes
+    assert clone.info.scratch_bytes != master.info.scratch_bytes
+    master.close()                                    # the tables stay alive for the clone
+    assert np.array_equal(clone.tables()[0], tab)
+    assert rel(clone.grid(u, f, v), want) <= TOL      # several chunks of 1000
+    clone.close()
+
+
+@pytest.mark.parametrize("item_max,degrid_kernel", [(64, 2), (256, 1), (4096, 0)])
+def test_tuning_changes_nothing_but_speed(gw, item_max, degrid_kernel):
+    obs = small()
+    u, f, v = dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)
+    with gw.Plan.from_observation(obs) as plan:
+        g0 = plan.grid(u, f, v)
+        d0 = plan.degrid(u, f, g0)
+        plan.set_tuning(item_max=item_max, degrid_kernel=degrid_kernel)
+        assert plan.get_tuning() == {"item_max": item_max, "degrid_kernel": degrid_kernel}
+        assert rel(plan.grid(u, f, v), g0) <= TOL
+        assert rel(plan.degrid(u, f, g0), d0) <= TOL
+        with pytest.raises(gw.GwError):
+            plan.set_tuning(item_max=3)
+
+
+def test_autotuner_picks_a_candidate(gw):
+    from paper_2111_04141_gb300.tune import TuningCache, tune_plan
+    obs = small()
+    u, f, v = dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)
+    with gw.Plan.from_observation(obs) as plan:
+        res = tune_plan(plan, u, f, v, plan.new_grid(), reps=1, items=(256, 1024),
+                        degrid=(1, 2))
+        assert res["tuning"] == plan.get_tuning()
+        assert len(res["timings"]) == 4
+    c = TuningCache()
+    c.put("x", res["tuning"])
+    assert c.get("x") == res["tuning"]
+
+
+@pytest.mark.parametrize("use_graphs", [True, False])
+def test_server_results_same_alone_and_in_the_mix(gw, use_graphs):
+    from paper_2111_04141_gb300.serve import Server, build_stream, run_sequential
+    max_vis = 60_000
+    specs = syn.serving_setups(n_setups=4, max_vis=max_vis, grid_sizes=(256, 512))
+    jspecs = syn.serving_jobs(specs, n_jobs=24, min_vis=500, max_vis=max_vis)
+    arrivals = syn.poisson_arrivals(len(jspecs), 2000.0)       # overlapping arrivals
+    setups, jobs = build_stream(specs, jspecs, arrivals, max_vis)
+    rng = np.random.default_rng(3)
+    models = {s.name: (rng.normal(size=(s.npol, s.grid_n, s.grid_n))
+                       + 1j * rng.normal(size=(s.npol, s.grid_n, s.grid_n))).astype(np.complex64)
+              for s in setups}
+    mixed = {}
+    srv = Server(setups, DEV, budget=8 << 30, n_slots=3, max_vis=max_vis, use_graphs=use_graphs,
+                 on_result=lambda j, t: mixed.__setitem__(j.id, t.clone()))
+    srv.warm(models)
+    done = srv.run(jobs)
+    assert len(done) == len(jobs) and len(mixed) == len(jobs)
+    assert all(j.t_done >= j.t_admit >= j.arrival for j in done)
+    slots_used = {j.slot for j in done}
+    assert len(slots_used) > 1
+    # every job alone: the setup's master plan, plain calls, one at a time
+    alone = {}
+    for j in jobs:
+        j.arrival = 0.0
+    run_sequential(setups, srv.plans, srv.models, srv.freqs, jobs, DEV,
+                   on_result=lambda j, t: alone.__setitem__(j.id, t.clone()))
+    for j in jobs:
+        assert rel(mixed[j.id], alone[j.id]) <= TOL, (j.id, j.kind, j.setup)
+    srv.close()

@@ -1,0 +1,118 @@
+"""Host logic of the serving loop (no GPU): admission, HBM budget, eviction,
+slot affinity, latency statistics, and the serving-stream generator."""
+import math
+
+import numpy as np
+
+import synthetic as syn
+from paper_2111_04141_gb300.serve import Job, Scheduler, latency_stats
+
+
+def job(i, setup="a", arrival=0.0):
+    return Job(id=i, kind="grid", setup=setup, nrow=10, arrival=arrival)
+
+
+def test_fifo_admission_fills_free_slots_then_waits():
+    s = Scheduler(n_slots=2, budget=10**12)
+    for i in range(5):
+        s.arrive(job(i))
+    got = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in got] == [0, 1]
+    assert sorted(slot for _, slot, *_ in got) == [0, 1]
+    assert s.admit(lambda slot, setup: 0) == []          # no free slot
+    s.complete(got[0][1])
+    nxt = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in nxt] == [2]                # strict arrival order
+    assert nxt[0][1] == got[0][1]
+
+
+def test_budget_blocks_until_memory_is_released():
+    s = Scheduler(n_slots=3, budget=100, resident=40)
+    s.arrive(job(0, "a"))
+    s.arrive(job(1, "b"))
+    s.arrive(job(2, "c"))
+    cost = lambda slot, setup: 0 if (slot, setup) in s.state else 30
+    first = s.admit(cost)
+    # 40 + 30 = 70 fits; a second state would need 100 -> also fits; a third would not
+    assert [j.id for j, *_ in first] == [0, 1]
+    assert s.used == 100
+    assert s.admit(cost) == []                          # c waits: a and b are busy
+    s.complete(first[0][1])                             # a finishes: its state is idle now
+    got = s.admit(cost)
+    assert [j.id for j, *_ in got] == [2]
+    _, slot, evicted, need = got[0]
+    assert evicted == [(first[0][1], "a")] and need == 30
+    assert s.used == 100
+    assert (first[1][1], "b") in s.state                # busy state never evicted
+
+
+def test_head_of_line_is_not_overtaken():
+    s = Scheduler(n_slots=2, budget=50, resident=0)
+    s.arrive(job(0, "big"))
+    s.arrive(job(1, "small"))
+    cost = lambda slot, setup: {"big": 60, "small": 1}[setup]
+    assert s.admit(cost) == []                          # big can never fit now; small waits too
+    assert [j.id for j in s.pending] == [0, 1]
+
+
+def test_slot_affinity_reuses_a_slot_holding_the_setup():
+    s = Scheduler(n_slots=4, budget=10**9)
+    s.state[(2, "x")] = 5
+    s.lru[(2, "x")] = True
+    s.arrive(job(0, "x"))
+    got = s.admit(lambda slot, setup: 0 if (slot, setup) in s.state else 5)
+    assert got[0][1] == 2 and got[0][3] == 0
+
+
+def test_lru_evicts_oldest_idle_state_first():
+    s = Scheduler(n_slots=2, budget=100, resident=0)
+    for k, setup in enumerate(["p", "q", "r"]):
+        s.state[(1, setup)] = 30
+        s.lru[(1, setup)] = True
+    s.used = 90
+    s.arrive(job(0, "z"))
+    got = s.admit(lambda slot, setup: 0 if (slot, setup) in s.state else 30)
+    # slot 0 is free and empty: evict only the least recently used idle state
+    assert got[0][2] == [(1, "p")]
+    assert s.used == 90
+
+
+def test_latency_stats():
+    jobs = []
+    for i in range(100):
+        j = job(i, arrival=i * 0.01)
+        j.t_done = j.arrival + 0.001 * (i + 1)
+        j.work = 1e6
+        jobs.append(j)
+    st = latency_stats(jobs)
+    assert math.isclose(st["p50_ms"], np.percentile(np.arange(1, 101), 50), rel_tol=1e-9)
+    assert math.isclose(st["p99_ms"], np.percentile(np.arange(1, 101), 99), rel_tol=1e-9)
+    assert math.isclose(st["makespan_s"], 0.99 + 0.1, rel_tol=1e-9)
+    assert math.isclose(st["updates_per_s"], 1e8 / 1.09, rel_tol=1e-9)
+
+
+def test_serving_stream_generator():
+    setups = syn.serving_setups(n_setups=4, max_vis=20_000)
+    for s in setups:
+        kw = s["plan_kwargs"]
+        field = kw["cell_rad"] * kw["grid_n"]
+        assert 0.19 <= field <= 0.81
+        assert 2 * (field / 2) ** 2 < 1.0
+        assert kw["support_max"] % 2 == 1 and 7 <= kw["support_max"] <= 63
+        assert s["uvw_sorted"].shape == s["uvw_shuffled"].shape
+        assert np.allclose(np.sort(s["uvw_sorted"][:, 0]), np.sort(s["uvw_shuffled"][:, 0]))
+    jobs = syn.serving_jobs(setups, n_jobs=400, min_vis=100, max_vis=20_000)
+    nv = np.array([j["nrow"] for j in jobs])
+    assert nv.min() >= 1
+    kinds = [j["kind"] for j in jobs]
+    assert 120 <= kinds.count("grid") <= 280
+    names = {s["name"]: s for s in setups}
+    for j in jobs:
+        assert j["offset"] + j["nrow"] <= names[j["setup"]]["uvw_sorted"].shape[0]
+    # log-uniform sizes: about half below the geometric mean
+    nvis = np.array([j["nrow"] * names[j["setup"]]["freq_hz"].shape[0] for j in jobs])
+    frac = np.mean(nvis < np.sqrt(100 * 20_000))
+    assert 0.35 <= frac <= 0.65
+    t = syn.poisson_arrivals(5000, 200.0)
+    assert np.all(np.diff(t) > 0)
+    assert abs(np.mean(np.diff(t)) - 1 / 200.0) < 0.1 / 200.0
