@@ -46,7 +46,6 @@ namespace {
 constexpr int kComputeWarps = 8;
 constexpr int kThreads = (kComputeWarps + 1) * 32;
 constexpr int kBatch = 256;
-constexpr int kBufs = 2;
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
     int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
@@ -82,21 +81,23 @@ __device__ __forceinline__ void commit_compensated(float2* g, float2* err, float
     if (e.x != 0.f || e.y != 0.f) atomicAdd(err, e);
 }
 
-template <int NPOL>
+template <int NPOL, int B>
 struct Smem {
-    int rec[kBufs][kBatch];                // padded-table index of the tile origin for the record
-    float4 v[kBufs][kBatch][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation
-    uint32_t list[kBufs][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
-    int cnt[kBufs][kComputeWarps];
-    int tile[kBufs];                       // tile of the batch; -1 = end of work
-    int last[kBufs];                       // batch ends its work item
+    int rec[B][kBatch];                    // padded-table index of the tile origin for the record
+    float4 v[B][kBatch][NPOL];             // (A.re, A.im, B.re, B.im) per polarisation
+    uint32_t list[B][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
+    int cnt[B][kComputeWarps];
+    int tile[B];                           // tile of the batch; -1 = end of work
+    int last[B];                           // batch ends its work item
 };
 
-template <int NPOL, int SP, int TK>
+// Named barriers: FULL(b) = 1 + b (batch b staged), EMPTY(b) = 1 + B + b (consumed).
+template <int NPOL, int SP, int TK, int D, int B>
 __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
     using TE = TabElem<TK>;
+    constexpr int kBufs = B;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<NPOL>& sm = *reinterpret_cast<Smem<NPOL>*>(smem_raw);
+    Smem<NPOL, B>& sm = *reinterpret_cast<Smem<NPOL, B>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int side = a.ntiles_u;
     const int hb = a.beta / 2;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
             if (!done) item = a.items[it];
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
-                if (uses >= kBufs) bar_sync(3 + buf, kThreads);  // wait until consumed
+                if (uses >= kBufs) bar_sync(1 + kBufs + buf, kThreads);  // wait until consumed
                 if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
                 __syncwarp();
                 if (done) {
@@ -173,13 +174,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                 __syncwarp();
                 __threadfence_block();
                 bar_arrive(1 + buf, kThreads);  // batch ready
-                buf ^= 1;
+                buf = (buf + 1 == kBufs) ? 0 : buf + 1;
                 ++uses;
             }
             if (done) {
-                // complete the consumers' last release of the other buffer so
-                // that every barrier generation is balanced before exit
-                if (uses >= 2) bar_sync(3 + buf, kThreads);
+                // complete the consumers' releases of the batches whose
+                // buffers were not reused, so every barrier generation is
+                // balanced before exit (the end-of-work batch is not released)
+                for (int q = max(0, uses - kBufs); q <= uses - 2; ++q)
+                    bar_sync(1 + kBufs + q % kBufs, kThreads);
                 break;
             }
         }
@@ -207,51 +210,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
         const int n = sm.cnt[buf][warp];
         const uint32_t* lst = sm.list[buf][warp];
 
-        // software pipeline: kernel values of entry i+1 load during entry i's FMAs
-        float2 Kc0, Kc1, Kc2, Kc3, Kn0 = {}, Kn1 = {}, Kn2 = {}, Kn3 = {};
-        uint32_t ec = 0, en = 0;
-#define GW_LOAD_K(e, K0, K1, K2, K3)                                                  \
+        // software pipeline: kernel values of entries i+1 .. i+D-1 are in
+        // flight while entry i's FMAs run (a ring of D register sets)
+#define GW_LOAD_K(e, K)                                                                \
         do {                                                                          \
             const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
             const typename TE::T* p_ = tab + sm.rec[buf][r_];                          \
-            K0 = K1 = K2 = K3 = make_float2(0.f, 0.f);                                 \
-            if (0 >= j0_ && 0 <= j1_) K0 = TE::load(p_);                               \
-            if (1 >= j0_ && 1 <= j1_) K1 = TE::load(p_ + 4 * SP);                      \
-            if (2 >= j0_ && 2 <= j1_) K2 = TE::load(p_ + 8 * SP);                      \
-            if (3 >= j0_ && 3 <= j1_) K3 = TE::load(p_ + 12 * SP);                     \
+            K[0] = K[1] = K[2] = K[3] = make_float2(0.f, 0.f);                         \
+            if (0 >= j0_ && 0 <= j1_) K[0] = TE::load(p_);                             \
+            if (1 >= j0_ && 1 <= j1_) K[1] = TE::load(p_ + 4 * SP);                    \
+            if (2 >= j0_ && 2 <= j1_) K[2] = TE::load(p_ + 8 * SP);                    \
+            if (3 >= j0_ && 3 <= j1_) K[3] = TE::load(p_ + 12 * SP);                   \
         } while (0)
-        if (n > 0) {
-            ec = lst[0];
-            GW_LOAD_K(ec, Kc0, Kc1, Kc2, Kc3);
-        }
-        for (int i = 0; i < n; ++i) {
-            if (i + 1 < n) {
-                en = lst[i + 1];
-                GW_LOAD_K(en, Kn0, Kn1, Kn2, Kn3);
+        float2 Kr[D][4];
+        uint32_t er[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            er[d] = 0;
+            Kr[d][0] = Kr[d][1] = Kr[d][2] = Kr[d][3] = make_float2(0.f, 0.f);
+            if (d < n) {
+                er[d] = lst[d];
+                GW_LOAD_K(er[d], Kr[d]);
             }
-            const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
-            float4 V[NPOL];
+        }
+        for (int i = 0; i < n; i += D) {
 #pragma unroll
-            for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
-            const float2 Kc[4] = {Kc0, Kc1, Kc2, Kc3};
+            for (int d = 0; d < D; ++d) {
+                if (i + d < n) {
+                    const uint32_t ec = er[d];
+                    const float2 Kc[4] = {Kr[d][0], Kr[d][1], Kr[d][2], Kr[d][3]};
+                    if (i + d + D < n) {
+                        er[d] = lst[i + d + D];
+                        GW_LOAD_K(er[d], Kr[d]);
+                    }
+                    const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
+                    float4 V[NPOL];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j >= j0 && j <= j1) {
-                    // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
-                    const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
-                    const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+                    for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
 #pragma unroll
-                    for (int p = 0; p < NPOL; ++p) {
-                        acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
-                        acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+                    for (int j = 0; j < 4; ++j) {
+                        if (j >= j0 && j <= j1) {
+                            // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
+                            const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
+                            const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+#pragma unroll
+                            for (int p = 0; p < NPOL; ++p) {
+                                acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y),
+                                                       acc[j][p]);
+                                acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w),
+                                                       acc[j][p]);
+                            }
+                        }
                     }
                 }
             }
-            ec = en;
-            Kc0 = Kn0;
-            Kc1 = Kn1;
-            Kc2 = Kn2;
-            Kc3 = Kn3;
         }
 #undef GW_LOAD_K
         if (last) {
@@ -277,21 +289,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                 }
             }
         }
-        bar_arrive(3 + buf, kThreads);  // buffer free
-        buf ^= 1;
+        bar_arrive(1 + kBufs + buf, kThreads);  // buffer free
+        buf = (buf + 1 == kBufs) ? 0 : buf + 1;
     }
 }
 
-template <int NPOL, int SP, int TK>
-void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
-    const size_t smem = sizeof(Smem<NPOL>);
-    cudaFuncSetAttribute(k_grid<NPOL, SP, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int NPOL, int SP, int TK, int D, int B>
+void launch_v(const GridArgs& a, int num_sms, cudaStream_t s) {
+    const size_t smem = sizeof(Smem<NPOL, B>);
+    cudaFuncSetAttribute(k_grid<NPOL, SP, TK, D, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP, TK>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP, TK, D, B>, kThreads,
+                                                  smem);
     if (per_sm < 1) per_sm = 1;
-    k_grid<NPOL, SP, TK><<<num_sms * per_sm, kThreads, smem, s>>>(a);
+    k_grid<NPOL, SP, TK, D, B><<<num_sms * per_sm, kThreads, smem, s>>>(a);
     note_launch();
+}
+
+// Two register sets of kernel values in flight and two staging buffers:
+// measured fastest on the 4-pol w-projection workload among rings of 2-4
+// entries and 2-4 buffers (deeper rings raise register pressure, more
+// buffers gave no gain).
+template <int NPOL, int SP, int TK>
+void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
+    launch_v<NPOL, SP, TK, 2, 2>(a, num_sms, s);
 }
 
 template <int NPOL, int TK>

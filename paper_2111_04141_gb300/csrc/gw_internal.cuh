@@ -54,14 +54,17 @@ __device__ __forceinline__ float2 unpack_f16x2(uint32_t u) {
 template <int TK> struct TabElem;
 template <> struct TabElem<GW_C64> {
     using T = float2;
+    static __device__ __forceinline__ float2 cvt(T v) { return v; }
     static __device__ __forceinline__ float2 load(const T* p) { return __ldg(p); }
 };
 template <> struct TabElem<GW_BF16X2> {
     using T = uint32_t;
+    static __device__ __forceinline__ float2 cvt(T v) { return unpack_bf16x2(v); }
     static __device__ __forceinline__ float2 load(const T* p) { return unpack_bf16x2(__ldg(p)); }
 };
 template <> struct TabElem<GW_F16X2> {
     using T = uint32_t;
+    static __device__ __forceinline__ float2 cvt(T v) { return unpack_f16x2(v); }
     static __device__ __forceinline__ float2 load(const T* p) { return unpack_f16x2(__ldg(p)); }
 };
 
