@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-stream measurement")
     ap.add_argument("--serving-jobs", type=int, default=256)
+    ap.add_argument("--no-imaging", action="store_true",
+                    help="skip the dirty-image pipeline and R(X) measurements")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 16-bit-storage and compensated-commit measurements")
     ap.add_argument("--cpu-sample-rows", type=int, default=0,
@@ -256,6 +258,46 @@ def measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
                               "grid_kernel_ms": tm["grid_ms"] / max(1, tm["grid_calls"]),
                               "rel_l2_vs_fp32": float(torch.linalg.vector_norm(g - ref) / nref)}
     return out
+
+
+def measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
+    """Dirty image of the batch (grid, shift, cuFFT inverse transform, correct,
+    normalise) and the aliasing experiment R(X) = |1 - K(X)| (unit point source
+    at pixel (X, X), X = 0..63, 128^2 image, support 7, oversampling 128)."""
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_2111_04141_gb300.imaging import dirty_image
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dirty_image(plan, uvw, freq, vis)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        dirty_image(plan, uvw, freq, vis)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    # R(X): point-source visibilities from the measurement equation in FP64
+    N = 128
+    o2 = syn.config_2d()
+    cell = syn.fit_cell(o2.uvw_m, o2.freq_hz, N, 7)
+    lam = (o2.uvw_m[:, None, :] * o2.freq_hz[None, :, None] / 299792458.0).reshape(-1, 3)
+    r = []
+    with gw.Plan(grid_n=N, cell_rad=cell, support_min=7, support_max=7, oversample=128,
+                 n_wplanes=1, npol=1) as p2:
+        u2, f2 = torch.from_numpy(o2.uvw_m).to(dev), torch.from_numpy(o2.freq_hz).to(dev)
+        for x in range(64):
+            v = np.exp(-2j * np.pi * (lam[:, 0] + lam[:, 1]) * (x * cell))
+            img = dirty_image(p2, u2, f2, torch.from_numpy(
+                v.reshape(o2.nrow, o2.nchan, 1).astype(np.complex64)).to(dev))
+            r.append(abs(1.0 - float(img[0, N // 2 + x, N // 2 + x].real)))
+    r = np.array(r)
+    return {"dirty_image_ms": ms, "images_per_s": 1e3 / ms,
+            "steps": "grid + shift + inverse FFT (cuFFT) + correct + normalise, "
+                     f"{obs.grid_n}^2 x {obs.npol}",
+            "R_X": {"max_X_le_32": float(r[:33].max()), "max_all": float(r.max()),
+                    "X": list(range(64)), "R": [float(t) for t in r],
+                    "setup": "16 antennas, 3,840 vis, 128^2, support 7, oversampling 128"}}
 
 
 def measure_serving(args, dev):
@@ -480,6 +522,8 @@ def main():
     precision = measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
         if not args.no_precision else None
 
+    imaging = measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
+        if not args.no_imaging else None
     serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
 
     cpu = None
@@ -507,7 +551,8 @@ def main():
                        "l2": "inputs larger than L2 (vis 264 MB, grid 512 MB); no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "degrid": degrid, "precision": precision, "serving": serving,
+            "clocks": clocks, "degrid": degrid, "precision": precision, "imaging": imaging,
+            "serving": serving,
         }
         print(json.dumps(line))
     plan.close()

@@ -15,6 +15,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   at the image pixels l_j = (j - N/2) * cell.  P = 1 (2-D mode) drops w.
 * ``measurement``: Eq. (measurmentequation) of Section 1.2 for a pixelised
   model, V = sum_{i,j} I[i, j] exp(-j 2 pi (u l_j + v m_i + w (n_ij - 1))).
+* ``point_source_vis``: the same for one unit point source at pixel
+  (N/2 + dy, N/2 + dx), the simulator of the aliasing experiment of
+  Section 8 (R(X) = |1 - K(X)|, K(X) the image value at the source).
 """
 from __future__ import annotations
 
@@ -87,3 +90,16 @@ def measurement(image: np.ndarray, uvw_m, freq_hz, prm: Params) -> np.ndarray:
         for pol in range(prm.npol):
             out[r, pol] = np.sum(image[pol] * e)
     return out
+
+
+def point_source_vis(uvw_m, freq_hz, prm: Params, dx: int, dy: int) -> np.ndarray:
+    """[nrow * nchan, npol] visibilities (FP64) of a unit point source at
+    pixel (row N/2 + dy, column N/2 + dx), all polarisations equal."""
+    l = dx * prm.cell_rad
+    m = dy * prm.cell_rad
+    r2 = l * l + m * m
+    nm1 = -r2 / (1.0 + np.sqrt(1.0 - r2))
+    lam = (uvw_m[:, None, :] * freq_hz[None, :, None] / C0).reshape(-1, 3)
+    ph = lam[:, 0] * l + lam[:, 1] * m + (lam[:, 2] * nm1 if prm.n_wplanes > 1 else 0.0)
+    v = np.exp(-2j * np.pi * ph)
+    return np.repeat(v[:, None], prm.npol, axis=1)

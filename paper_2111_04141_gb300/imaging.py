@@ -1,0 +1,52 @@
+"""Imaging pipeline around the gridder: dirty images and model visibilities.
+
+The imaging chain of Section 2.3 (Algorithm (convgridding)): gridding, the
+inverse FFT of the grid and the correction step, giving the dirty image
+(Eq. (ID) of Section 1.7 up to the approximation of the method); and its
+adjoint, model image -> visibilities.  Gridding, degridding, the origin
+shift and the correction run in libgw's kernels; the FFTs are cuFFT calls
+through torch.fft (unnormalised, so the two operators are exact adjoints).
+
+The dirty image is normalised by the sum of the weights of the visibilities
+that were gridded (dropped records excluded), so a unit point source
+observed by every visibility images to 1 at its pixel.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+
+def dirty_image(plan, uvw, freq, vis, weight: Optional[torch.Tensor] = None,
+                normalise: bool = True, stream=None) -> torch.Tensor:
+    """[npol, N, N] complex64 dirty image (the real part is the image)."""
+    g, dropped = plan.grid(uvw, freq, vis, weight=weight, stream=stream, return_dropped=True)
+    plan.shift(g, stream=stream)
+    img = torch.fft.ifft2(g, norm="forward")          # sum_k G_k exp(+j 2 pi k x / N)
+    plan.correct(img, direction=+1, stream=stream)
+    if normalise:
+        nrow, nchan = uvw.shape[0], freq.shape[0]
+        if weight is None:
+            wsum = float(nrow * nchan - dropped)
+        else:
+            # drops are visibilities whose footprint leaves the grid: their
+            # weights are excluded through the index records' valid flags
+            raw, _ = plan.index(uvw, freq, stream=stream)
+            valid = ((raw[:, 3] >> 16) & 1).to(torch.float32)
+            w = weight.reshape(nrow * nchan, -1) * valid[:, None]
+            ws = w.sum(0).to(torch.float64).clamp_min(1e-30)     # per polarisation
+            img /= ws.to(img.real.dtype)[:, None, None]
+            return img
+        img /= max(wsum, 1e-30)
+    return img
+
+
+def model_vis(plan, uvw, freq, image: torch.Tensor, stream=None) -> torch.Tensor:
+    """Visibilities [nrow, nchan, npol] of a [npol, N, N] model image: the
+    adjoint of the unnormalised dirty image (correct, FFT, shift, degrid)."""
+    x = image.to(torch.complex64).contiguous().clone()
+    plan.correct(x, direction=-1, stream=stream)
+    g = torch.fft.fft2(x, norm="backward").contiguous()  # sum_x I_x exp(-j 2 pi k x / N)
+    plan.shift(g, stream=stream)
+    return plan.degrid(uvw, freq, g, stream=stream)
