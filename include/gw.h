@@ -210,6 +210,22 @@ gw_status gw_grid_vis_compensated(gw_plan plan, const double* uvw_m, const doubl
                                   const float* weight, void* grid, void* grid_err,
                                   int64_t* n_dropped, void* cuda_stream);
 
+/* Gridding with full compression (Section 3.3.5, "Full Compression"):
+ * visibilities that fall on the same pixel of the beta-oversampled grid,
+ * in the same w-plane and with the same sign of w, are summed (weights
+ * applied) before gridding, so the gridder sees each distinct record once.
+ * The result equals gw_grid_vis up to FP32 summation order.  Arguments as
+ * gw_grid_vis, plus n_gridded (host, optional): receives the number of
+ * records gridded after compression (summed over internal chunks:
+ * compression acts within a chunk of max_vis_per_call visibilities); when
+ * non-NULL the call synchronises the stream.  The first call allocates the
+ * plan's compression scratch (a hash table of 2^ceil(log2(2 chunk)) keys).
+ * Errors: GW_EINVAL, GW_EDEVICE, GW_ENOMEM, GW_ECUDA. */
+gw_status gw_grid_vis_compressed(gw_plan plan, const double* uvw_m, const double* freq_hz,
+                                 int64_t nrow, int32_t nchan, const void* vis,
+                                 const float* weight, void* grid, int64_t* n_gridded,
+                                 int64_t* n_dropped, void* cuda_stream);
+
 /* grid += grid_err, then grid_err = 0 (device, both [npol][N][N] c64):
  * ends a sequence of gw_grid_vis_compensated calls.  Asynchronous on the
  * stream.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */

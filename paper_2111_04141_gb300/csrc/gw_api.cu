@@ -66,6 +66,7 @@ struct gw_plan_s {
     int max_tiles_per_vis = 0;
     int64_t chunk = 0;
     TableSet* tabs = nullptr;     // owner of the device tables below once the plan is built
+    CompressScratch cs;           // full-compression scratch (allocated on first use)
     int64_t scratch_bytes = 0;
     gw_tuning tuning{};
     // device state
@@ -109,6 +110,11 @@ void plan_free(gw_plan p) {
     for (auto e : p->pool) cudaEventDestroy(e);
     cudaFree(p->sc.work);
     cudaFree(p->sc.wvis);
+    cudaFree(p->cs.keys);
+    cudaFree(p->cs.acc);
+    cudaFree(p->cs.rec);
+    cudaFree(p->cs.vis);
+    cudaFree(p->cs.count);
     if (p->tabs) {
         TableSet* t = p->tabs;
         if (t->refs.fetch_sub(1) == 1) {
@@ -637,6 +643,105 @@ gw_status gw_grid_vis_compensated(gw_plan p, const double* uvw_m, const double* 
     if (!grid_err) return fail(GW_EINVAL, "null grid_err");
     return grid_impl(p, uvw_m, freq_hz, nrow, nchan, vis, weight, grid, grid_err, n_dropped,
                      cuda_stream);
+}
+
+static gw_status ensure_compress(gw_plan p, cudaStream_t s) {
+    CompressScratch& cs = p->cs;
+    if (cs.keys) return GW_OK;
+    int64_t cap = 1;
+    while (cap < 2 * p->chunk) cap <<= 1;
+    const int npol = p->desc.npol;
+    cudaError_t e = cudaSuccess;
+#define GW_CALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { \
+        cudaFree(cs.keys); cudaFree(cs.acc); cudaFree(cs.rec); cudaFree(cs.vis); \
+        cudaFree(cs.count); cs = CompressScratch{}; \
+        return fail(GW_ENOMEM, "allocating compression scratch (%s)", #x); } } while (0)
+    GW_CALLOC(cs.keys, (size_t)cap);
+    GW_CALLOC(cs.acc, (size_t)cap * npol);
+    GW_CALLOC(cs.rec, (size_t)p->chunk);
+    GW_CALLOC(cs.vis, (size_t)p->chunk * npol);
+    GW_CALLOC(cs.count, 2);
+#undef GW_CALLOC
+    cs.total = cs.count + 1;
+    cs.cap = cap;
+    clear_compress_table(cs, npol, s);
+    return GW_OK;
+}
+
+gw_status gw_grid_vis_compressed(gw_plan p, const double* uvw_m, const double* freq_hz,
+                                 int64_t nrow, int32_t nchan, const void* vis,
+                                 const float* weight, void* grid, int64_t* n_gridded,
+                                 int64_t* n_dropped, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!grid) return fail(GW_EINVAL, "null grid");
+    if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
+    const int vk = p->desc.vis_dtype;
+    const size_t vb = dtype_bytes(vk);
+    if ((reinterpret_cast<uintptr_t>(grid) % 8 != 0) || (reinterpret_cast<uintptr_t>(vis) % vb != 0))
+        return fail(GW_EINVAL, "grid must be 8-byte aligned and vis aligned to its element size");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    st = ensure_compress(p, s);
+    if (st != GW_OK) return st;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->cs.total, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const int npol = p->desc.npol;
+    const int64_t rpc = rows_per_chunk(p, nchan);
+    for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
+        const int64_t nr = std::min(rpc, nrow - r0);
+        const int64_t v0 = r0 * nchan;
+        const int64_t nv = nr * nchan;
+        {
+            StageTimer t(p, kStIndex, s);
+            launch_index(uvw_m + 3 * r0, freq_hz, nr, nchan, p->ip, p->sc.rec, p->sc.dropped, s);
+        }
+        launch_compress(p->sc.rec, nv, static_cast<const char*>(vis) + (size_t)v0 * npol * vb, vk,
+                        weight ? weight + v0 * npol : nullptr, npol, p->desc.oversample, p->cs, s);
+        // bin and grid the compressed records (count read on the device)
+        const DevCount dc{reinterpret_cast<const int64_t*>(p->cs.count), 1};
+        {
+            StageTimer t(p, kStBin, s);
+            launch_bin(p->cs.rec, nv, p->geom_grid, p->desc.n_wplanes, p->desc.support_min,
+                       p->desc.support_max, p->sc, s, dc);
+        }
+        GridArgs a;
+        a.rec = p->cs.rec;
+        a.ptable = p->ptable;
+        a.pplane_off = p->d_pplane_off;
+        a.vis = p->cs.vis;
+        a.vis_kind = GW_C64;
+        a.weight = nullptr;
+        a.table_kind = p->desc.table_dtype;
+        a.table_inv = p->table_inv;
+        a.plane_off = p->d_plane_off;
+        a.support = p->d_support;
+        a.entries = p->sc.entries;
+        a.items = p->sc.items;
+        a.item_count = p->sc.item_off + p->geom_grid.ntu * p->geom_grid.ntv;
+        a.queue = p->sc.counters;
+        a.grid = reinterpret_cast<float2*>(grid);
+        a.grid_err = nullptr;
+        a.N = p->desc.grid_n;
+        a.npol = npol;
+        a.beta = p->desc.oversample;
+        a.ntiles_u = p->geom_grid.ntu;
+        a.pad_stride = p->pad_stride;
+        {
+            StageTimer t(p, kStGrid, s);
+            launch_grid(a, p->num_sms, s);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "compressed grid launch");
+    }
+    if (n_gridded) {
+        unsigned long long h = 0;
+        e = cudaMemcpyAsync(&h, p->cs.total, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the compressed count");
+        *n_gridded = (int64_t)h;
+    }
+    return finish_dropped(p, n_dropped, s);
 }
 
 gw_status gw_grid_fold(gw_plan p, void* grid, void* grid_err, void* cuda_stream) {

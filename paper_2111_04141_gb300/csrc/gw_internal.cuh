@@ -235,6 +235,24 @@ bool degrid_staged_fits(int hmax, int npol);
 // Returns false (nothing launched) if the region does not fit.
 bool launch_degrid_staged(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s);
 
+// ---- full compression (gw_compress.cu) --------------------------------------
+struct CompressScratch {
+    unsigned long long* keys = nullptr;   // [cap] hash keys (all ones = empty)
+    float2* acc = nullptr;                // [cap * npol] summed weighted visibilities
+    gw_index_rec* rec = nullptr;          // [chunk] compressed records
+    float2* vis = nullptr;                // [chunk * npol] their visibilities
+    unsigned long long* count = nullptr;  // [1] compressed records of the current chunk
+    unsigned long long* total = nullptr;  // [1] compressed records of the call
+    int64_t cap = 0;                      // power of two >= 2 * chunk
+};
+// Adds the weighted visibilities of valid records with equal (k, o, plane,
+// sign of w) and writes the distinct records to cs.rec / cs.vis (*cs.count
+// of them, order unspecified); the table is left empty for the next call.
+void launch_compress(const gw_index_rec* rec, int64_t nvis, const void* vis, int vis_kind,
+                     const float* weight, int npol, int beta, CompressScratch& cs,
+                     cudaStream_t s);
+void clear_compress_table(CompressScratch& cs, int npol, cudaStream_t s);
+
 // ---- allocation-free scratch (gw_noalloc.cu) ------------------------------
 // View of the file-scope static scratch on `device` (current); looks up the
 // symbol's device address on first use per device.

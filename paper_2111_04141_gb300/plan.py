@@ -228,6 +228,25 @@ class Plan:
               "gw_degrid_vis_devcount")
         return out
 
+    def grid_compressed(self, uvw, freq, vis, weight=None, out=None, stream=None):
+        """Gridding with full compression (gw_grid_vis_compressed).  Returns
+        (grid, records gridded after compression, dropped)."""
+        nrow, nchan = self._coords(uvw, freq)
+        vis = self._vis_arg(vis, "vis", nrow, nchan)
+        if weight is not None:
+            _need(weight, "weight", torch.float32, self.device, (nrow, nchan, self.npol))
+        if out is None:
+            out = self.new_grid()
+        _need(out, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        ng, nd = ctypes.c_int64(-1), ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_vis_compressed(self._h, _ptr(uvw), _ptr(freq), nrow, nchan,
+                                                   _ptr(vis), _ptr(weight), _ptr(out),
+                                                   ctypes.byref(ng), ctypes.byref(nd),
+                                                   _stream_ptr(stream, self.device)),
+                  "gw_grid_vis_compressed")
+        return out, int(ng.value), int(nd.value)
+
     def fold(self, grid, err, stream=None):
         """grid += err; err = 0 (ends a compensated gridding sequence)."""
         gshape = (self.npol, self.grid_n, self.grid_n)
