@@ -226,6 +226,33 @@ gw_status gw_grid_vis_compressed(gw_plan plan, const double* uvw_m, const double
                                  const float* weight, void* grid, int64_t* n_gridded,
                                  int64_t* n_dropped, void* cuda_stream);
 
+/* W-stacking (Section 1.7.1, "Correction of the W-term in the (l,m)-plane"):
+ * each visibility is gridded with the plan's 2-D kernel (the plan must have
+ * n_wplanes == 1) onto the grid of its w-layer, layer
+ * l = clamp(floor((w_lambda - w_min) / dw + 1/2), 0, n_layers - 1),
+ * dw = (w_max - w_min) / (n_layers - 1), computed in FP64 like the index
+ * stage (records beyond the range use the outermost layer).
+ *   layers  device, [n_layers][npol][N][N] c64, accumulated (+=)
+ * Other arguments as gw_grid_vis.  The image is then formed per layer
+ * (gw_grid_shift, an unnormalised inverse FFT) and combined with
+ * gw_wstack_combine, then gw_grid_correct(+1).  The first call allocates
+ * the plan's layered bins.  Errors: GW_EINVAL, GW_EDEVICE, GW_ENOMEM, GW_ECUDA. */
+gw_status gw_grid_vis_wstack(gw_plan plan, const double* uvw_m, const double* freq_hz,
+                             int64_t nrow, int32_t nchan, const void* vis, const float* weight,
+                             int32_t n_layers, double w_min_lambda, double w_max_lambda,
+                             void* layers, int64_t* n_dropped, void* cuda_stream);
+
+/* image[pol][i][j] += sum_l layer_images[l][pol][i][j] * exp(+j 2 pi w_l (n_ij - 1)),
+ * w_l = w_min + l dw as in gw_grid_vis_wstack, n_ij - 1 = -r^2 / (1 + sqrt(1 - r^2)),
+ * r^2 = l_j^2 + m_i^2, l_j = (j - N/2) cell_rad, m_i = (i - N/2) cell_rad: the
+ * w-screen correction of each layer's image (Eq. (lmwcorr)) and their sum.
+ * The screen is formed in FP64.  layer_images: device [n_layers][npol][N][N]
+ * c64 (the inverse transforms of the shifted layer grids); image: device
+ * [npol][N][N] c64, accumulated.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */
+gw_status gw_wstack_combine(gw_plan plan, const void* layer_images, int32_t n_layers,
+                            double w_min_lambda, double w_max_lambda, void* image,
+                            void* cuda_stream);
+
 /* grid += grid_err, then grid_err = 0 (device, both [npol][N][N] c64):
  * ends a sequence of gw_grid_vis_compensated calls.  Asynchronous on the
  * stream.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */

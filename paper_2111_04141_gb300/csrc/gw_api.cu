@@ -67,6 +67,12 @@ struct gw_plan_s {
     int64_t chunk = 0;
     TableSet* tabs = nullptr;     // owner of the device tables below once the plan is built
     CompressScratch cs;           // full-compression scratch (allocated on first use)
+    // w-stacking bins over layers x tiles (allocated on first use, grown on demand)
+    int ws_layers = 0;
+    uint32_t *ws_count = nullptr, *ws_offsets = nullptr, *ws_cursor = nullptr,
+             *ws_item_off = nullptr;
+    Item* ws_items = nullptr;
+    int64_t ws_items_cap = 0;
     int64_t scratch_bytes = 0;
     gw_tuning tuning{};
     // device state
@@ -115,6 +121,11 @@ void plan_free(gw_plan p) {
     cudaFree(p->cs.rec);
     cudaFree(p->cs.vis);
     cudaFree(p->cs.count);
+    cudaFree(p->ws_count);
+    cudaFree(p->ws_offsets);
+    cudaFree(p->ws_cursor);
+    cudaFree(p->ws_item_off);
+    cudaFree(p->ws_items);
     if (p->tabs) {
         TableSet* t = p->tabs;
         if (t->refs.fetch_sub(1) == 1) {
@@ -742,6 +753,132 @@ gw_status gw_grid_vis_compressed(gw_plan p, const double* uvw_m, const double* f
         *n_gridded = (int64_t)h;
     }
     return finish_dropped(p, n_dropped, s);
+}
+
+static gw_status ensure_wstack(gw_plan p, int nlayers) {
+    if (p->ws_layers >= nlayers) return GW_OK;
+    cudaFree(p->ws_count);
+    cudaFree(p->ws_offsets);
+    cudaFree(p->ws_cursor);
+    cudaFree(p->ws_item_off);
+    cudaFree(p->ws_items);
+    p->ws_count = p->ws_offsets = p->ws_cursor = p->ws_item_off = nullptr;
+    p->ws_items = nullptr;
+    p->ws_layers = 0;
+    const int64_t nt = (int64_t)nlayers * p->geom_grid.ntu * p->geom_grid.ntv;
+    if (nt >= ((int64_t)1 << 31)) return fail(GW_EINVAL, "too many layer tiles");
+    const int64_t icap = p->sc.entries_cap / kItemMin + nt + 1;
+    cudaError_t e = dmalloc(&p->ws_count, (size_t)nt);
+    if (e == cudaSuccess) e = dmalloc(&p->ws_offsets, (size_t)nt + 1);
+    if (e == cudaSuccess) e = dmalloc(&p->ws_cursor, (size_t)nt);
+    if (e == cudaSuccess) e = dmalloc(&p->ws_item_off, (size_t)nt + 1);
+    if (e == cudaSuccess) e = dmalloc(&p->ws_items, (size_t)icap);
+    if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating w-stacking bins");
+    p->ws_layers = nlayers;
+    p->ws_items_cap = icap;
+    return GW_OK;
+}
+
+gw_status gw_grid_vis_wstack(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                             int32_t nchan, const void* vis, const float* weight,
+                             int32_t n_layers, double w_min_lambda, double w_max_lambda,
+                             void* layers, int64_t* n_dropped, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (p->desc.n_wplanes != 1)
+        return fail(GW_EINVAL, "w-stacking needs a 2-D plan (n_wplanes == 1)");
+    if (n_layers < 1 || n_layers > 4096) return fail(GW_EINVAL, "n_layers must be in [1, 4096]");
+    if (!std::isfinite(w_min_lambda) || !std::isfinite(w_max_lambda) ||
+        (n_layers > 1 && !(w_max_lambda > w_min_lambda)))
+        return fail(GW_EINVAL, "w range must be finite with w_max > w_min");
+    if (!layers) return fail(GW_EINVAL, "null layers");
+    if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
+    const int vk = p->desc.vis_dtype;
+    const size_t vb = dtype_bytes(vk);
+    if ((reinterpret_cast<uintptr_t>(layers) % 8 != 0) ||
+        (reinterpret_cast<uintptr_t>(vis) % vb != 0))
+        return fail(GW_EINVAL, "layers must be 8-byte aligned and vis aligned to its element size");
+    st = ensure_wstack(p, n_layers);
+    if (st != GW_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    IndexParams ip = p->ip;
+    ip.nlayers = n_layers;
+    ip.wmin = w_min_lambda;
+    ip.dw = n_layers > 1 ? (w_max_lambda - w_min_lambda) / (double)(n_layers - 1) : 1.0;
+    BinGeom g = p->geom_grid;
+    g.layer_tiles = g.ntu * g.ntv;
+    g.nlayers = n_layers;
+    Scratch sc = p->sc;
+    sc.count = p->ws_count;
+    sc.offsets = p->ws_offsets;
+    sc.cursor = p->ws_cursor;
+    sc.item_off = p->ws_item_off;
+    sc.items = p->ws_items;
+    sc.items_cap = p->ws_items_cap;
+    const int npol = p->desc.npol;
+    const int64_t rpc = rows_per_chunk(p, nchan);
+    for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
+        const int64_t nr = std::min(rpc, nrow - r0);
+        const int64_t v0 = r0 * nchan;
+        {
+            StageTimer t(p, kStIndex, s);
+            launch_index(uvw_m + 3 * r0, freq_hz, nr, nchan, ip, sc.rec, sc.dropped, s);
+        }
+        {
+            StageTimer t(p, kStBin, s);
+            launch_bin(sc.rec, nr * (int64_t)nchan, g, 1, p->desc.support_min,
+                       p->desc.support_min, sc, s);
+        }
+        GridArgs a;
+        a.rec = sc.rec;
+        a.ptable = p->ptable;
+        a.pplane_off = p->d_pplane_off;
+        a.vis = static_cast<const char*>(vis) + (size_t)v0 * npol * vb;
+        a.vis_kind = vk;
+        a.weight = weight ? weight + v0 * npol : nullptr;
+        a.table_kind = p->desc.table_dtype;
+        a.table_inv = p->table_inv;
+        a.plane_off = p->d_plane_off;
+        a.support = p->d_support;
+        a.entries = sc.entries;
+        a.items = sc.items;
+        a.item_count = sc.item_off + (int64_t)g.layer_tiles * n_layers;
+        a.queue = sc.counters;
+        a.grid = reinterpret_cast<float2*>(layers);
+        a.grid_err = nullptr;
+        a.N = p->desc.grid_n;
+        a.npol = npol;
+        a.beta = p->desc.oversample;
+        a.ntiles_u = g.ntu;
+        a.pad_stride = p->pad_stride;
+        a.layer_tiles = g.layer_tiles;
+        a.layer_stride = (int64_t)npol * p->desc.grid_n * p->desc.grid_n;
+        {
+            StageTimer t(p, kStGrid, s);
+            launch_grid(a, p->num_sms, s);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "w-stacking grid launch");
+    }
+    return finish_dropped(p, n_dropped, s);
+}
+
+gw_status gw_wstack_combine(gw_plan p, const void* layer_images, int32_t n_layers,
+                            double w_min_lambda, double w_max_lambda, void* image,
+                            void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    if (!layer_images || !image) return fail(GW_EINVAL, "null argument");
+    if (n_layers < 1 || n_layers > 4096) return fail(GW_EINVAL, "n_layers must be in [1, 4096]");
+    const double dw = n_layers > 1 ? (w_max_lambda - w_min_lambda) / (double)(n_layers - 1) : 1.0;
+    launch_wstack_combine(reinterpret_cast<const float2*>(layer_images), n_layers, w_min_lambda, dw,
+                          p->desc.grid_n, p->desc.npol, p->desc.cell_rad,
+                          reinterpret_cast<float2*>(image), (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "w-stacking combine launch");
 }
 
 gw_status gw_grid_fold(gw_plan p, void* grid, void* grid_err, void* cuda_stream) {

@@ -54,8 +54,10 @@ __global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, DevC
         ++n_valid;
         n_taps += (unsigned long long)(S * S);
         const TileRange t = tile_range(r, g, P, smin, smax);
+        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
-            for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(count + tv * g.ntu + tu, 1u);
+            for (int tu = t.tu0; tu <= t.tu1; ++tu)
+                atomicAdd(count + lbase + tv * g.ntu + tu, 1u);
     }
     for (int d = 16; d > 0; d >>= 1) {
         n_valid += __shfl_down_sync(0xffffffffu, n_valid, d);
@@ -124,9 +126,10 @@ __global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, De
         const gw_index_rec r = load_rec(rec, i);
         if (!(r.flags & GW_FLAG_VALID)) continue;
         const TileRange t = tile_range(r, g, P, smin, smax);
+        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu) {
-                const int tile = tv * g.ntu + tu;
+                const int tile = lbase + tv * g.ntu + tu;
                 const uint32_t pos = atomicAdd(cursor + tile, 1u);
                 entries[offsets[tile] + pos] = (uint32_t)i;
             }
@@ -154,7 +157,7 @@ __global__ void k_items(const uint32_t* __restrict__ count, const uint32_t* __re
 
 void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
                 Scratch& sc, cudaStream_t s, DevCount dc) {
-    const int ntiles = g.ntu * g.ntv;
+    const int ntiles = g.ntu * g.ntv * (g.layer_tiles ? g.nlayers : 1);
     cudaMemsetAsync(sc.count, 0, sizeof(uint32_t) * ntiles, s);
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;

@@ -63,6 +63,44 @@ __global__ void k_zero_vis(uint32_t* __restrict__ v, int64_t n_max, int words, D
         v[e] = 0u;
 }
 
+// Sum of layer images times their w-screens (w-stacking, Section 1.7.1):
+// the screen of layer l at pixel (i, j) is exp(+j 2 pi w_l (n - 1)) with
+// n - 1 = -r^2 / (1 + sqrt(1 - r^2)), r^2 = l_j^2 + m_i^2; it is formed in
+// FP64 as screen_0 * rot^l, rot = exp(+j 2 pi dw (n - 1)).
+__global__ void k_wstack_combine(const float2* __restrict__ layers, int nlayers, double wmin,
+                                 double dw, int N, int npol, double cell,
+                                 float2* __restrict__ image) {
+    const int64_t n = (int64_t)N * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e - (int64_t)i * N);
+        const double l = (j - N / 2) * cell, m = (i - N / 2) * cell;
+        const double r2 = l * l + m * m;
+        const double nm1 = r2 < 1.0 ? -r2 / (1.0 + sqrt(1.0 - r2)) : 0.0;
+        double s0, c0, s1, c1;
+        sincospi(2.0 * wmin * nm1, &s0, &c0);
+        sincospi(2.0 * dw * nm1, &s1, &c1);
+        double cr = c0, ci = s0;                     // screen of layer 0
+        double acc[4][2] = {};
+        for (int L = 0; L < nlayers; ++L) {
+            for (int p = 0; p < npol && p < 4; ++p) {
+                const float2 v = layers[((int64_t)L * npol + p) * n + e];
+                acc[p][0] += v.x * cr - v.y * ci;
+                acc[p][1] += v.x * ci + v.y * cr;
+            }
+            const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
+            cr = nr;
+            ci = ni;
+        }
+        for (int p = 0; p < npol && p < 4; ++p) {
+            float2 o = image[(int64_t)p * n + e];
+            o.x += (float)acc[p][0];
+            o.y += (float)acc[p][1];
+            image[(int64_t)p * n + e] = o;
+        }
+    }
+}
+
 unsigned blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     if (b > 152 * 32) b = 152 * 32;
@@ -85,6 +123,13 @@ void launch_zero_vis(void* vis, int kind, int64_t n_max, int npol, DevCount dc, 
     const int words = npol * dtype_bytes(kind) / 4;
     k_zero_vis<<<blocks_for(n_max * words), 256, 0, s>>>(static_cast<uint32_t*>(vis), n_max, words,
                                                         dc);
+    note_launch();
+}
+
+void launch_wstack_combine(const float2* layers, int nlayers, double wmin, double dw, int N,
+                           int npol, double cell, float2* image, cudaStream_t s) {
+    k_wstack_combine<<<blocks_for((int64_t)N * N), 256, 0, s>>>(layers, nlayers, wmin, dw, N, npol,
+                                                                 cell, image);
     note_launch();
 }
 

@@ -124,15 +124,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                         sm.last[buf] = 1;
                     }
                 } else {
-                    const int tu0 = (item.tile % side) * kTile;
-                    const int tv0 = (item.tile / side) * kTile;
+                    // with w-layers (w-stacking) a tile id is layer * layer_tiles + tile
+                    const int ltile = a.layer_tiles ? item.tile % a.layer_tiles : item.tile;
+                    const int tu0 = (ltile % side) * kTile;
+                    const int tv0 = (ltile / side) * kTile;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
                     for (int r = lane; r < nb; r += 32) {
                         const uint32_t id = __ldg(a.entries + item.start + b0 + r);
                         const gw_index_rec rc = load_rec(a.rec, id);
-                        const int S = __ldg(a.support + rc.plane), h = S >> 1;
-                        const int64_t slice = __ldg(a.pplane_off + rc.plane) +
+                        // w-stacking records carry their layer in `plane`; the
+                        // kernel is the plan's single (w = 0) plane
+                        const int plane = a.layer_tiles ? 0 : rc.plane;
+                        const int S = __ldg(a.support + plane), h = S >> 1;
+                        const int64_t slice = __ldg(a.pplane_off + plane) +
                                               ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
                                                   (int64_t)(S + 6) * SP;
                         // padded index of the tile origin relative to this record
@@ -268,8 +273,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
 #undef GW_LOAD_K
         if (last) {
             // commit the tile's accumulators of this work item
-            const int u = (tile % a.ntiles_u) * kTile + bu + lu;
-            const int v0 = (tile / a.ntiles_u) * kTile + bv + lv;
+            const int ltile = a.layer_tiles ? tile % a.layer_tiles : tile;
+            float2* const gbase = a.grid + (a.layer_tiles ? (int64_t)(tile / a.layer_tiles) *
+                                                                 a.layer_stride : 0);
+            const int u = (ltile % a.ntiles_u) * kTile + bu + lu;
+            const int v0 = (ltile / a.ntiles_u) * kTile + bv + lv;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int v = v0 + 4 * j;
@@ -280,9 +288,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                                                        acc[j][p].y * a.table_inv);
                         const int64_t off = ((int64_t)p * N + v) * N + u;
                         if (a.grid_err) {
-                            commit_compensated(a.grid + off, a.grid_err + off, val);
+                            commit_compensated(gbase + off, a.grid_err + off, val);
                         } else {
-                            atomicAdd(a.grid + off, val);
+                            atomicAdd(gbase + off, val);
                         }
                     }
                     acc[j][p] = make_float2(0.f, 0.f);

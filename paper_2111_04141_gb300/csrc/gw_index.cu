@@ -57,6 +57,13 @@ __global__ void k_index(const double* __restrict__ uvw, const double* __restrict
             okw = isfinite(pf);
             plane = okw ? (int)fmin(pf, p.Pm1_d) : 0;
             conj = wl < 0.0;
+        } else if (p.nlayers > 0) {
+            // w-stacking layer: nearest of w_l = wmin + l dw, clamped to the layers
+            const double w = __ldg(uvw + 3 * row + 2);
+            const double wl = __ddiv_rn(__dmul_rn(w, f), kC0);
+            const double t = floor(__dadd_rn(__ddiv_rn(__dsub_rn(wl, p.wmin), p.dw), 0.5));
+            okw = isfinite(t);
+            plane = okw ? (int)fmin(fmax(t, 0.0), (double)(p.nlayers - 1)) : 0;
         }
         const int h = plane_support(plane, p.P, p.smin, p.smax) / 2;
         const bool inside = (au.k - h >= 0) && (au.k + h <= p.N - 1) &&

@@ -93,6 +93,10 @@ struct IndexParams {
     double Pm1_d;    // P - 1 as double
     double wmax;     // w_max (wavelengths)
     int N, beta, P, smin, smax;
+    // w-stacking (2-D plans only): layer = clamp(floor((w - wmin) / dw + 1/2), 0, nlayers - 1)
+    // stored in the record's `plane` field; nlayers = 0: off
+    int nlayers = 0;
+    double wmin = 0.0, dw = 1.0;
 };
 
 // Work item of the gridder: a contiguous run of one tile's bin.
@@ -147,6 +151,8 @@ void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan
 struct BinGeom {
     int mode, su, sv, ntu, ntv;
     int item_max = kItemMax;
+    int layer_tiles = 0;   // > 0: tile id += record.plane * layer_tiles (w-stacking layers)
+    int nlayers = 1;       // layers binned when layer_tiles > 0 (ntu * ntv * nlayers tiles)
 };
 // Also accumulates sc.work[0] += valid records, sc.work[1] += sum of S_p^2.
 // Work items are written only when sc.items is non-null.
@@ -192,6 +198,10 @@ struct GridArgs {
     int pad_stride;              // padded row stride (padded_stride(S_max))
     int vis_kind, table_kind;    // gw_dtype of vis and of the tables
     float table_inv;             // 2^-exp2: undoes the table storage scale at the commit
+    // w-stacking: tile ids are layer * layer_tiles + tile, records carry their
+    // layer in `plane`, layer grids are layer_stride elements apart (0 = off)
+    int layer_tiles = 0;
+    int64_t layer_stride = 0;
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
 // One instantiation set per table kind (gw_grid_c64.cu, gw_grid_bf16.cu, gw_grid_f16.cu).
@@ -263,6 +273,10 @@ int static_scratch_max_tiles();
 // ---- correction (gw_correct.cu) -------------------------------------------
 void launch_correct(float2* image, const float* h, int N, int npol, int mode, cudaStream_t s);
 void launch_shift(float2* grid, int N, int npol, cudaStream_t s);
+// image[p][i][j] += sum_l layers[l][p][i][j] exp(+j 2 pi w_l (n_ij - 1)),
+// w_l = wmin + l dw, l_j = (j - N/2) cell, m_i = (i - N/2) cell (w-stacking).
+void launch_wstack_combine(const float2* layers, int nlayers, double wmin, double dw, int N,
+                           int npol, double cell, float2* image, cudaStream_t s);
 // grid[i] += err[i]; err[i] = 0 over n complex elements.
 void launch_fold(float2* grid, float2* err, int64_t n, cudaStream_t s);
 // Zero elements [0, min(n_max, dc count) * npol) of a visibility buffer of kind `kind`.

@@ -247,6 +247,40 @@ class Plan:
                   "gw_grid_vis_compressed")
         return out, int(ng.value), int(nd.value)
 
+    def grid_wstack(self, uvw, freq, vis, n_layers, w_min, w_max, weight=None, out=None,
+                    stream=None, return_dropped=False):
+        """W-stacking gridding (gw_grid_vis_wstack) onto [n_layers, npol, N, N]."""
+        nrow, nchan = self._coords(uvw, freq)
+        vis = self._vis_arg(vis, "vis", nrow, nchan)
+        if weight is not None:
+            _need(weight, "weight", torch.float32, self.device, (nrow, nchan, self.npol))
+        shape = (int(n_layers), self.npol, self.grid_n, self.grid_n)
+        if out is None:
+            out = torch.zeros(shape, dtype=torch.complex64, device=self.device)
+        _need(out, "layers", torch.complex64, self.device, shape)
+        nd = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_vis_wstack(self._h, _ptr(uvw), _ptr(freq), nrow, nchan,
+                                               _ptr(vis), _ptr(weight), int(n_layers),
+                                               float(w_min), float(w_max), _ptr(out),
+                                               ctypes.byref(nd) if return_dropped else None,
+                                               _stream_ptr(stream, self.device)),
+                  "gw_grid_vis_wstack")
+        return (out, int(nd.value)) if return_dropped else out
+
+    def wstack_combine(self, layer_images, w_min, w_max, image, stream=None):
+        """image += sum over layers of the layer image times its w-screen."""
+        L = int(layer_images.shape[0])
+        _need(layer_images, "layer_images", torch.complex64, self.device,
+              (L, self.npol, self.grid_n, self.grid_n))
+        _need(image, "image", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_wstack_combine(self._h, _ptr(layer_images), L, float(w_min),
+                                              float(w_max), _ptr(image),
+                                              _stream_ptr(stream, self.device)),
+                  "gw_wstack_combine")
+        return image
+
     def fold(self, grid, err, stream=None):
         """grid += err; err = 0 (ends a compensated gridding sequence)."""
         gshape = (self.npol, self.grid_n, self.grid_n)
