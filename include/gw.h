@@ -253,6 +253,36 @@ gw_status gw_wstack_combine(gw_plan plan, const void* layer_images, int32_t n_la
                             double w_min_lambda, double w_max_lambda, void* image,
                             void* cuda_stream);
 
+/* Hybrid Gridding with a column pruner (Section 2.4, Algorithm (hybrid)),
+ * for 2-D plans (n_wplanes == 1, grid_n % 4 == 0).  Four steps:
+ *   gw_hybrid_grid   Gridding Step: each visibility is convolved along u with
+ *                    the plan's oversampled 1-D GCF (support_min taps) and
+ *                    put on the nearest of beta*N rows along v:
+ *                    fine[pol][kv*beta + ov][ku + t] += c(t - ou/beta) * vis;
+ *                    fine: device [npol][beta*N][N] c64, accumulated.
+ *   gw_hybrid_prune  Pruning Step: each column is sampled down by beta/2 onto
+ *                    2N rows through the pruning GCF Z, the zeroth-order PSWF
+ *                    with odd support sz on the 2x grid (normalised taps):
+ *                    pruned[pol][k][u] = sum_r Z(k - 2r/beta) fine[pol][r][u];
+ *                    pruned: device [npol][2N][N] c64, overwritten.
+ *   gw_hybrid_shift  pruned *= (-1)^(k + u) before an unnormalised inverse FFT.
+ *   gw_hybrid_image  Correction Step: keeps rows N/2 .. 3N/2 - 1 of the
+ *                    transform `raw` ([npol][2N][N]), re-centres them and
+ *                    applies h_co(l) h_pr(m) (Eq. (hhy)); image: device
+ *                    [npol][N][N] c64, overwritten.
+ * A visibility is dropped (and counted) when the index stage drops it or
+ * its pruning window leaves the 2N rows.  The pruner of a support is built
+ * on first use (synchronous).  Errors: GW_EINVAL, GW_EDEVICE, GW_ENOMEM,
+ * GW_ECUDA. */
+gw_status gw_hybrid_grid(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                         int32_t nchan, const void* vis, const float* weight, int32_t sz,
+                         void* fine, int64_t* n_dropped, void* cuda_stream);
+gw_status gw_hybrid_prune(gw_plan plan, int32_t sz, const void* fine, void* pruned,
+                          void* cuda_stream);
+gw_status gw_hybrid_shift(gw_plan plan, void* pruned, void* cuda_stream);
+gw_status gw_hybrid_image(gw_plan plan, int32_t sz, const void* raw, void* image,
+                          void* cuda_stream);
+
 /* grid += grid_err, then grid_err = 0 (device, both [npol][N][N] c64):
  * ends a sequence of gw_grid_vis_compensated calls.  Asynchronous on the
  * stream.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */

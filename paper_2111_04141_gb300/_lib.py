@@ -65,6 +65,11 @@ _SIGS = {
     "gw_grid_vis_compensated": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
                                         ctypes.POINTER(c_i64), c_vp]),
     "gw_grid_fold": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "gw_hybrid_grid": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_i32, c_vp,
+                               ctypes.POINTER(c_i64), c_vp]),
+    "gw_hybrid_prune": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "gw_hybrid_shift": (c_i32, [c_vp, c_vp, c_vp]),
+    "gw_hybrid_image": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "gw_grid_vis_wstack": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_i32, c_f64, c_f64,
                                    c_vp, ctypes.POINTER(c_i64), c_vp]),
     "gw_wstack_combine": (c_i32, [c_vp, c_vp, c_i32, c_f64, c_f64, c_vp, c_vp]),

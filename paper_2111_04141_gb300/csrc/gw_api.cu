@@ -73,6 +73,15 @@ struct gw_plan_s {
              *ws_item_off = nullptr;
     Item* ws_items = nullptr;
     int64_t ws_items_cap = 0;
+    // hybrid gridding: the 1-D w = 0 kernel (kept from the table build) and
+    // the pruner of the last support used
+    double* d_c1 = nullptr;
+    int c1_fmin = 0;
+    double c1_norm = 1.0;
+    int hy_sz = 0;
+    float* d_z = nullptr;
+    double* d_hpr = nullptr;
+    float* d_hprf = nullptr;
     int64_t scratch_bytes = 0;
     gw_tuning tuning{};
     // device state
@@ -126,6 +135,10 @@ void plan_free(gw_plan p) {
     cudaFree(p->ws_cursor);
     cudaFree(p->ws_item_off);
     cudaFree(p->ws_items);
+    cudaFree(p->d_c1);
+    cudaFree(p->d_z);
+    cudaFree(p->d_hpr);
+    cudaFree(p->d_hprf);
     if (p->tabs) {
         TableSet* t = p->tabs;
         if (t->refs.fetch_sub(1) == 1) {
@@ -404,6 +417,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     GW_ALLOC(p->d_support, (size_t)P);
     GW_ALLOC(p->d_h, (size_t)N);
     GW_ALLOC(p->d_hf, (size_t)N);
+    GW_ALLOC(p->d_c1, (size_t)beta * p->support[0]);
 #undef GW_ALLOC
     if (alloc_scratch(p) != GW_OK) {
         plan_free(p);
@@ -435,8 +449,19 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     tb.plane_off = p->plane_off.data();
     tb.num_sms = p->num_sms;
     e = build_tables(tb, p->table, p->table16, desc->table_dtype, p->d_h, p->d_hf,
-                     &p->table_scale, &p->table_exp2, s);
+                     &p->table_scale, &p->table_exp2, p->d_c1, s);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "building kernel tables"); }
+    {
+        // normalisation of the 1-D kernel: its zero-offset taps sum to 1
+        const int S0 = p->support[0], h0 = S0 / 2;
+        p->c1_fmin = -beta * h0 - beta / 2 + 1;
+        std::vector<double> c1((size_t)beta * S0);
+        e = cudaMemcpy(c1.data(), p->d_c1, sizeof(double) * c1.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "reading the 1-D kernel"); }
+        double nrm = 0.0;
+        for (int t = -h0; t <= h0; ++t) nrm += c1[beta * t - p->c1_fmin];
+        p->c1_norm = nrm;
+    }
     p->table_inv = std::ldexp(1.0f, -p->table_exp2);
     if (desc->table_dtype == GW_C64)
         launch_pad_tables(p->table, GW_C64, p->d_plane_off, p->d_pplane_off, p->d_support, P,
@@ -516,8 +541,16 @@ gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream
     p->d_hf = src->d_hf;
     st = alloc_scratch(p);
     if (st != GW_OK) { plan_free(p); return st; }
-    cudaError_t e = cudaMemsetAsync(p->sc.work, 0, 2 * sizeof(unsigned long long),
-                                    (cudaStream_t)cuda_stream);
+    p->c1_fmin = src->c1_fmin;
+    p->c1_norm = src->c1_norm;
+    const size_t nc1 = (size_t)src->desc.oversample * src->support[0];
+    cudaError_t e = dmalloc(&p->d_c1, nc1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_c1, src->d_c1, sizeof(double) * nc1, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "copying the 1-D kernel"); }
+    e = cudaMemsetAsync(p->sc.work, 0, 2 * sizeof(unsigned long long),
+                        (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaMemsetAsync"); }
     apply_tuning(p);
     *out = p;
@@ -879,6 +912,118 @@ gw_status gw_wstack_combine(gw_plan p, const void* layer_images, int32_t n_layer
                           reinterpret_cast<float2*>(image), (cudaStream_t)cuda_stream);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GW_OK : cuda_fail(e, "w-stacking combine launch");
+}
+
+static gw_status hybrid_checks(gw_plan p, int32_t sz) {
+    if (p->desc.n_wplanes != 1) return fail(GW_EINVAL, "hybrid gridding needs a 2-D plan");
+    if (sz < 1 || !(sz & 1) || sz > 127) return fail(GW_EINVAL, "sz must be odd in [1, 127]");
+    if (p->desc.grid_n % 4 != 0) return fail(GW_EINVAL, "hybrid gridding needs grid_n % 4 == 0");
+    if ((int64_t)p->desc.oversample * p->desc.grid_n >= ((int64_t)1 << 31))
+        return fail(GW_EINVAL, "oversample * grid_n too large");
+    return GW_OK;
+}
+
+static gw_status ensure_prune(gw_plan p, int32_t sz, cudaStream_t s) {
+    if (p->hy_sz == sz) return GW_OK;
+    cudaFree(p->d_z);
+    cudaFree(p->d_hpr);
+    cudaFree(p->d_hprf);
+    p->d_z = nullptr;
+    p->d_hpr = nullptr;
+    p->d_hprf = nullptr;
+    p->hy_sz = 0;
+    const int N = p->desc.grid_n, beta = p->desc.oversample;
+    cudaError_t e = dmalloc(&p->d_z, (size_t)(beta / 2) * sz);
+    if (e == cudaSuccess) e = dmalloc(&p->d_hpr, (size_t)N);
+    if (e == cudaSuccess) e = dmalloc(&p->d_hprf, (size_t)N);
+    if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating the pruner");
+    e = build_prune(sz, beta, N, p->d_z, p->d_hpr, p->d_hprf, s);
+    if (e != cudaSuccess) return cuda_fail(e, "building the pruner");
+    p->hy_sz = sz;
+    return GW_OK;
+}
+
+gw_status gw_hybrid_grid(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
+                         int32_t nchan, const void* vis, const float* weight, int32_t sz,
+                         void* fine, int64_t* n_dropped, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
+    if (st != GW_OK) return st;
+    st = hybrid_checks(p, sz);
+    if (st != GW_OK) return st;
+    if (!fine) return fail(GW_EINVAL, "null fine grid");
+    if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
+    const int vk = p->desc.vis_dtype;
+    const size_t vb = dtype_bytes(vk);
+    if ((reinterpret_cast<uintptr_t>(fine) % 8 != 0) || (reinterpret_cast<uintptr_t>(vis) % vb != 0))
+        return fail(GW_EINVAL, "fine must be 8-byte aligned and vis aligned to its element size");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const int npol = p->desc.npol;
+    const int64_t rpc = rows_per_chunk(p, nchan);
+    for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
+        const int64_t nr = std::min(rpc, nrow - r0);
+        const int64_t v0 = r0 * nchan;
+        {
+            StageTimer t(p, kStIndex, s);
+            launch_index(uvw_m + 3 * r0, freq_hz, nr, nchan, p->ip, p->sc.rec, p->sc.dropped, s);
+        }
+        {
+            StageTimer t(p, kStGrid, s);
+            launch_hybrid_grid(p->sc.rec, nr * nchan, static_cast<const char*>(vis) + v0 * npol * vb,
+                               vk, weight ? weight + v0 * npol : nullptr, npol,
+                               p->desc.oversample, p->support[0], p->d_c1, p->c1_fmin,
+                               p->c1_norm, p->desc.grid_n, sz, reinterpret_cast<float2*>(fine),
+                               p->sc.dropped, s);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "hybrid grid launch");
+    }
+    return finish_dropped(p, n_dropped, s);
+}
+
+gw_status gw_hybrid_prune(gw_plan p, int32_t sz, const void* fine, void* pruned,
+                          void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    st = hybrid_checks(p, sz);
+    if (st != GW_OK) return st;
+    if (!fine || !pruned) return fail(GW_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    st = ensure_prune(p, sz, s);
+    if (st != GW_OK) return st;
+    launch_prune(reinterpret_cast<const float2*>(fine), p->desc.npol, p->desc.grid_n,
+                 p->desc.oversample, sz, p->d_z, reinterpret_cast<float2*>(pruned), s);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "prune launch");
+}
+
+gw_status gw_hybrid_shift(gw_plan p, void* pruned, void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    if (!pruned) return fail(GW_EINVAL, "null argument");
+    launch_hybrid_shift(reinterpret_cast<float2*>(pruned), p->desc.npol, p->desc.grid_n,
+                        (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "hybrid shift launch");
+}
+
+gw_status gw_hybrid_image(gw_plan p, int32_t sz, const void* raw, void* image, void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    st = hybrid_checks(p, sz);
+    if (st != GW_OK) return st;
+    if (!raw || !image) return fail(GW_EINVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    st = ensure_prune(p, sz, s);
+    if (st != GW_OK) return st;
+    launch_hybrid_image(reinterpret_cast<const float2*>(raw), p->desc.npol, p->desc.grid_n,
+                        p->d_hf, p->d_hprf, reinterpret_cast<float2*>(image), s);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "hybrid image launch");
 }
 
 gw_status gw_grid_fold(gw_plan p, void* grid, void* grid_err, void* cuda_stream) {

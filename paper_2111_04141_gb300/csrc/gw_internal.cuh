@@ -176,7 +176,14 @@ struct TableBuild {
 // w = 0, o = 0 centre tap) in [2^14, 2^15) so no entry overflows and small
 // ones stay clear of the subnormal range.
 cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_table16, int kind16,
-                         double* d_h, float* d_hf, double* h_scale, int* h_exp2, cudaStream_t s);
+                         double* d_h, float* d_hf, double* h_scale, int* h_exp2, double* d_c1,
+                         cudaStream_t s);
+// d_c1 (optional, beta * support[0] doubles): the unnormalised 1-D w = 0
+// kernel C(f / beta) at fine offsets f = fmin .. fmin + F - 1, fmin = -beta h - beta/2 + 1.
+// Hybrid pruner (Section 2.4): Z table [beta/2][sz] (float) and the pruning
+// corrector h_pr [N] (FP64 and FP32).  Synchronous.
+cudaError_t build_prune(int sz, int beta, int N, float* d_z, double* d_hpr, float* d_hprf,
+                        cudaStream_t s);
 int quad_nodes(double field, double w, int support, int smin);
 
 // ---- gridding / degridding (gw_grid.cu, gw_degrid.cu) -----------------------
@@ -262,6 +269,17 @@ void launch_compress(const gw_index_rec* rec, int64_t nvis, const void* vis, int
                      const float* weight, int npol, int beta, CompressScratch& cs,
                      cudaStream_t s);
 void clear_compress_table(CompressScratch& cs, int npol, cudaStream_t s);
+
+// ---- hybrid gridding (gw_hybrid.cu) ------------------------------------------
+void launch_hybrid_grid(const gw_index_rec* rec, int64_t nvis, const void* vis, int vis_kind,
+                        const float* weight, int npol, int beta, int S, const double* c1,
+                        int fmin, double norm, int N, int sz, float2* fine,
+                        unsigned long long* dropped, cudaStream_t s);
+void launch_prune(const float2* fine, int npol, int N, int beta, int sz, const float* z,
+                  float2* pruned, cudaStream_t s);
+void launch_hybrid_shift(float2* g, int npol, int N, cudaStream_t s);
+void launch_hybrid_image(const float2* raw, int npol, int N, const float* hco, const float* hpr,
+                         float2* image, cudaStream_t s);
 
 // ---- allocation-free scratch (gw_noalloc.cu) ------------------------------
 // View of the file-scope static scratch on `device` (current); looks up the

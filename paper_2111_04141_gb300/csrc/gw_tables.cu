@@ -363,7 +363,8 @@ __global__ void k_corrector(int N, int F, int fmin, int beta, int h0,
 }  // namespace
 
 cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_table16, int kind16,
-                         double* d_h, float* d_hf, double* h_scale, int* h_exp2, cudaStream_t s) {
+                         double* d_h, float* d_hf, double* h_scale, int* h_exp2, double* d_c1,
+                         cudaStream_t s) {
     const double c = M_PI * tb.smin / 2.0;
     const int K = (int)std::ceil(0.5 * c) + 40;
     if (K > kMaxTerms) return cudaErrorInvalidValue;
@@ -422,6 +423,8 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_tabl
                 k_c1<<<(F + 127) / 128, 128, 0, s>>>(F, fmin, beta, Qh, th, tw, C1);
                 k_corrector<<<(tb.N + 127) / 128, 128, 0, s>>>(tb.N, F, fmin, beta, h, C1, d_h, d_hf);
                 note_launch(3);
+                if (d_c1)   // the 1-D w = 0 kernel on the fine offsets, kept for hybrid gridding
+                    GW_TRY(cudaMemcpyAsync(d_c1, C1, sizeof(double) * F, cudaMemcpyDeviceToDevice, s));
                 if (d_table16 && kind16 == GW_F16X2) {
                     // storage exponent from the largest entry: peak * 2^exp2 in [2^14, 2^15)
                     double sp[2];
@@ -449,6 +452,85 @@ done:
 #undef GW_TRY
     cudaFree(coef); cudaFree(chi); cudaFree(th); cudaFree(wm); cudaFree(tw); cudaFree(Cm);
     cudaFree(A); cudaFree(Bt); cudaFree(Kf); cudaFree(Kf0); cudaFree(scale); cudaFree(C1);
+    return err;
+}
+
+namespace {
+
+// Z table of the hybrid pruner: psi_0(c_z, x) at x = (t - o/beta) 2/sz for
+// even o in [-beta/2, beta/2) and |t| <= hz, normalised by the sum of its
+// zero-offset taps (psi at x = 2t/sz).
+__global__ void k_prune_points(int beta, int sz, double* __restrict__ x) {
+    const int hz = (sz - 1) / 2, no = beta / 2;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < no * sz) {
+        const int row = e / sz, t = e % sz - hz;
+        const int o = 2 * row - beta / 2;
+        const double v = (t - (double)o / beta) * 2.0 / sz;
+        x[e] = fmin(1.0, fmax(-1.0, v));
+    } else if (e < no * sz + sz) {
+        const int t = e - no * sz - hz;
+        x[e] = t * 2.0 / sz;
+    }
+}
+
+__global__ void k_prune_finish(int beta, int sz, int N, const double* __restrict__ psi,
+                               float* __restrict__ z, double* __restrict__ hd,
+                               float* __restrict__ hf) {
+    const int hz = (sz - 1) / 2, no = beta / 2;
+    double norm = 0.0;
+    for (int t = 0; t < sz; ++t) norm += psi[no * sz + t];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < no * sz) z[i] = (float)(psi[i] / norm);
+    if (i >= N) return;
+    // realised transform of Z averaged over the beta/2 offsets, and the
+    // nearest-neighbour factor of the beta-fine v rows
+    const double x = (double)(i - N / 2) / (double)N;
+    double zh = 0.0;
+    for (int e = 0; e < no * sz; ++e) {
+        const int row = e / sz, t = e % sz - hz;
+        const double d = t - (double)(2 * row - beta / 2) / beta;
+        zh += psi[e] / norm * cospi(d * x);
+    }
+    zh *= 2.0 / beta;
+    const double a = x / beta;
+    const double sinc = (a == 0.0) ? 1.0 : sinpi(a) / (M_PI * a);
+    const double hv = 1.0 / (zh * sinc);
+    hd[i] = hv;
+    hf[i] = (float)hv;
+}
+
+}  // namespace
+
+cudaError_t build_prune(int sz, int beta, int N, float* d_z, double* d_hpr, float* d_hprf,
+                        cudaStream_t s) {
+    const double c = M_PI * sz / 2.0;
+    const int K = (int)std::ceil(0.5 * c) + 40;
+    if (K > kMaxTerms) return cudaErrorInvalidValue;
+    const int np = (beta / 2) * sz + sz;
+    double *coef = nullptr, *chi = nullptr, *x = nullptr, *ones = nullptr, *psi = nullptr;
+    cudaError_t err = cudaSuccess;
+#define GW_TRY(x_) do { err = (x_); if (err != cudaSuccess) goto done; } while (0)
+    GW_TRY(cudaMalloc(&coef, sizeof(double) * K));
+    GW_TRY(cudaMalloc(&chi, sizeof(double)));
+    GW_TRY(cudaMalloc(&x, sizeof(double) * np));
+    GW_TRY(cudaMalloc(&ones, sizeof(double) * np));
+    GW_TRY(cudaMalloc(&psi, sizeof(double) * np));
+    {
+        std::vector<double> h1(np, 1.0);
+        GW_TRY(cudaMemcpyAsync(ones, h1.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+        k_pswf<<<1, 1, 0, s>>>(c, K, coef, chi);
+        k_prune_points<<<(np + 127) / 128, 128, 0, s>>>(beta, sz, x);
+        k_taper<<<(np + 127) / 128, 128, 0, s>>>(np, x, ones, coef, K, psi);
+        const int nf = std::max(N, (beta / 2) * sz);
+        k_prune_finish<<<(nf + 127) / 128, 128, 0, s>>>(beta, sz, N, psi, d_z, d_hpr, d_hprf);
+        note_launch(4);
+        GW_TRY(cudaGetLastError());
+        GW_TRY(cudaStreamSynchronize(s));
+    }
+done:
+#undef GW_TRY
+    cudaFree(coef); cudaFree(chi); cudaFree(x); cudaFree(ones); cudaFree(psi);
     return err;
 }
 

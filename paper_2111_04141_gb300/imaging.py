@@ -70,3 +70,19 @@ def dirty_image_wstack(plan, uvw, freq, vis, n_layers: int, w_min: float, w_max:
     if normalise:
         img /= max(float(uvw.shape[0] * freq.shape[0] - dropped), 1e-30)
     return img
+
+
+def dirty_image_hybrid(plan, uvw, freq, vis, sz: int = 15, normalise: bool = True,
+                       stream=None) -> torch.Tensor:
+    """Dirty image by Hybrid Gridding (Section 2.4, Algorithm (hybrid)) with a
+    2-D plan: Gridding Step onto beta N v-rows, column pruning to 2N rows,
+    inverse FFT of the 2N x N grid, central N rows corrected."""
+    fine, dropped = plan.hybrid_grid(uvw, freq, vis, sz, stream=stream, return_dropped=True)
+    pruned = plan.hybrid_prune(sz, fine, stream=stream)
+    del fine
+    plan.hybrid_shift(pruned, stream=stream)
+    raw = torch.fft.ifft2(pruned, norm="forward")
+    img = plan.hybrid_image(sz, raw, stream=stream)
+    if normalise:
+        img /= max(float(uvw.shape[0] * freq.shape[0] - dropped), 1e-30)
+    return img

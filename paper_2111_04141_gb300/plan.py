@@ -281,6 +281,55 @@ class Plan:
                   "gw_wstack_combine")
         return image
 
+    def hybrid_grid(self, uvw, freq, vis, sz, weight=None, out=None, stream=None,
+                    return_dropped=False):
+        """Hybrid Gridding Step onto the fine grid [npol, beta N, N]."""
+        nrow, nchan = self._coords(uvw, freq)
+        vis = self._vis_arg(vis, "vis", nrow, nchan)
+        if weight is not None:
+            _need(weight, "weight", torch.float32, self.device, (nrow, nchan, self.npol))
+        shape = (self.npol, self.desc.oversample * self.grid_n, self.grid_n)
+        if out is None:
+            out = torch.zeros(shape, dtype=torch.complex64, device=self.device)
+        _need(out, "fine", torch.complex64, self.device, shape)
+        nd = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_hybrid_grid(self._h, _ptr(uvw), _ptr(freq), nrow, nchan, _ptr(vis),
+                                           _ptr(weight), int(sz), _ptr(out),
+                                           ctypes.byref(nd) if return_dropped else None,
+                                           _stream_ptr(stream, self.device)), "gw_hybrid_grid")
+        return (out, int(nd.value)) if return_dropped else out
+
+    def hybrid_prune(self, sz, fine, out=None, stream=None):
+        shape = (self.npol, 2 * self.grid_n, self.grid_n)
+        _need(fine, "fine", torch.complex64, self.device,
+              (self.npol, self.desc.oversample * self.grid_n, self.grid_n))
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device=self.device)
+        _need(out, "pruned", torch.complex64, self.device, shape)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_hybrid_prune(self._h, int(sz), _ptr(fine), _ptr(out),
+                                            _stream_ptr(stream, self.device)), "gw_hybrid_prune")
+        return out
+
+    def hybrid_shift(self, pruned, stream=None):
+        _need(pruned, "pruned", torch.complex64, self.device,
+              (self.npol, 2 * self.grid_n, self.grid_n))
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_hybrid_shift(self._h, _ptr(pruned), _stream_ptr(stream, self.device)),
+                  "gw_hybrid_shift")
+        return pruned
+
+    def hybrid_image(self, sz, raw, out=None, stream=None):
+        _need(raw, "raw", torch.complex64, self.device, (self.npol, 2 * self.grid_n, self.grid_n))
+        if out is None:
+            out = self.new_grid()
+        _need(out, "image", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_hybrid_image(self._h, int(sz), _ptr(raw), _ptr(out),
+                                            _stream_ptr(stream, self.device)), "gw_hybrid_image")
+        return out
+
     def fold(self, grid, err, stream=None):
         """grid += err; err = 0 (ends a compensated gridding sequence)."""
         gshape = (self.npol, self.grid_n, self.grid_n)
