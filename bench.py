@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-stream measurement")
     ap.add_argument("--serving-jobs", type=int, default=256)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip compression, hybrid gridding and w-stacking measurements")
     ap.add_argument("--no-imaging", action="store_true",
                     help="skip the dirty-image pipeline and R(X) measurements")
     ap.add_argument("--no-precision", action="store_true",
@@ -300,6 +302,63 @@ def measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
                     "setup": "16 antennas, 3,840 vis, 128^2, support 7, oversampling 128"}}
 
 
+def measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
+    """The batch through the other gridding variants: full compression with
+    the w-projection plan; and with a 2-D plan (support 7, the same grid):
+    convolutional gridding, Hybrid Gridding (gridding + column pruning,
+    pruner support 15) and a 32-layer w-stacked dirty image."""
+    import torch
+    from paper_2111_04141_gb300.imaging import dirty_image, dirty_image_wstack
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n=steps):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    out = {}
+    g = plan.new_grid()
+    _, ncomp, _ = plan.grid_compressed(uvw, freq, vis, out=g)
+    out["compression"] = {"records_in": obs.nvis, "records_gridded": ncomp,
+                          "ratio": obs.nvis / max(ncomp, 1),
+                          "ms_per_step": timed(lambda: plan.grid_compressed(uvw, freq, vis,
+                                                                            out=g))}
+    kw = dict(obs.plan_kwargs())
+    kw.update(support_min=7, support_max=7, n_wplanes=1, w_max_lambda=0.0)
+    sz = 15
+    with gw.Plan(**kw) as p2:
+        g2 = p2.new_grid()
+        conv_ms = timed(lambda: p2.grid(uvw, freq, vis, out=g2))
+        fine = torch.zeros((obs.npol, obs.oversample * obs.grid_n, obs.grid_n),
+                           dtype=torch.complex64, device=dev)
+        pruned = torch.empty((obs.npol, 2 * obs.grid_n, obs.grid_n), dtype=torch.complex64,
+                             device=dev)
+        hy_grid_ms = timed(lambda: p2.hybrid_grid(uvw, freq, vis, sz, out=fine))
+        hy_prune_ms = timed(lambda: p2.hybrid_prune(sz, fine, out=pruned))
+        del fine, pruned
+        torch.cuda.empty_cache()
+        upd = obs.nvis * obs.npol
+        out["2d_support7"] = {
+            "convolutional_grid_ms": conv_ms,
+            "convolutional_updates_per_s": upd * 49 / (conv_ms * 1e-3),
+            "hybrid_grid_ms": hy_grid_ms, "hybrid_prune_ms": hy_prune_ms,
+            "hybrid_speedup_grid_only": conv_ms / hy_grid_ms,
+            "hybrid_speedup_with_prune": conv_ms / (hy_grid_ms + hy_prune_ms),
+            "pruner_support": sz}
+        wmax = obs.w_max_lambda
+        ws_ms = timed(lambda: dirty_image_wstack(p2, uvw, freq, vis, 32, -wmax, wmax), n=2)
+        torch.cuda.empty_cache()
+    wp_ms = timed(lambda: dirty_image(plan, uvw, freq, vis), n=2)
+    out["wstack_vs_wproj_dirty_image_ms"] = {"wstack_32_layers_support7": ws_ms,
+                                             "wproj_32_planes_support7to63": wp_ms}
+    return out
+
+
 def measure_serving(args, dev):
     """Mixed grid/degrid stream (256 jobs, 8 setups with 1024^2-8192^2 grids,
     support 7-63, 1 or 4 pols, 1e4-1e7 visibilities log-uniform, sorted or
@@ -537,6 +596,8 @@ def main():
 
     imaging = measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
         if not args.no_imaging else None
+    variants = measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, 3) \
+        if not args.no_variants else None
     serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
 
     cpu = None
@@ -565,6 +626,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "degrid": degrid, "precision": precision, "imaging": imaging,
+            "variants": variants,
             "serving": serving,
         }
         print(json.dumps(line))
