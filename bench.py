@@ -590,7 +590,10 @@ def main():
               "achieved_tflops": dg["taps"] / nd * npol * FLOP_PER_UPDATE /
                                  (dg["degrid_ms"] / max(1, dg["degrid_calls"]) * 1e-3) / 1e12}
 
-    # ---- storage precision and compensated commits on the same batch -------
+    # ---- serving stream first (its latencies are sensitive to what the
+    # process allocated before), then the other measurements on the batch
+    serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
+    torch.cuda.empty_cache()
     precision = measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
         if not args.no_precision else None
 
@@ -598,7 +601,6 @@ def main():
         if not args.no_imaging else None
     variants = measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, 3) \
         if not args.no_variants else None
-    serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -254,7 +254,8 @@ gw_status gw_wstack_combine(gw_plan plan, const void* layer_images, int32_t n_la
                             void* cuda_stream);
 
 /* Hybrid Gridding with a column pruner (Section 2.4, Algorithm (hybrid)),
- * for 2-D plans (n_wplanes == 1, grid_n % 4 == 0).  Four steps:
+ * for 2-D plans (n_wplanes == 1, grid_n % 4 == 0, oversample % 4 == 0).
+ * Four steps:
  *   gw_hybrid_grid   Gridding Step: each visibility is convolved along u with
  *                    the plan's oversampled 1-D GCF (support_min taps) and
  *                    put on the nearest of beta*N rows along v:

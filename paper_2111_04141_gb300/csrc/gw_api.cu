@@ -918,6 +918,8 @@ static gw_status hybrid_checks(gw_plan p, int32_t sz) {
     if (p->desc.n_wplanes != 1) return fail(GW_EINVAL, "hybrid gridding needs a 2-D plan");
     if (sz < 1 || !(sz & 1) || sz > 127) return fail(GW_EINVAL, "sz must be odd in [1, 127]");
     if (p->desc.grid_n % 4 != 0) return fail(GW_EINVAL, "hybrid gridding needs grid_n % 4 == 0");
+    if (p->desc.oversample % 4 != 0)
+        return fail(GW_EINVAL, "hybrid gridding needs oversample % 4 == 0");
     if ((int64_t)p->desc.oversample * p->desc.grid_n >= ((int64_t)1 << 31))
         return fail(GW_EINVAL, "oversample * grid_n too large");
     return GW_OK;

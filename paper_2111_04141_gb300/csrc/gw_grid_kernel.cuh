@@ -85,11 +85,82 @@ template <int NPOL, int B>
 struct Smem {
     int rec[B][kBatch];                    // padded-table index of the tile origin for the record
     float4 v[B][kBatch][NPOL];             // (A.re, A.im, B.re, B.im) per polarisation
-    uint32_t list[B][kComputeWarps][kBatch];  // r | j0 << 16 | j1 << 20
-    int cnt[B][kComputeWarps];
+    // per warp: entries meeting all four slots from the front, the others
+    // (r | j0 << 16 | j1 << 20) from the back
+    uint32_t list[B][kComputeWarps][kBatch];
+    int cnt[B][kComputeWarps];             // entries meeting all four slots
+    int cntp[B][kComputeWarps];            // entries meeting some slots
     int tile[B];                           // tile of the batch; -1 = end of work
     int last[B];                           // batch ends its work item
 };
+
+// One warp's pass over n list entries of a batch.  Software pipeline: the
+// kernel values of entry i + 1 load while entry i's FMAs run (a ring of D
+// register sets, unrolled so no register copies are needed).  FULL: every
+// entry meets all four slots of the warp's block (no per-slot tests).
+template <int NPOL, int SP, int D, bool FULL, class TE>
+__device__ __forceinline__ void run_entries(const uint32_t* lst, int n, const int* rec,
+                                            const float4 (*vs)[NPOL],
+                                            const typename TE::T* __restrict__ tab,
+                                            float2 (&acc)[4][NPOL]) {
+    float2 Kr[D][4];
+    uint32_t er[D];
+    auto load_k = [&](uint32_t e, float2 (&K)[4]) {
+        const typename TE::T* p_ = tab + rec[e & 0xffff];
+        if (FULL) {
+            K[0] = TE::load(p_);
+            K[1] = TE::load(p_ + 4 * SP);
+            K[2] = TE::load(p_ + 8 * SP);
+            K[3] = TE::load(p_ + 12 * SP);
+        } else {
+            const int j0_ = (e >> 16) & 15, j1_ = (e >> 20) & 15;
+            K[0] = K[1] = K[2] = K[3] = make_float2(0.f, 0.f);
+            if (0 >= j0_ && 0 <= j1_) K[0] = TE::load(p_);
+            if (1 >= j0_ && 1 <= j1_) K[1] = TE::load(p_ + 4 * SP);
+            if (2 >= j0_ && 2 <= j1_) K[2] = TE::load(p_ + 8 * SP);
+            if (3 >= j0_ && 3 <= j1_) K[3] = TE::load(p_ + 12 * SP);
+        }
+    };
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        er[d] = 0;
+        Kr[d][0] = Kr[d][1] = Kr[d][2] = Kr[d][3] = make_float2(0.f, 0.f);
+        if (d < n) {
+            er[d] = lst[d];
+            load_k(er[d], Kr[d]);
+        }
+    }
+    for (int i = 0; i < n; i += D) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (i + d < n) {
+                const uint32_t ec = er[d];
+                const float2 Kc[4] = {Kr[d][0], Kr[d][1], Kr[d][2], Kr[d][3]};
+                if (i + d + D < n) {
+                    er[d] = lst[i + d + D];
+                    load_k(er[d], Kr[d]);
+                }
+                const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
+                float4 V[NPOL];
+#pragma unroll
+                for (int p = 0; p < NPOL; ++p) V[p] = vs[r][p];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (FULL || (j >= j0 && j <= j1)) {
+                        // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
+                        const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
+                        const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+#pragma unroll
+                        for (int p = 0; p < NPOL; ++p) {
+                            acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
+                            acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
 
 // Named barriers: FULL(b) = 1 + b (batch b staged), EMPTY(b) = 1 + B + b (consumed).
 template <int NPOL, int SP, int TK, int D, int B>
@@ -116,7 +187,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
                 if (uses >= kBufs) bar_sync(1 + kBufs + buf, kThreads);  // wait until consumed
-                if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
+                if (lane < kComputeWarps) {
+                    sm.cnt[buf][lane] = 0;
+                    sm.cntp[buf][lane] = 0;
+                }
                 __syncwarp();
                 if (done) {
                     if (lane == 0) {
@@ -164,10 +238,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                             const int j0 = max(0, vlo - 16 * cv) >> 2;
                             const int j1 = min(15, vhi - 16 * cv) >> 2;
                             const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
+                            const bool full = j0 == 0 && j1 == 3;
                             for (int cu = cu0; cu <= cu1; ++cu) {
                                 const int w = cv * 4 + cu;
-                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
-                                sm.list[buf][w][pos] = e;
+                                if (full) {
+                                    const int pos = atomicAdd(&sm.cnt[buf][w], 1);
+                                    sm.list[buf][w][pos] = e;
+                                } else {
+                                    const int pos = atomicAdd(&sm.cntp[buf][w], 1);
+                                    sm.list[buf][w][kBatch - 1 - pos] = e;
+                                }
                             }
                         }
                     }
@@ -212,65 +292,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
         const int tile = sm.tile[buf];
         if (tile < 0) break;
         const int last = sm.last[buf];
-        const int n = sm.cnt[buf][warp];
+        const int nf = sm.cnt[buf][warp], np = sm.cntp[buf][warp];
         const uint32_t* lst = sm.list[buf][warp];
-
-        // software pipeline: kernel values of entries i+1 .. i+D-1 are in
-        // flight while entry i's FMAs run (a ring of D register sets)
-#define GW_LOAD_K(e, K)                                                                \
-        do {                                                                          \
-            const int r_ = (e) & 0xffff, j0_ = ((e) >> 16) & 15, j1_ = ((e) >> 20) & 15; \
-            const typename TE::T* p_ = tab + sm.rec[buf][r_];                          \
-            K[0] = K[1] = K[2] = K[3] = make_float2(0.f, 0.f);                         \
-            if (0 >= j0_ && 0 <= j1_) K[0] = TE::load(p_);                             \
-            if (1 >= j0_ && 1 <= j1_) K[1] = TE::load(p_ + 4 * SP);                    \
-            if (2 >= j0_ && 2 <= j1_) K[2] = TE::load(p_ + 8 * SP);                    \
-            if (3 >= j0_ && 3 <= j1_) K[3] = TE::load(p_ + 12 * SP);                   \
-        } while (0)
-        float2 Kr[D][4];
-        uint32_t er[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            er[d] = 0;
-            Kr[d][0] = Kr[d][1] = Kr[d][2] = Kr[d][3] = make_float2(0.f, 0.f);
-            if (d < n) {
-                er[d] = lst[d];
-                GW_LOAD_K(er[d], Kr[d]);
-            }
-        }
-        for (int i = 0; i < n; i += D) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                if (i + d < n) {
-                    const uint32_t ec = er[d];
-                    const float2 Kc[4] = {Kr[d][0], Kr[d][1], Kr[d][2], Kr[d][3]};
-                    if (i + d + D < n) {
-                        er[d] = lst[i + d + D];
-                        GW_LOAD_K(er[d], Kr[d]);
-                    }
-                    const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
-                    float4 V[NPOL];
-#pragma unroll
-                    for (int p = 0; p < NPOL; ++p) V[p] = sm.v[buf][r][p];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (j >= j0 && j <= j1) {
-                            // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
-                            const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
-                            const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
-#pragma unroll
-                            for (int p = 0; p < NPOL; ++p) {
-                                acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y),
-                                                       acc[j][p]);
-                                acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w),
-                                                       acc[j][p]);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-#undef GW_LOAD_K
+        // entries meeting all four slots: no per-slot tests
+        run_entries<NPOL, SP, D, true, TE>(lst, nf, sm.rec[buf], sm.v[buf], tab, acc);
+        // entries meeting a subset of the slots
+        run_entries<NPOL, SP, D, false, TE>(lst + kBatch - np, np, sm.rec[buf], sm.v[buf], tab,
+                                            acc);
         if (last) {
             // commit the tile's accumulators of this work item
             const int ltile = a.layer_tiles ? tile % a.layer_tiles : tile;

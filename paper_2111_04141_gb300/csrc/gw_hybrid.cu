@@ -59,11 +59,14 @@ __global__ void k_hybrid_grid(const gw_index_rec* __restrict__ rec, int64_t nvis
     }
 }
 
-// One thread per (pol, output row k, column u): the fine rows whose nearest
-// 2x-grid row k0 lies within hz of k, weighted by Z at their offset.
+// The fine rows with nearest 2x row k' are r = k' beta/2 - beta/4 + m,
+// m = 0 .. beta/2 - 1 (beta % 4 == 0), at offset row m of the Z table; an
+// output row k gathers them for k' = k - t, |t| <= hz, with weight Z[m][t + hz].
+
+// One thread per (pol, output row k, column u), reading the fine grid.
 __global__ void k_prune(const float2* __restrict__ fine, int npol, int N, int beta, int sz,
                         const float* __restrict__ z, float2* __restrict__ pruned) {
-    const int hz = sz / 2;
+    const int hz = sz / 2, hb = beta / 2;
     const int64_t rows2 = 2LL * N, fr = (int64_t)beta * N;
     const int64_t total = (int64_t)npol * rows2 * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -72,24 +75,75 @@ __global__ void k_prune(const float2* __restrict__ fine, int npol, int N, int be
         const int64_t pk = e / N;
         const int k = (int)(pk % rows2);
         const int p = (int)(pk / rows2);
-        // 2r in [(k - hz) beta - beta/2, (k + hz) beta + beta/2)
-        const long long lo2 = (long long)(k - hz) * beta - beta / 2;
-        const long long hi2 = (long long)(k + hz) * beta + beta / 2;
-        long long r0 = (lo2 + 1) >> 1;                       // ceil(lo2 / 2)
-        long long r1 = (hi2 + 1) >> 1;                       // ceil(hi2 / 2), exclusive
-        if (r0 < 0) r0 = 0;
-        if (r1 > fr) r1 = fr;
-        float ax = 0.f, ay = 0.f;
         const float2* col = fine + (int64_t)p * fr * N + u;
-        for (long long r = r0; r < r1; ++r) {
-            const long long k0 = floor_div(2 * r + beta / 2, beta);
-            const int o = (int)(2 * r - k0 * beta);
-            const float wz = __ldg(z + ((o + beta / 2) / 2) * sz + (k - (int)k0) + hz);
-            const float2 f = col[r * N];
-            ax = fmaf(wz, f.x, ax);
-            ay = fmaf(wz, f.y, ay);
+        float ax = 0.f, ay = 0.f;
+        for (int t = -hz; t <= hz; ++t) {
+            const int64_t rs = (int64_t)(k - t) * hb - beta / 4;
+            const int m0 = rs < 0 ? (int)(-rs) : 0;
+            const int m1 = rs + hb > fr ? (int)(fr - rs) : hb;
+            for (int m = m0; m < m1; ++m) {
+                const float wz = __ldg(z + m * sz + t + hz);
+                const float2 f = col[(rs + m) * N];
+                ax = fmaf(wz, f.x, ax);
+                ay = fmaf(wz, f.y, ay);
+            }
         }
         pruned[e] = make_float2(ax, ay);
+    }
+}
+
+// Tiled pruner: a CTA produces R output rows x 32 columns of one
+// polarisation; the fine rows they need ((R + 2 hz + 1) beta / 2 of them) and
+// the Z table are staged in shared memory once, so the fine grid is read
+// from memory about once instead of once per output row.
+constexpr int kPruneCols = 32;
+constexpr int kPruneRowsMax = 384;          // staged fine rows (96 KB of float2 x 32 columns)
+constexpr int kPruneZMax = 4096;            // staged Z entries (beta/2 * sz)
+
+__global__ void __launch_bounds__(256) k_prune_tiled(const float2* __restrict__ fine, int N,
+                                                    int beta, int sz, int R,
+                                                    const float* __restrict__ z,
+                                                    float2* __restrict__ pruned) {
+    extern __shared__ __align__(16) float2 tilebuf[];      // [rows][kPruneCols], then Z
+    const int hz = sz / 2, hb = beta / 2;
+    const int u0 = blockIdx.x * kPruneCols;
+    const int kstart = blockIdx.y * R;
+    const int p = blockIdx.z;
+    const int64_t fr = (int64_t)beta * N;
+    int64_t r_lo = (int64_t)(kstart - hz) * hb - beta / 4;
+    int64_t r_hi = (int64_t)(kstart + R - 1 + hz) * hb - beta / 4 + hb;
+    if (r_lo < 0) r_lo = 0;
+    if (r_hi > fr) r_hi = fr;
+    const int nrows = (int)(r_hi - r_lo);                  // <= kPruneRowsMax by the launch
+    float* zs = reinterpret_cast<float*>(tilebuf + kPruneRowsMax * kPruneCols);
+    for (int e = threadIdx.x; e < hb * sz; e += blockDim.x) zs[e] = z[e];
+    const float2* src = fine + (int64_t)p * fr * N;
+    for (int e = threadIdx.x; e < nrows * kPruneCols; e += blockDim.x) {
+        const int rr = e / kPruneCols, c = e - rr * kPruneCols;
+        const int u = u0 + c;
+        tilebuf[e] = u < N ? src[(r_lo + rr) * (int64_t)N + u] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int c = threadIdx.x % kPruneCols;
+    const int u = u0 + c;
+    for (int kk = threadIdx.x / kPruneCols; kk < R; kk += blockDim.x / kPruneCols) {
+        const int k = kstart + kk;
+        if (k >= 2 * N || u >= N) continue;
+        float ax = 0.f, ay = 0.f;
+        for (int t = -hz; t <= hz; ++t) {
+            const int64_t rs = (int64_t)(k - t) * hb - beta / 4;     // first row of k' = k - t
+            const int m0 = rs < r_lo ? (int)(r_lo - rs) : 0;
+            const int m1 = rs + hb > r_hi ? (int)(r_hi - rs) : hb;
+            const float2* f = tilebuf + (rs - r_lo) * kPruneCols + c;
+            const float* zt = zs + t + hz;
+            for (int m = m0; m < m1; ++m) {
+                const float wz = zt[m * sz];
+                const float2 fv = f[m * kPruneCols];
+                ax = fmaf(wz, fv.x, ax);
+                ay = fmaf(wz, fv.y, ay);
+            }
+        }
+        pruned[((int64_t)p * 2 * N + k) * N + u] = make_float2(ax, ay);
     }
 }
 
@@ -140,8 +194,21 @@ void launch_hybrid_grid(const gw_index_rec* rec, int64_t nvis, const void* vis, 
 
 void launch_prune(const float2* fine, int npol, int N, int beta, int sz, const float* z,
                   float2* pruned, cudaStream_t s) {
-    k_prune<<<blocks_for((int64_t)npol * 2 * N * N), 256, 0, s>>>(fine, npol, N, beta, sz, z,
-                                                                 pruned);
+    // largest power-of-two row block whose fine-row window fits the tile
+    int R = 128;
+    while (R >= 8 && ((int64_t)(R + sz) * beta / 2 + 2 > kPruneRowsMax)) R >>= 1;
+    if (R >= 8 && (beta / 2) * sz <= kPruneZMax && npol <= 65535 &&
+        (2LL * N + R - 1) / R <= 65535) {
+        const size_t smem = sizeof(float2) * kPruneRowsMax * kPruneCols + sizeof(float) * kPruneZMax;
+        cudaFuncSetAttribute(k_prune_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        const dim3 grid((N + kPruneCols - 1) / kPruneCols, (unsigned)((2LL * N + R - 1) / R),
+                        (unsigned)npol);
+        k_prune_tiled<<<grid, 256, smem, s>>>(fine, N, beta, sz, R, z, pruned);
+    } else {
+        k_prune<<<blocks_for((int64_t)npol * 2 * N * N), 256, 0, s>>>(fine, npol, N, beta, sz, z,
+                                                                     pruned);
+    }
     note_launch();
 }
 
