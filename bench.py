@@ -541,15 +541,13 @@ def main():
     pin_freq = torch.from_numpy(obs.freq_hz).pin_memory()
     pin_vis = torch.from_numpy(obs.vis).pin_memory()
     pin_out = torch.empty(grid.shape, dtype=grid.dtype).pin_memory()
-    d_uvw, d_freq, d_vis = torch.empty_like(uvw), torch.empty_like(freq), torch.empty_like(vis)
     ne = max(1, args.e2e_steps)
 
     def e2e_step():
-        d_uvw.copy_(pin_uvw, non_blocking=True)
-        d_freq.copy_(pin_freq, non_blocking=True)
-        d_vis.copy_(pin_vis, non_blocking=True)
+        # public API from host buffers: gw_grid_vis_host pipelines the
+        # host-to-device copies of uvw / vis with the gridding of earlier rows
         grid.zero_()
-        plan.grid(d_uvw, d_freq, d_vis, out=grid)
+        plan.grid_host(pin_uvw, pin_freq, pin_vis, out=grid)
         pin_out.copy_(grid, non_blocking=True)
 
     e2e_step()

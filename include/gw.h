@@ -194,6 +194,19 @@ gw_status gw_grid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz, 
                       int32_t nchan, const void* vis, const float* weight, void* grid,
                       int64_t* n_dropped, void* cuda_stream);
 
+/* gw_grid_vis from HOST inputs (no thesis counterpart): uvw_h, freq_h,
+ * vis_h and weight_h (optional) are host arrays with the layouts of
+ * gw_grid_vis; grid is on the device.  The rows are processed in steps
+ * whose host-to-device copies run on the plan's own copy stream while the
+ * previous step is gridded on `cuda_stream` (two device staging sets, events
+ * between the streams).  Host arrays should be page-locked for the copies
+ * to overlap; the caller must keep them unchanged until the stream reaches
+ * the end of the call.  The first call allocates the staging (grown on
+ * demand).  Errors: as gw_grid_vis, and GW_ENOMEM. */
+gw_status gw_grid_vis_host(gw_plan plan, const double* uvw_h, const double* freq_h, int64_t nrow,
+                           int32_t nchan, const void* vis_h, const float* weight_h, void* grid,
+                           int64_t* n_dropped, void* cuda_stream);
+
 /* Gridding with compensated commits (the Kahan-style variant of
  * gw_grid_vis; same arguments plus grid_err).  Each grid point's partial
  * sum over a work item is committed with an atomic add that returns the

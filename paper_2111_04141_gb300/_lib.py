@@ -65,6 +65,8 @@ _SIGS = {
     "gw_grid_vis_compensated": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
                                         ctypes.POINTER(c_i64), c_vp]),
     "gw_grid_fold": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "gw_grid_vis_host": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp,
+                                 ctypes.POINTER(c_i64), c_vp]),
     "gw_hybrid_grid": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_i32, c_vp,
                                ctypes.POINTER(c_i64), c_vp]),
     "gw_hybrid_prune": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),

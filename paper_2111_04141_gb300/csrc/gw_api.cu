@@ -78,6 +78,14 @@ struct gw_plan_s {
     double* d_c1 = nullptr;
     int c1_fmin = 0;
     double c1_norm = 1.0;
+    // host-input pipeline (gw_grid_vis_host): a copy stream, two staging sets
+    cudaStream_t h_copy = nullptr;
+    cudaEvent_t h_ready[2] = {nullptr, nullptr}, h_free[2] = {nullptr, nullptr};
+    double* h_uvw[2] = {nullptr, nullptr};
+    void* h_vis[2] = {nullptr, nullptr};
+    float* h_wt[2] = {nullptr, nullptr};
+    double* h_freq = nullptr;
+    int64_t h_rows = 0, h_freq_n = 0;
     int hy_sz = 0;
     float* d_z = nullptr;
     double* d_hpr = nullptr;
@@ -135,6 +143,15 @@ void plan_free(gw_plan p) {
     cudaFree(p->ws_cursor);
     cudaFree(p->ws_item_off);
     cudaFree(p->ws_items);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->h_uvw[b]);
+        cudaFree(p->h_vis[b]);
+        cudaFree(p->h_wt[b]);
+        if (p->h_ready[b]) cudaEventDestroy(p->h_ready[b]);
+        if (p->h_free[b]) cudaEventDestroy(p->h_free[b]);
+    }
+    cudaFree(p->h_freq);
+    if (p->h_copy) cudaStreamDestroy(p->h_copy);
     cudaFree(p->d_c1);
     cudaFree(p->d_z);
     cudaFree(p->d_hpr);
@@ -605,7 +622,8 @@ gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
 
 static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
                            int32_t nchan, const void* vis, const float* weight, void* grid,
-                           void* grid_err, int64_t* n_dropped, void* cuda_stream) {
+                           void* grid_err, int64_t* n_dropped, void* cuda_stream,
+                           bool reset_dropped = true) {
     gw_status st = common_checks(p, uvw_m, freq_hz, nrow, nchan);
     if (st != GW_OK) return st;
     if (!grid) return fail(GW_EINVAL, "null grid");
@@ -619,7 +637,8 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
     if (grid_err && reinterpret_cast<uintptr_t>(grid_err) % 8 != 0)
         return fail(GW_EINVAL, "grid_err must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    cudaError_t e = reset_dropped ? cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s)
+                                  : cudaSuccess;
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     const int npol = p->desc.npol;
     const int64_t rpc = rows_per_chunk(p, nchan);
@@ -678,6 +697,100 @@ gw_status gw_grid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, int
                       int64_t* n_dropped, void* cuda_stream) {
     return grid_impl(p, uvw_m, freq_hz, nrow, nchan, vis, weight, grid, nullptr, n_dropped,
                      cuda_stream);
+}
+
+// Staging for the host-input pipeline: two sets of `rows` rows.
+static gw_status ensure_host_pipe(gw_plan p, int64_t rows, int nchan) {
+    const int npol = p->desc.npol;
+    const size_t vb = dtype_bytes(p->desc.vis_dtype);
+    cudaError_t e = cudaSuccess;
+    if (!p->h_copy) {
+        e = cudaStreamCreateWithFlags(&p->h_copy, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&p->h_ready[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->h_free[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "creating the copy stream");
+    }
+    if (p->h_rows < rows || p->h_freq_n < nchan) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(p->h_uvw[b]);
+            cudaFree(p->h_vis[b]);
+            cudaFree(p->h_wt[b]);
+            p->h_uvw[b] = nullptr;
+            p->h_vis[b] = nullptr;
+            p->h_wt[b] = nullptr;
+        }
+        cudaFree(p->h_freq);
+        p->h_freq = nullptr;
+        p->h_rows = 0;
+        const int64_t r = std::max(rows, p->h_rows), c = std::max<int64_t>(nchan, p->h_freq_n);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMalloc(&p->h_uvw[b], sizeof(double) * 3 * r);
+            if (e == cudaSuccess) e = cudaMalloc(&p->h_vis[b], vb * r * c * npol);
+            if (e == cudaSuccess) e = cudaMalloc(&p->h_wt[b], sizeof(float) * r * c * npol);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&p->h_freq, sizeof(double) * c);
+        if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating host-pipeline staging");
+        p->h_rows = r;
+        p->h_freq_n = c;
+    }
+    return GW_OK;
+}
+
+gw_status gw_grid_vis_host(gw_plan p, const double* uvw_h, const double* freq_h, int64_t nrow,
+                           int32_t nchan, const void* vis_h, const float* weight_h, void* grid,
+                           int64_t* n_dropped, void* cuda_stream) {
+    gw_status st = common_checks(p, uvw_h, freq_h, nrow, nchan);
+    if (st != GW_OK) return st;
+    if (!grid) return fail(GW_EINVAL, "null grid");
+    if (nrow > 0 && nchan > 0 && !vis_h) return fail(GW_EINVAL, "null vis");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (nrow == 0 || nchan == 0) return finish_dropped(p, n_dropped, s);
+    const int npol = p->desc.npol;
+    const size_t vb = dtype_bytes(p->desc.vis_dtype);
+    // pipeline step: a quarter of the rows or the plan's chunk, whichever is smaller
+    int64_t rows = std::min(rows_per_chunk(p, nchan), (nrow + 3) / 4);
+    rows = std::max<int64_t>(rows, 1);
+    st = ensure_host_pipe(p, rows, nchan);
+    if (st != GW_OK) return st;
+    e = cudaMemcpyAsync(p->h_freq, freq_h, sizeof(double) * nchan, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copying frequencies");
+    // the copy stream may start only after the call's earlier work on s
+    e = cudaEventRecord(p->h_free[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(p->h_free[1], s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    int b = 0;
+    for (int64_t r0 = 0; r0 < nrow; r0 += rows, b ^= 1) {
+        const int64_t nr = std::min(rows, nrow - r0);
+        const int64_t nv = nr * nchan;
+        // copy stream: wait until set b is free, then copy the step's inputs
+        e = cudaStreamWaitEvent(p->h_copy, p->h_free[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->h_uvw[b], uvw_h + 3 * r0, sizeof(double) * 3 * nr,
+                                cudaMemcpyHostToDevice, p->h_copy);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->h_vis[b], static_cast<const char*>(vis_h) + vb * npol * r0 * nchan,
+                                vb * npol * nv, cudaMemcpyHostToDevice, p->h_copy);
+        if (e == cudaSuccess && weight_h)
+            e = cudaMemcpyAsync(p->h_wt[b], weight_h + (size_t)npol * r0 * nchan,
+                                sizeof(float) * npol * nv, cudaMemcpyHostToDevice, p->h_copy);
+        if (e == cudaSuccess) e = cudaEventRecord(p->h_ready[b], p->h_copy);
+        // compute stream: wait for the copies, grid the step, release set b
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->h_ready[b], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "host pipeline copy");
+        st = grid_impl(p, p->h_uvw[b], p->h_freq, nr, nchan, p->h_vis[b],
+                       weight_h ? p->h_wt[b] : nullptr, grid, nullptr, nullptr, s, false);
+        if (st != GW_OK) return st;
+        e = cudaEventRecord(p->h_free[b], s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    // the next call's copies must not overtake this call's last gridding
+    e = cudaStreamWaitEvent(p->h_copy, p->h_free[b ^ 1], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    return finish_dropped(p, n_dropped, s);
 }
 
 gw_status gw_grid_vis_compensated(gw_plan p, const double* uvw_m, const double* freq_hz,

@@ -330,6 +330,40 @@ class Plan:
                                             _stream_ptr(stream, self.device)), "gw_hybrid_image")
         return out
 
+    def grid_host(self, uvw, freq, vis, weight=None, out=None, stream=None,
+                  return_dropped=False):
+        """gw_grid_vis_host: uvw/freq/vis (and weight) are HOST tensors
+        (page-locked for overlap); their copies to the device are pipelined
+        with the gridding.  ``out`` is a device grid."""
+        def host(t, name, dtype):
+            if not isinstance(t, torch.Tensor) or t.device.type != "cpu" or t.dtype != dtype:
+                raise TypeError(f"{name} must be a host {dtype} tensor")
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+        host(uvw, "uvw", torch.float64)
+        host(freq, "freq", torch.float64)
+        nrow, nchan = int(uvw.shape[0]), int(freq.shape[0])
+        k = self.vis_dtype
+        vt = vis
+        if k == "f16" and vis.dtype == torch.complex32:
+            vt = torch.view_as_real(vis)
+        host(vt, "vis", _TORCH[k])
+        if tuple(vt.shape) != vis_shape(k, nrow, nchan, self.npol):
+            raise ValueError("vis has the wrong shape")
+        if weight is not None:
+            host(weight, "weight", torch.float32)
+        if out is None:
+            out = self.new_grid()
+        _need(out, "grid", torch.complex64, self.device, (self.npol, self.grid_n, self.grid_n))
+        nd = ctypes.c_int64(-1)
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_grid_vis_host(self._h, _ptr(uvw), _ptr(freq), nrow, nchan,
+                                             _ptr(vt), _ptr(weight), _ptr(out),
+                                             ctypes.byref(nd) if return_dropped else None,
+                                             _stream_ptr(stream, self.device)),
+                  "gw_grid_vis_host")
+        return (out, int(nd.value)) if return_dropped else out
+
     def fold(self, grid, err, stream=None):
         """grid += err; err = 0 (ends a compensated gridding sequence)."""
         gshape = (self.npol, self.grid_n, self.grid_n)

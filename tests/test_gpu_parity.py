@@ -302,3 +302,27 @@ def test_launch_count_increases(gw):
     with gw.Plan.from_observation(obs) as plan:
         plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis))
     assert gw.launch_count() > before
+
+
+def test_grid_from_host_inputs_matches_device_inputs(gw):
+    """gw_grid_vis_host (pipelined host-to-device copies) gives the grid of
+    gw_grid_vis on the same data, with and without weights, for ragged steps."""
+    obs = CASES["small-w"]()
+    wt = syn.random_weights(obs)
+    for nrow in (obs.nrow, 3, 1):
+        uvw, vis, w = obs.uvw_m[:nrow], obs.vis[:nrow], wt[:nrow]
+        with gw.Plan.from_observation(obs, max_vis_per_call=7 * obs.nchan) as plan:
+            ref, dref = plan.grid(dev(uvw), dev(obs.freq_hz), dev(vis), weight=dev(w),
+                                  return_dropped=True)
+            hu = torch.from_numpy(np.ascontiguousarray(uvw)).pin_memory()
+            hf = torch.from_numpy(obs.freq_hz).pin_memory()
+            hv = torch.from_numpy(np.ascontiguousarray(vis)).pin_memory()
+            hw = torch.from_numpy(np.ascontiguousarray(w)).pin_memory()
+            got, dgot = plan.grid_host(hu, hf, hv, weight=hw, return_dropped=True)
+            got2 = plan.grid_host(hu, hf, hv)
+            ref2 = plan.grid(dev(uvw), dev(obs.freq_hz), dev(vis))
+        assert dgot == dref
+        a, b = got.cpu().numpy().astype(np.complex128), ref.cpu().numpy().astype(np.complex128)
+        assert rel_l2(a, b) <= 1e-6
+        a, b = got2.cpu().numpy().astype(np.complex128), ref2.cpu().numpy().astype(np.complex128)
+        assert rel_l2(a, b) <= 1e-6
