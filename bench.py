@@ -40,8 +40,8 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
-GRID_TRAFFIC = {"sha256": "79742d88160e95f056fe985c4c2db419d1e05ed026e3677d48e0f8ab1bc9d9b0",
-                "bytes_per_launch": 1.014889e9 + 0.266981e9,
+GRID_TRAFFIC = {"sha256": "41ac9a99c32049682340a7883ca6648006a181b9a3c3367e41f8e84cbe31f04d",
+                "bytes_per_launch": 1.015117e9 + 0.266591e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
 
 

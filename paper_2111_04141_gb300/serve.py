@@ -348,6 +348,12 @@ class Server:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             body()
+        # one replay with no rows: the graph's first launch (upload to the
+        # device) happens here instead of in the first job that uses it
+        with torch.cuda.stream(stream):
+            st.d_nrow.zero_()
+            g.replay()
+        stream.synchronize()
         st.graphs[kind] = g
         return g
 
