@@ -97,10 +97,11 @@ __global__ void k_prune(const float2* __restrict__ fine, int npol, int N, int be
 // the Z table are staged in shared memory once, so the fine grid is read
 // from memory about once instead of once per output row.
 constexpr int kPruneCols = 32;
-constexpr int kPruneRowsMax = 384;          // staged fine rows (96 KB of float2 x 32 columns)
-constexpr int kPruneZMax = 4096;            // staged Z entries (beta/2 * sz)
+constexpr int kPruneRowsMax = 352;          // staged fine rows (88 KB of float2 x 32 columns)
+constexpr int kPruneZMax = 2048;            // staged Z entries (beta/2 * sz)
+constexpr int kPruneThreads = 512;          // two CTAs of 16 warps per SM
 
-__global__ void __launch_bounds__(256) k_prune_tiled(const float2* __restrict__ fine, int N,
+__global__ void __launch_bounds__(kPruneThreads) k_prune_tiled(const float2* __restrict__ fine, int N,
                                                     int beta, int sz, int R,
                                                     const float* __restrict__ z,
                                                     float2* __restrict__ pruned) {
@@ -204,7 +205,7 @@ void launch_prune(const float2* fine, int npol, int N, int beta, int sz, const f
                              (int)smem);
         const dim3 grid((N + kPruneCols - 1) / kPruneCols, (unsigned)((2LL * N + R - 1) / R),
                         (unsigned)npol);
-        k_prune_tiled<<<grid, 256, smem, s>>>(fine, N, beta, sz, R, z, pruned);
+        k_prune_tiled<<<grid, kPruneThreads, smem, s>>>(fine, N, beta, sz, R, z, pruned);
     } else {
         k_prune<<<blocks_for((int64_t)npol * 2 * N * N), 256, 0, s>>>(fine, npol, N, beta, sz, z,
                                                                      pruned);
