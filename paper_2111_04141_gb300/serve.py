@@ -417,7 +417,6 @@ class Server:
         with admission and completion times filled in."""
         jobs = sorted(jobs, key=lambda j: j.arrival)
         for j in jobs:
-            s = self.setups[j.setup]
             j.work = self._job_work(j)
         t0 = clock()
         i = 0
@@ -444,9 +443,10 @@ class Server:
         return done
 
     def _job_work(self, job: Job) -> float:
-        """Grid-point pol-updates of a job (sum of S_p^2 over its records, x npol),
-        from the plan's work counters is not available per job; estimated
-        from the mean S^2 of the setup's planes weighted like the records."""
+        """Nominal grid-point pol-updates of a job: visibilities x npol x the
+        mean S_p^2 over the setup's planes (the per-record planes are not
+        known on the host; the same nominal figure is used for the
+        sequential baseline, so throughputs compare like with like)."""
         s = self.setups[job.setup]
         return float(job.nrow * s.nchan * s.npol * _mean_s2(s))
 
