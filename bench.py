@@ -622,12 +622,12 @@ def main():
     serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
     torch.cuda.empty_cache()
     precision = measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
-        if not args.no_precision else None
+        if (world == 1 and not args.no_precision) else None
 
     imaging = measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
-        if not args.no_imaging else None
+        if (world == 1 and not args.no_imaging) else None
     variants = measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, 3) \
-        if not args.no_variants else None
+        if (world == 1 and not args.no_variants) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
