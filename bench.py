@@ -546,6 +546,10 @@ def main():
                                       if clocks and clocks.get("sm_mhz") else None),
             "stage_ms_per_step": {k: tm[f"{k}_ms"] / args.steps
                                   for k in ("index", "bin", "grid")}}
+    # cross-check of the nominal peak: a kernel of independent packed FMAs
+    ffma = gw.ffma_peak()
+    roof["peak_ffma_measured"] = ffma
+    roof["frac_of_measured_ffma"] = achieved / ffma
 
     # ---- end to end through the public API with host buffers --------------
     pin_uvw = torch.from_numpy(obs.uvw_m).pin_memory()

@@ -433,6 +433,12 @@ gw_status gw_plan_timing_get(gw_plan plan, gw_timing* out);
  * Misc
  * ------------------------------------------------------------------------ */
 
+/* Measured FP32 FMA throughput of the current device (TFLOP/s, FMA = 2
+ * FLOP) from a kernel of independent packed FMAs running `iters` iterations
+ * on every SM: a cross-check of the nominal FP32 roofline.  Synchronous.
+ * No thesis counterpart.  Errors: GW_EINVAL, GW_ECUDA. */
+gw_status gw_ffma_peak(int32_t iters, double* tflops, void* cuda_stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t gw_launch_count(void);
 

@@ -89,6 +89,7 @@ _SIGS = {
     "gw_plan_copy_tables": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "gw_plan_copy_stored_tables": (c_i32, [c_vp, c_vp]),
     "gw_plan_copy_corrector": (c_i32, [c_vp, c_vp]),
+    "gw_ffma_peak": (c_i32, [c_i32, ctypes.POINTER(c_f64), c_vp]),
     "gw_plan_timing_enable": (c_i32, [c_vp, c_i32]),
     "gw_plan_timing_get": (c_i32, [c_vp, ctypes.POINTER(Timing)]),
     "gw_debug_bins": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp]),

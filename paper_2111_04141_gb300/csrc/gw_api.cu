@@ -1432,6 +1432,15 @@ gw_status gw_plan_copy_stored_tables(gw_plan p, void* out) {
     return e == cudaSuccess ? GW_OK : cuda_fail(e, "copying stored tables");
 }
 
+gw_status gw_ffma_peak(int32_t iters, double* tflops, void* cuda_stream) {
+    if (!tflops || iters < 1) return fail(GW_EINVAL, "bad arguments");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = measure_ffma_peak(sms, iters, tflops, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "FFMA probe");
+}
+
 gw_status gw_plan_timing_enable(gw_plan p, int32_t enable) {
     if (!p) return fail(GW_EINVAL, "null plan");
     p->timing = enable != 0;

@@ -281,6 +281,9 @@ void launch_hybrid_shift(float2* g, int npol, int N, cudaStream_t s);
 void launch_hybrid_image(const float2* raw, int npol, int N, const float* hco, const float* hpr,
                          float2* image, cudaStream_t s);
 
+// ---- FP32 FMA throughput probe (gw_peak.cu) ---------------------------------
+cudaError_t measure_ffma_peak(int num_sms, int iters, double* tflops, cudaStream_t s);
+
 // ---- allocation-free scratch (gw_noalloc.cu) ------------------------------
 // View of the file-scope static scratch on `device` (current); looks up the
 // symbol's device address on first use per device.

@@ -510,5 +510,14 @@ class Plan:
         return offs, ent[:offs[-1]]
 
 
+def ffma_peak(iters: int = 4096, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s (gw_ffma_peak)."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    check(lib.gw_ffma_peak(int(iters), ctypes.byref(out), _stream_ptr(stream, dev)), "gw_ffma_peak")
+    return float(out.value)
+
+
 def launch_count() -> int:
     return int(_lib.load().gw_launch_count())

@@ -326,3 +326,12 @@ def test_grid_from_host_inputs_matches_device_inputs(gw):
         assert rel_l2(a, b) <= 1e-6
         a, b = got2.cpu().numpy().astype(np.complex128), ref2.cpu().numpy().astype(np.complex128)
         assert rel_l2(a, b) <= 1e-6
+
+
+def test_ffma_peak_probe(gw):
+    """The FP32 FMA probe runs and lands near the nominal peak (152 SMs x 128
+    FMA/clk x 2 FLOP x clock: 80.5 TFLOP/s at 2.07 GHz)."""
+    t = gw.ffma_peak(2048)
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    assert 0.3 * nominal <= t <= 1.1 * nominal
