@@ -623,15 +623,26 @@ def main():
 
     # ---- serving stream first (its latencies are sensitive to what the
     # process allocated before), then the other measurements on the batch
-    serving = measure_serving(args, dev) if (world == 1 and not args.no_serving) else None
-    torch.cuda.empty_cache()
-    precision = measure_precision(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
-        if (world == 1 and not args.no_precision) else None
+    def optional(enabled, fn):
+        """A secondary measurement: its failure is reported in the line
+        instead of losing the headline measurement."""
+        if not (enabled and world == 1):
+            return None
+        try:
+            return fn()
+        except Exception as exc:                      # noqa: BLE001
+            torch.cuda.synchronize(dev)
+            return {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        finally:
+            torch.cuda.empty_cache()
 
-    imaging = measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, nd) \
-        if (world == 1 and not args.no_imaging) else None
-    variants = measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, 3) \
-        if (world == 1 and not args.no_variants) else None
+    serving = optional(not args.no_serving, lambda: measure_serving(args, dev))
+    precision = optional(not args.no_precision, lambda: measure_precision(
+        gw, plan, obs, uvw, freq, vis, dev, stream, nd))
+    imaging = optional(not args.no_imaging, lambda: measure_imaging(
+        gw, plan, obs, uvw, freq, vis, dev, stream, nd))
+    variants = optional(not args.no_variants, lambda: measure_next(
+        gw, plan, obs, uvw, freq, vis, dev, stream, 3))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
