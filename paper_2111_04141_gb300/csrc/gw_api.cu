@@ -88,6 +88,7 @@ struct gw_plan_s {
     int64_t h_rows = 0, h_freq_n = 0;
     int hy_sz = 0;
     float* d_z = nullptr;
+    std::vector<float> h_z;       // host copy of d_z (kernel-argument weights)
     double* d_hpr = nullptr;
     float* d_hprf = nullptr;
     int64_t scratch_bytes = 0;
@@ -1054,6 +1055,11 @@ static gw_status ensure_prune(gw_plan p, int32_t sz, cudaStream_t s) {
     if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating the pruner");
     e = build_prune(sz, beta, N, p->d_z, p->d_hpr, p->d_hprf, s);
     if (e != cudaSuccess) return cuda_fail(e, "building the pruner");
+    p->h_z.assign((size_t)(beta / 2) * sz, 0.f);
+    e = cudaMemcpyAsync(p->h_z.data(), p->d_z, sizeof(float) * p->h_z.size(),
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the pruning table");
     p->hy_sz = sz;
     return GW_OK;
 }
@@ -1109,7 +1115,8 @@ gw_status gw_hybrid_prune(gw_plan p, int32_t sz, const void* fine, void* pruned,
     st = ensure_prune(p, sz, s);
     if (st != GW_OK) return st;
     launch_prune(reinterpret_cast<const float2*>(fine), p->desc.npol, p->desc.grid_n,
-                 p->desc.oversample, sz, p->d_z, reinterpret_cast<float2*>(pruned), s);
+                 p->desc.oversample, sz, p->d_z, p->h_z.data(), p->num_sms,
+                 reinterpret_cast<float2*>(pruned), s);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GW_OK : cuda_fail(e, "prune launch");
 }

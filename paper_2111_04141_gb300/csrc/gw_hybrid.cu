@@ -180,6 +180,126 @@ __global__ void k_hybrid_image(const float2* __restrict__ raw, int npol, int N,
     }
 }
 
+// Streaming pruner.  The pruning of one column is a polyphase filter: fine
+// row r (2x row k' = nearest, offset m) feeds the S_z output rows
+// k' - hz .. k' + hz.  A thread owns one column and a segment of output rows
+// and walks the 2x rows k' in order: it reads the beta/2 fine rows of k'
+// once (coalesced across the warp, streaming loads), adds them into a ring of
+// S_z register accumulators and stores output row k' - hz, which no later k'
+// touches.  The walk is unrolled by S_z from a multiple of S_z, so output k
+// sits in accumulator k mod S_z at a compile-time index, and the Z weights
+// are a by-value kernel argument, i.e. constant-bank operands of the FMAs.
+// Each fine value is read from memory about once and there is no shared
+// memory traffic: the kernel is bound by HBM bandwidth.
+template <int HB, int SZ>
+struct PruneZ {
+    float z[HB * SZ];   // Z[m][t + hz]
+};
+
+template <int HB>
+__device__ __forceinline__ void prune_rows(const float2* __restrict__ col, int64_t r0, int64_t fr,
+                                           int N, float2 (&f)[HB]) {
+#pragma unroll
+    for (int m = 0; m < HB; ++m) {
+        const int64_t r = r0 + m;
+        f[m] = (r >= 0 && r < fr) ? __ldcs(col + r * N) : make_float2(0.f, 0.f);
+    }
+}
+
+template <int HB, int SZ>
+__global__ void __launch_bounds__(256) k_prune_stream(const float2* __restrict__ fine, int N, int L,
+                                                      const PruneZ<HB, SZ> Z,
+                                                      float2* __restrict__ pruned) {
+    constexpr int hz = SZ / 2;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= N) return;
+    const int p = blockIdx.z;
+    const int64_t fr = (int64_t)2 * HB * N;        // beta N fine rows
+    const int rows2 = 2 * N;
+    const float2* col = fine + (int64_t)p * fr * N + u;
+    float2* out = pruned + (int64_t)p * rows2 * N + u;
+    const int kb = blockIdx.y * L;                 // this thread's output rows [kb, ke)
+    const int ke = min(kb + L, rows2);
+    if (kb >= ke) return;
+    // 2x rows k' = kb - hz .. ke - 1 + hz, walked from a multiple of SZ
+    const int a = kb - hz;
+    const int g0 = a >= 0 ? a - a % SZ : -((-a + SZ - 1) / SZ) * SZ;
+    const int glast = ke - 1 + hz;
+    float2 acc[SZ];
+#pragma unroll
+    for (int q = 0; q < SZ; ++q) acc[q] = make_float2(0.f, 0.f);
+    // fine rows of k' start at k' HB - beta / 4 = (k' - 1/2) HB; the rows of
+    // the next PD 2x rows are in flight while k' is added (PD = 2 for
+    // beta = 8, 1 for beta = 16 to bound the registers)
+    constexpr int PD = HB == 4 ? 2 : 1;
+    float2 fa[HB], fb[HB];
+    prune_rows<HB>(col, (int64_t)g0 * HB - HB / 2, fr, N, fa);
+    if (PD == 2) prune_rows<HB>(col, (int64_t)(g0 + 1) * HB - HB / 2, fr, N, fb);
+    for (int g = g0; g <= glast; g += SZ) {
+#pragma unroll
+        for (int i = 0; i < SZ; ++i) {
+            const int kp = g + i;
+            float2 fc[HB];                          // PD 2x rows ahead
+            prune_rows<HB>(col, (int64_t)(kp + PD) * HB - HB / 2, fr, N, fc);
+#pragma unroll
+            for (int t = -hz; t <= hz; ++t) {
+                const int q = (i + t + SZ) % SZ;    // accumulator of output kp + t
+#pragma unroll
+                for (int m = 0; m < HB; ++m) {
+                    const float w = Z.z[m * SZ + t + hz];
+                    acc[q].x = fmaf(w, fa[m].x, acc[q].x);
+                    acc[q].y = fmaf(w, fa[m].y, acc[q].y);
+                }
+            }
+            const int k = kp - hz;                  // complete: no later k' reaches it
+            const int qd = (i - hz + SZ) % SZ;
+            if (k >= kb && k < ke) __stcs(out + (int64_t)k * N, acc[qd]);
+            acc[qd] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < HB; ++m) {
+                if (PD == 2) {
+                    fa[m] = fb[m];
+                    fb[m] = fc[m];
+                } else {
+                    fa[m] = fc[m];
+                }
+            }
+        }
+    }
+}
+
+template <int HB, int SZ>
+void launch_prune_stream(const float2* fine, int npol, int N, const float* h_z, int num_sms,
+                         float2* pruned, cudaStream_t s) {
+    PruneZ<HB, SZ> Z;
+    for (int i = 0; i < HB * SZ; ++i) Z.z[i] = h_z[i];
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune_stream<HB, SZ>, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    // one wave: segments per column so that every resident thread owns one
+    const int64_t resident = (int64_t)std::max(num_sms, 1) * per_sm * 256;
+    const int64_t cols = (int64_t)npol * N;
+    int64_t nseg = std::max<int64_t>(1, resident / cols);
+    int64_t L = (2LL * N + nseg - 1) / nseg;
+    if (L < SZ) L = SZ;
+    nseg = (2LL * N + L - 1) / L;
+    const dim3 grid((unsigned)((N + 255) / 256), (unsigned)nseg, (unsigned)npol);
+    k_prune_stream<HB, SZ><<<grid, 256, 0, s>>>(fine, N, (int)L, Z, pruned);
+}
+
+template <int HB>
+bool launch_prune_stream_hb(const float2* fine, int npol, int N, int sz, const float* h_z,
+                            int num_sms, float2* pruned, cudaStream_t s) {
+    switch (sz) {
+        case 7: launch_prune_stream<HB, 7>(fine, npol, N, h_z, num_sms, pruned, s); return true;
+        case 9: launch_prune_stream<HB, 9>(fine, npol, N, h_z, num_sms, pruned, s); return true;
+        case 11: launch_prune_stream<HB, 11>(fine, npol, N, h_z, num_sms, pruned, s); return true;
+        case 13: launch_prune_stream<HB, 13>(fine, npol, N, h_z, num_sms, pruned, s); return true;
+        case 15: launch_prune_stream<HB, 15>(fine, npol, N, h_z, num_sms, pruned, s); return true;
+        default: return false;
+    }
+}
+
 }  // namespace
 
 void launch_hybrid_grid(const gw_index_rec* rec, int64_t nvis, const void* vis, int vis_kind,
@@ -194,7 +314,18 @@ void launch_hybrid_grid(const gw_index_rec* rec, int64_t nvis, const void* vis, 
 }
 
 void launch_prune(const float2* fine, int npol, int N, int beta, int sz, const float* z,
-                  float2* pruned, cudaStream_t s) {
+                  const float* h_z, int num_sms, float2* pruned, cudaStream_t s) {
+    if (h_z) {
+        const bool done = beta == 8 ? launch_prune_stream_hb<4>(fine, npol, N, sz, h_z, num_sms,
+                                                                pruned, s)
+                        : beta == 16 ? launch_prune_stream_hb<8>(fine, npol, N, sz, h_z, num_sms,
+                                                                 pruned, s)
+                                     : false;
+        if (done) {
+            note_launch();
+            return;
+        }
+    }
     // largest power-of-two row block whose fine-row window fits the tile
     int R = 128;
     while (R >= 8 && ((int64_t)(R + sz) * beta / 2 + 2 > kPruneRowsMax)) R >>= 1;

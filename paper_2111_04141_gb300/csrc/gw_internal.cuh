@@ -275,8 +275,10 @@ void launch_hybrid_grid(const gw_index_rec* rec, int64_t nvis, const void* vis, 
                         const float* weight, int npol, int beta, int S, const double* c1,
                         int fmin, double norm, int N, int sz, float2* fine,
                         unsigned long long* dropped, cudaStream_t s);
+// z: device Z table [beta/2][sz]; h_z: its host copy (null = shared-memory
+// tiled pruner only); the streaming pruner covers beta in {8, 16}, sz in 7..15.
 void launch_prune(const float2* fine, int npol, int N, int beta, int sz, const float* z,
-                  float2* pruned, cudaStream_t s);
+                  const float* h_z, int num_sms, float2* pruned, cudaStream_t s);
 void launch_hybrid_shift(float2* g, int npol, int N, cudaStream_t s);
 void launch_hybrid_image(const float2* raw, int npol, int N, const float* hco, const float* hpr,
                          float2* image, cudaStream_t s);

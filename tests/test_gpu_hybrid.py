@@ -33,7 +33,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("beta,sz", [(8, 15), (16, 9)])
+# (8, 15), (8, 7), (16, 9): streaming pruner; (8, 17): shared-memory tiled pruner
+@pytest.mark.parametrize("beta,sz", [(8, 15), (8, 7), (16, 9), (8, 17)])
 def test_hybrid_steps_match_oracle(gw, beta, sz):
     obs = syn.small_case(n_ant=7, n_times=10, n_chan=3, npol=2, grid_n=128, s_min=7, s_max=7,
                          n_w=1, diameter_m=1500.0, beta=beta)
