@@ -372,9 +372,11 @@ gw_status gw_grid_shift(gw_plan plan, void* grid, void* cuda_stream);
 /* The index stage alone (pre-processing of Section 3.3.5): writes
  * nrow * nchan records, (row, channel) order, to `out` (device).  Each record
  * is computed in FP64 with the operation sequence
- *     u_lambda = (u * f) / c0;  x = u_lambda * L + N/2;
+ *     s_c = f / c0 (once per channel);  u_lambda = u * s_c;  x = u_lambda * L + N/2;
  *     q = floor(beta * x + 0.5);  k = floor((q + beta/2) / beta);  o = q - k beta
- * (same for v), plane p = min(floor(sqrt(|w_lambda| / w_max) (P-1) + 0.5), P-1),
+ * (same for v), plane p = the number of thresholds
+ * T_j = ((j - 1/2) / (P-1))^2 * w_max, j = 1 .. P-1, with T_j <= |w * s_c|
+ * (the plane nearest in sqrt|w|, ties up, at most P-1; w * s_c must be finite),
  * every operation rounded to nearest with no fused multiply-add.  n_dropped
  * as for gw_grid_vis. */
 gw_status gw_index_vis(gw_plan plan, const double* uvw_m, const double* freq_hz, int64_t nrow,

@@ -4,15 +4,19 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 For each visibility (row r, channel c) with uvw in metres and frequency f:
 
-* u_lambda = (u * f) / c0                    (wavelengths)
+* s_c = f / c0                               (one factor per channel, 1/lambda)
+* u_lambda = u * s_c                         (wavelengths)
 * x = u_lambda * L + N/2                     (pixel coordinate; the uv origin
                                               sits on pixel N/2, Section 2.1.2)
 * q = floor(beta * x + 0.5)                  (nearest point of the
                                               beta-oversampled grid, ties up)
 * k = floor((q + beta/2) / beta), o = q - k beta, o in [-beta/2, beta/2)
 * the same for v; the record sits at pixel k + o / beta.
-* w-plane (P > 1): s = sqrt(|w_lambda| / w_max) * (P - 1),
-  p = min(floor(s + 0.5), P - 1); conj = (w_lambda < 0).  P = 1 ignores w.
+* w-plane (P > 1): the plane nearest in sqrt(|w|), ties up, as a count of
+  thresholds: T_j = ((j - 1/2) / (P - 1))^2 * w_max, j = 1 .. P - 1 (each
+  step rounded), p = #{j : T_j <= |w_lambda|} (so p <= P - 1 and records
+  beyond w_max use the outermost plane); w_lambda must be finite;
+  conj = (w_lambda < 0).  P = 1 ignores w.
 * valid (Bounded Records Assumption, Section 2.3.1): every tap of the
   plane's S_p x S_p footprint lands inside [0, N); also q finite and
   |q| < 2^30.
@@ -34,9 +38,22 @@ FLAG_VALID = 1
 FLAG_CONJ = 2
 
 
+def chan_scale(freq: np.ndarray) -> np.ndarray:
+    """s_c = f / c0 per channel (wavelengths per metre)."""
+    return np.asarray(freq, dtype=np.float64) / C0
+
+
+def plane_thresholds(prm: Params) -> np.ndarray:
+    """T_j = ((j - 1/2) / (P - 1))^2 w_max, j = 1 .. P - 1: |w| at which the
+    nearest plane in sqrt(|w|) steps from j - 1 to j."""
+    P = prm.n_wplanes
+    t = (np.arange(1, P, dtype=np.float64) - 0.5) / float(P - 1)
+    return (t * t) * float(prm.w_max_lambda)
+
+
 def _axis(coord_m: np.ndarray, freq: np.ndarray, prm: Params):
     L = float(prm.grid_n) * float(prm.cell_rad)
-    lam = (coord_m[:, None] * freq[None, :]) / C0
+    lam = coord_m[:, None] * chan_scale(freq)[None, :]
     x = lam * L + float(prm.grid_n // 2)
     q = np.floor(float(prm.oversample) * x + 0.5)
     ok = np.isfinite(q) & (np.abs(q) < Q_LIMIT)
@@ -60,11 +77,11 @@ def index_vis(uvw_m: np.ndarray, freq_hz: np.ndarray, prm: Params) -> dict:
         conj = np.zeros(shape, dtype=bool)
         okw = np.ones(shape, dtype=bool)
     else:
-        wl = (uvw_m[:, 2][:, None] * freq_hz[None, :]) / C0
-        s = np.sqrt(np.abs(wl) / float(prm.w_max_lambda)) * float(P - 1)
-        pf = np.floor(s + 0.5)
-        okw = np.isfinite(pf)
-        plane = np.minimum(np.where(okw, pf, 0.0), float(P - 1)).astype(np.int64)
+        wl = uvw_m[:, 2][:, None] * chan_scale(freq_hz)[None, :]
+        okw = np.isfinite(wl)
+        cnt = np.searchsorted(plane_thresholds(prm), np.abs(np.where(okw, wl, 0.0)),
+                              side="right")
+        plane = np.where(okw, cnt, 0).astype(np.int64)
         conj = wl < 0.0
     S = plane_support(prm)[plane]
     h = (S - 1) // 2

@@ -11,19 +11,19 @@ the corrector is applied once to the sum.
 Reading: layers w_l = w_min + l dw, dw = (w_max - w_min)/(L - 1); a
 visibility belongs to the nearest layer, ties up, clamped to [0, L - 1]:
 l = clamp(floor((w_lambda - w_min)/dw + 1/2), 0, L - 1), in FP64 with the
-operation order of the index stage (w_lambda = (w f)/c0).
+operation order of the index stage (w_lambda = w (f/c0)).
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .image import _lmn, centred_idft, correct
-from .wkernel import C0
+from .index import chan_scale
 
 
 def layer_of(uvw_m, freq_hz, n_layers: int, w_min: float, w_max: float) -> np.ndarray:
     """Layer of every visibility, (row, channel) order."""
-    wl = (uvw_m[:, 2][:, None] * freq_hz[None, :]) / C0
+    wl = uvw_m[:, 2][:, None] * chan_scale(freq_hz)[None, :]
     if n_layers <= 1:
         return np.zeros(wl.size, dtype=np.int64)
     dw = (w_max - w_min) / (n_layers - 1)

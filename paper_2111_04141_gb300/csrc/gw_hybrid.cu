@@ -23,38 +23,60 @@ unsigned blocks_for(int64_t n) {
     return (unsigned)std::max<int64_t>(b, 1);
 }
 
-// One thread per (record, tap); consecutive taps of a record are
-// consecutive columns of its fine row (coalesced vector atomics).
-__global__ void k_hybrid_grid(const gw_index_rec* __restrict__ rec, int64_t nvis,
-                              const void* __restrict__ vis, int vis_kind,
-                              const float* __restrict__ weight, int npol, int beta, int S,
-                              const double* __restrict__ c1, int fmin, double norm, int N, int sz,
-                              float2* __restrict__ fine, unsigned long long* __restrict__ dropped) {
-    const int h = S / 2, hz = sz / 2;
-    const int64_t total = nvis * S;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / S;
-        const int t = (int)(e - i * S) - h;
+// Lanes over (record, tap): a warp takes 32 / S records of S taps at a
+// time (S > 32: one record, lanes loop over its taps), so consecutive taps
+// of a record are consecutive columns of its fine row (coalesced vector
+// atomics).  The 1-D GCF weights c(t - o_u/beta) / norm are rounded to FP32
+// once per CTA into a [beta][S] shared table (wtab != 0), not per tap.
+__global__ void __launch_bounds__(256) k_hybrid_grid(const gw_index_rec* __restrict__ rec,
+                                                     int64_t nvis, const void* __restrict__ vis,
+                                                     int vis_kind, const float* __restrict__ weight,
+                                                     int npol, int beta, int S,
+                                                     const double* __restrict__ c1, int fmin,
+                                                     double norm, int N, int sz, int wtab,
+                                                     float2* __restrict__ fine,
+                                                     unsigned long long* __restrict__ dropped) {
+    extern __shared__ float ws[];                          // [beta][S] when wtab
+    const int h = S / 2, hz = sz / 2, hb = beta / 2;
+    if (wtab) {
+        for (int e = threadIdx.x; e < beta * S; e += blockDim.x) {
+            const int a = e / S, tt = e - a * S;          // a = o_u + beta/2, tt = t + h
+            ws[e] = (float)(c1[beta * (tt - h) - (a - hb) - fmin] / norm);
+        }
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int G = S <= 32 ? 32 / S : 1;                    // records per warp pass
+    const int rl = S <= 32 ? lane / S : 0;
+    const int t0 = S <= 32 ? lane - rl * S : lane;         // first tap (0-based) of this lane
+    if (rl >= G) return;                                   // idle lanes (no barriers below)
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp * G + rl; i < nvis; i += nwarps * G) {
         int4 rv = __ldg(reinterpret_cast<const int4*>(rec) + i);
         const gw_index_rec r = *reinterpret_cast<gw_index_rec*>(&rv);
-        if (!(r.flags & GW_FLAG_VALID)) continue;      // counted by the index stage
+        if (!(r.flags & GW_FLAG_VALID)) continue;          // counted by the index stage
         const int64_t q = (int64_t)r.kv * beta + r.ov;
-        const long long k0 = floor_div(2 * q + beta / 2, beta);
+        const long long k0 = floor_div(2 * q + hb, beta);
         if (q < 0 || q >= (int64_t)beta * N || k0 - hz < 0 || k0 + hz > 2LL * N - 1) {
-            if (t == -h) atomicAdd(dropped, 1ULL);      // pruning window leaves the 2N rows
+            if (t0 == 0) atomicAdd(dropped, 1ULL);         // pruning window leaves the 2N rows
             continue;
         }
-        const float w = (float)(__ldg(c1 + beta * t - r.ou - fmin) / norm);
-        const int64_t col = (int64_t)r.ku + t;
-        for (int p = 0; p < npol; ++p) {
-            float2 v = load_vis(vis, vis_kind, i * npol + p);
-            if (weight) {
-                const float ww = __ldg(weight + i * npol + p);
-                v.x *= ww;
-                v.y *= ww;
+        for (int tt = t0; tt < S; tt += 32) {
+            const int t = tt - h;
+            const float w = wtab ? ws[(r.ou + hb) * S + tt]
+                                 : (float)(__ldg(c1 + beta * t - r.ou - fmin) / norm);
+            const int64_t col = (int64_t)r.ku + t;
+            for (int p = 0; p < npol; ++p) {
+                float2 vv = load_vis(vis, vis_kind, i * npol + p);   // L1 broadcast over the taps
+                if (weight) {
+                    const float ww = __ldg(weight + i * npol + p);
+                    vv.x *= ww;
+                    vv.y *= ww;
+                }
+                atomicAdd(fine + ((int64_t)p * beta * N + q) * N + col,
+                          make_float2(w * vv.x, w * vv.y));
             }
-            atomicAdd(fine + ((int64_t)p * beta * N + q) * N + col, make_float2(w * v.x, w * v.y));
         }
     }
 }
@@ -307,9 +329,13 @@ void launch_hybrid_grid(const gw_index_rec* rec, int64_t nvis, const void* vis, 
                         int fmin, double norm, int N, int sz, float2* fine,
                         unsigned long long* dropped, cudaStream_t s) {
     if (nvis <= 0) return;
-    k_hybrid_grid<<<blocks_for(nvis * S), 256, 0, s>>>(rec, nvis, vis, vis_kind, weight, npol,
-                                                       beta, S, c1, fmin, norm, N, sz, fine,
-                                                       dropped);
+    const size_t tab = sizeof(float) * (size_t)beta * S;
+    const int wtab = tab <= 16384 ? 1 : 0;
+    const int G = S <= 32 ? 32 / S : 1;
+    const int64_t warps = (nvis + G - 1) / G;
+    k_hybrid_grid<<<blocks_for(warps * 32), 256, wtab ? tab : 0, s>>>(
+        rec, nvis, vis, vis_kind, weight, npol, beta, S, c1, fmin, norm, N, sz, wtab, fine,
+        dropped);
     note_launch();
 }
 

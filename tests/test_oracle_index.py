@@ -60,3 +60,45 @@ def test_flags_and_invalid_zeros():
     assert idx["flags"][0] == FLAG_VALID | FLAG_CONJ
     assert idx["flags"][1] == 0
     assert idx["ku"][1] == 0 and idx["plane"][1] == 0
+
+
+def test_plane_is_nearest_in_sqrt_w_exactly():
+    """The threshold count equals the plane nearest in sqrt(|w|) (ties up,
+    clamped to P - 1) decided in exact rational arithmetic:
+    p >= j  <=>  (j - 1/2)^2 w_max <= (P - 1)^2 |w|."""
+    from fractions import Fraction
+    from oracle.index import plane_thresholds
+    rng = np.random.default_rng(11)
+    for P, wmax in ((2, 3.0), (5, 1000.0), (32, 2300.0), (129, 77.7)):
+        prm = Params(grid_n=64, cell_rad=1e-3, support_min=7, support_max=15, oversample=8,
+                     n_wplanes=P, w_max_lambda=wmax)
+        w = np.concatenate([rng.uniform(-1.2 * wmax, 1.2 * wmax, 400),
+                            rng.uniform(-wmax / P**2, wmax / P**2, 100)])
+        uvw = np.stack([np.zeros_like(w), np.zeros_like(w), w], axis=1)
+        got = index_vis(uvw, np.array([C0]), prm)["plane"]
+        Fw = Fraction(wmax)
+        for wi, pi in zip(w, got):
+            a = Fraction(abs(float(wi)))
+            exact = sum(1 for j in range(1, P)
+                        if (Fraction(2 * j - 1, 2) ** 2) * Fw <= (P - 1) ** 2 * a)
+            assert pi == exact, (P, wi, pi, exact)
+        # the square-root form of the same rule agrees away from the thresholds
+        T = plane_thresholds(prm)
+        far = np.min(np.abs(np.abs(w)[:, None] - T[None, :]), axis=1) > 1e-9 * wmax
+        s = np.sqrt(np.abs(w) / wmax) * (P - 1)
+        want = np.minimum(np.floor(s + 0.5), P - 1).astype(np.int64)
+        assert np.array_equal(got[far], want[far])
+
+
+def test_channel_factor_is_one_division_per_channel():
+    """u_lambda = u * (f / c0): with f = c0 the factor is exactly 1, so the
+    coordinate in wavelengths is the metre value itself."""
+    from oracle.index import chan_scale
+    assert chan_scale(np.array([C0]))[0] == 1.0
+    # u_lambda * lambda recovers u to rounding (two roundings, < 4 ulp)
+    rng = np.random.default_rng(5)
+    f = rng.uniform(5e7, 2e9, 64)
+    u = rng.uniform(-2e4, 2e4, 64)
+    lam_m = C0 / f
+    back = (u * chan_scale(f)) * lam_m
+    assert np.all(np.abs(back - u) <= 4 * np.spacing(np.abs(u)))
