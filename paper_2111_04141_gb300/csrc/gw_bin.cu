@@ -7,7 +7,8 @@
 //                   touches (the gridder owns a tile and needs all of them);
 //   centre mode:    a record is listed once, in the tile of its pixel (the
 //                   degridder reads a record's whole footprint).
-// Steps: histogram (atomics) -> exclusive scan -> scatter (atomic cursors),
+// Steps: histogram (atomics; per-CTA shared histograms when the tile count
+// allows) -> exclusive scan -> scatter (atomic cursors),
 // then the footprint bins are cut into work items of at most item_max
 // entries.  Order within a bin is unspecified.
 #include "gw_internal.cuh"
@@ -136,6 +137,87 @@ __global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, De
     }
 }
 
+// Shared-memory variants (ntiles small enough for a per-CTA histogram): a
+// CTA takes a contiguous chunk of records and counts its (record, tile)
+// pairs with shared-memory atomics; only the non-zero bins reach global
+// memory, one atomic each.  The scatter recounts its chunk, reserves one run
+// per (CTA, tile) in the tile's bin with a single global atomic, and places
+// the entries with shared-memory cursors that start at the run bases.
+constexpr int kBinSmThreads = 512;
+constexpr int kBinSmTilesMax = 49152;     // 192 KB of u32 counters
+
+__global__ void __launch_bounds__(kBinSmThreads) k_count_sm(
+    const gw_index_rec* __restrict__ rec, int64_t nvis, DevCount dc, BinGeom g, int P, int smin,
+    int smax, int ntiles, uint32_t* __restrict__ count, unsigned long long* __restrict__ work) {
+    extern __shared__ uint32_t hist[];
+    nvis = dc.clamp(nvis);
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    const int64_t chunk = (nvis + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = blockIdx.x * chunk, c1 = min(nvis, c0 + chunk);
+    unsigned long long n_valid = 0, n_taps = 0;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const gw_index_rec r = load_rec(rec, i);
+        if (!(r.flags & GW_FLAG_VALID)) continue;
+        const int S = plane_support(r.plane, P, smin, smax);
+        ++n_valid;
+        n_taps += (unsigned long long)(S * S);
+        const TileRange t = tile_range(r, g, P, smin, smax);
+        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        for (int tv = t.tv0; tv <= t.tv1; ++tv)
+            for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(hist + lbase + tv * g.ntu + tu, 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        if (hist[t]) atomicAdd(count + t, hist[t]);
+    for (int d = 16; d > 0; d >>= 1) {
+        n_valid += __shfl_down_sync(0xffffffffu, n_valid, d);
+        n_taps += __shfl_down_sync(0xffffffffu, n_taps, d);
+    }
+    if ((threadIdx.x & 31) == 0 && n_valid) {
+        atomicAdd(work, n_valid);
+        atomicAdd(work + 1, n_taps);
+    }
+}
+
+__global__ void __launch_bounds__(kBinSmThreads) k_scatter_sm(
+    const gw_index_rec* __restrict__ rec, int64_t nvis, DevCount dc, BinGeom g, int P, int smin,
+    int smax, int ntiles, const uint32_t* __restrict__ offsets, uint32_t* __restrict__ cursor,
+    uint32_t* __restrict__ entries) {
+    extern __shared__ uint32_t hist[];
+    nvis = dc.clamp(nvis);
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    const int64_t chunk = (nvis + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = blockIdx.x * chunk, c1 = min(nvis, c0 + chunk);
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const gw_index_rec r = load_rec(rec, i);
+        if (!(r.flags & GW_FLAG_VALID)) continue;
+        const TileRange t = tile_range(r, g, P, smin, smax);
+        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        for (int tv = t.tv0; tv <= t.tv1; ++tv)
+            for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(hist + lbase + tv * g.ntu + tu, 1u);
+    }
+    __syncthreads();
+    // this CTA's run in each bin: absolute position of its first entry
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t c = hist[t];
+        if (c) hist[t] = offsets[t] + atomicAdd(cursor + t, c);
+    }
+    __syncthreads();
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const gw_index_rec r = load_rec(rec, i);
+        if (!(r.flags & GW_FLAG_VALID)) continue;
+        const TileRange t = tile_range(r, g, P, smin, smax);
+        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        for (int tv = t.tv0; tv <= t.tv1; ++tv)
+            for (int tu = t.tu0; tu <= t.tu1; ++tu) {
+                const uint32_t pos = atomicAdd(hist + lbase + tv * g.ntu + tu, 1u);
+                entries[pos] = (uint32_t)i;
+            }
+    }
+}
+
 __global__ void k_items(const uint32_t* __restrict__ count, const uint32_t* __restrict__ offsets,
                         const uint32_t* __restrict__ item_off, int ntiles, int item_max,
                         Item* __restrict__ items) {
@@ -159,20 +241,42 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
                 Scratch& sc, cudaStream_t s, DevCount dc) {
     const int ntiles = g.ntu * g.ntv * (g.layer_tiles ? g.nlayers : 1);
     cudaMemsetAsync(sc.count, 0, sizeof(uint32_t) * ntiles, s);
+    // per-CTA shared histograms when the bins fit; CTAs: every SM busy
+    int sm_blocks = 0;
+    const size_t hsm = sizeof(uint32_t) * (size_t)ntiles;
+    if (ntiles <= kBinSmTilesMax && nvis > 0) {
+        int dev = 0, nsm = 0, c_sm = 0, s_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_count_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        cudaFuncSetAttribute(k_scatter_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c_sm, k_count_sm, kBinSmThreads, hsm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s_sm, k_scatter_sm, kBinSmThreads, hsm);
+        sm_blocks = std::min(c_sm, s_sm) * nsm;
+    }
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     if (nvis > 0) {
-        k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, dc, g, P, smin, smax, sc.count,
-                                                     sc.work);
+        if (sm_blocks > 0)
+            k_count_sm<<<sm_blocks, kBinSmThreads, hsm, s>>>(rec, nvis, dc, g, P, smin, smax, ntiles,
+                                                             sc.count, sc.work);
+        else
+            k_count<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, dc, g, P, smin, smax, sc.count,
+                                                         sc.work);
         note_launch();
     }
     k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, g.item_max, sc.offsets, sc.item_off, sc.cursor);
     note_launch();
     if (nvis > 0) {
-        k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, dc, g, P, smin, smax,
-                                                       sc.offsets, sc.cursor, sc.entries);
+        if (sm_blocks > 0)
+            k_scatter_sm<<<sm_blocks, kBinSmThreads, hsm, s>>>(rec, nvis, dc, g, P, smin, smax,
+                                                               ntiles, sc.offsets, sc.cursor,
+                                                               sc.entries);
+        else
+            k_scatter<<<(unsigned)blocks, threads, 0, s>>>(rec, nvis, dc, g, P, smin, smax,
+                                                           sc.offsets, sc.cursor, sc.entries);
         note_launch();
     }
     if (sc.items) {   // work items (the allocation-free degrid path has none)
