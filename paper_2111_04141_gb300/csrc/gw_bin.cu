@@ -241,10 +241,13 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
                 Scratch& sc, cudaStream_t s, DevCount dc) {
     const int ntiles = g.ntu * g.ntv * (g.layer_tiles ? g.nlayers : 1);
     cudaMemsetAsync(sc.count, 0, sizeof(uint32_t) * ntiles, s);
-    // per-CTA shared histograms when the bins fit; CTAs: every SM busy
+    // per-CTA shared histograms when the bins fit and every CTA has at
+    // least ntiles records (zeroing and flushing its histogram stays a small
+    // part of its work); small inputs keep the global-atomic kernels, which
+    // also leave the GPU to concurrent work on other streams
     int sm_blocks = 0;
     const size_t hsm = sizeof(uint32_t) * (size_t)ntiles;
-    if (ntiles <= kBinSmTilesMax && nvis > 0) {
+    if (ntiles <= kBinSmTilesMax && nvis >= 2LL * ntiles) {
         int dev = 0, nsm = 0, c_sm = 0, s_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -252,7 +255,8 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
         cudaFuncSetAttribute(k_scatter_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c_sm, k_count_sm, kBinSmThreads, hsm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s_sm, k_scatter_sm, kBinSmThreads, hsm);
-        sm_blocks = std::min(c_sm, s_sm) * nsm;
+        sm_blocks = (int)std::min<int64_t>((int64_t)std::min(c_sm, s_sm) * nsm,
+                                           nvis / ntiles);
     }
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;
