@@ -8,13 +8,16 @@
 // Two kernels:
 // * k_degrid_staged (used by gw_degrid_vis): a CTA takes a work item of one
 //   16 x 16 centre tile, copies the tile's grid region (the tile plus the
-//   plan's largest half-support on every side, polarisations interleaved) into
+//   plan's largest half-support on every side, one plane per polarisation) into
 //   shared memory once, and serves all records of the item from it, so the
 //   grid is read from L2/HBM about once per tile instead of once per tap.
 //   One warp per record: lanes take consecutive taps of the S x S footprint
 //   (flattened, so every lane is busy), multiply-accumulate all polarisations
-//   against the kernel slice (read coalesced from the table) and reduce with
-//   warp shuffles.
+//   against the kernel slice (read coalesced from the table, one step ahead)
+//   and reduce with warp shuffles.  The region fills most of an SM's shared
+//   memory, so a CTA is 32 warps: the table loads from L2 are the latency to
+//   hide, and planes per polarisation keep each lane's grid reads
+//   conflict-light (8-byte stride).
 // * k_degrid (the fallback when the region does not fit in shared memory,
 //   and the allocation-free entry point): the same per-record warp, reading
 //   the grid through L1/L2, records visited in 32 x 32 centre-tile order.
@@ -95,13 +98,13 @@ void launch_t(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
     note_launch();
 }
 
-constexpr int kStagedThreads = 512;
+constexpr int kStagedThreads = 1024;
 constexpr int kStagedTile = 16;
 
 template <int NPOL, int TK>
 __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, int hmax) {
     using TE = TabElem<TK>;
-    extern __shared__ __align__(16) float2 reg[];          // [RS][RS][NPOL]
+    extern __shared__ __align__(16) float2 reg[];          // [NPOL][RS][RS]
     __shared__ uint32_t s_item;
     const int RS = kStagedTile + 2 * hmax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
 #pragma unroll
             for (int p = 0; p < NPOL; ++p)
-                reg[(size_t)e * NPOL + p] =
+                reg[(size_t)p * RS * RS + e] =
                     in ? __ldg(a.grid + ((int64_t)p * N + gy) * N + gx) : make_float2(0.f, 0.f);
         }
         __syncthreads();
@@ -143,16 +146,19 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
 #pragma unroll
             for (int p = 0; p < NPOL; ++p) acc[p][0] = acc[p][1] = 0.f;
             const int n = S * S;
-            // flattened taps t = lane + 32 i, (tv, tu) advanced incrementally
+            // flattened taps t = lane + 32 i, (tv, tu) advanced incrementally;
+            // the kernel values of the next step load while this one's FMAs run
             const int dq = 32 / S, dr = 32 - dq * S;
             int tv = lane / S, tu = lane - (lane / S) * S;
+            float2 k1 = lane < n ? TE::load(K + lane) : make_float2(0.f, 0.f);
             for (int t = lane; t < n; t += 32) {
-                const float2 k = TE::load(K + t);
+                const float2 k = k1;
+                if (t + 32 < n) k1 = TE::load(K + t + 32);
                 const float ki = sg * k.y;
-                const float2* g = reg + (size_t)(base + tv * RS + tu) * NPOL;
+                const int off = base + tv * RS + tu;
 #pragma unroll
                 for (int p = 0; p < NPOL; ++p) {
-                    const float2 gv = g[p];
+                    const float2 gv = reg[(size_t)p * RS * RS + off];
                     // conj(K_i) G with K_i = K (w >= 0) or conj K (w < 0)
                     acc[p][0] = fmaf(k.x, gv.x, acc[p][0]);
                     acc[p][0] = fmaf(ki, gv.y, acc[p][0]);
