@@ -172,20 +172,46 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
                     ++tv;
                 }
             }
+            if constexpr (NPOL == 4) {
+                // reduce-scatter butterfly: lanes with bit 4 set keep pols 2, 3,
+                // then bit 3 picks one of the two; 12 shuffles instead of 40
+                const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+                const float k0r = (b4 ? acc[2][0] : acc[0][0]) +
+                                  __shfl_xor_sync(0xffffffffu, b4 ? acc[0][0] : acc[2][0], 16);
+                const float k0i = (b4 ? acc[2][1] : acc[0][1]) +
+                                  __shfl_xor_sync(0xffffffffu, b4 ? acc[0][1] : acc[2][1], 16);
+                const float k1r = (b4 ? acc[3][0] : acc[1][0]) +
+                                  __shfl_xor_sync(0xffffffffu, b4 ? acc[1][0] : acc[3][0], 16);
+                const float k1i = (b4 ? acc[3][1] : acc[1][1]) +
+                                  __shfl_xor_sync(0xffffffffu, b4 ? acc[1][1] : acc[3][1], 16);
+                float re = (b3 ? k1r : k0r) + __shfl_xor_sync(0xffffffffu, b3 ? k0r : k1r, 8);
+                float im = (b3 ? k1i : k0i) + __shfl_xor_sync(0xffffffffu, b3 ? k0i : k1i, 8);
 #pragma unroll
-            for (int p = 0; p < NPOL; ++p)
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    acc[p][0] += __shfl_xor_sync(0xffffffffu, acc[p][0], d);
-                    acc[p][1] += __shfl_xor_sync(0xffffffffu, acc[p][1], d);
+                for (int d = 4; d > 0; d >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, d);
+                    im += __shfl_xor_sync(0xffffffffu, im, d);
                 }
-            if (lane < NPOL) {
-                float re = acc[0][0], im = acc[0][1];
+                if ((lane & 7) == 0) {
+                    const int p = (b4 ? 2 : 0) + (b3 ? 1 : 0);
+                    store_vis(a.vis_out, a.vis_kind, (int64_t)id * NPOL + p, re * a.table_inv,
+                              im * a.table_inv);
+                }
+            } else {
 #pragma unroll
-                for (int p = 1; p < NPOL; ++p)
-                    if (lane == p) { re = acc[p][0]; im = acc[p][1]; }
-                store_vis(a.vis_out, a.vis_kind, (int64_t)id * NPOL + lane, re * a.table_inv,
-                          im * a.table_inv);
+                for (int p = 0; p < NPOL; ++p)
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) {
+                        acc[p][0] += __shfl_xor_sync(0xffffffffu, acc[p][0], d);
+                        acc[p][1] += __shfl_xor_sync(0xffffffffu, acc[p][1], d);
+                    }
+                if (lane < NPOL) {
+                    float re = acc[0][0], im = acc[0][1];
+#pragma unroll
+                    for (int p = 1; p < NPOL; ++p)
+                        if (lane == p) { re = acc[p][0]; im = acc[p][1]; }
+                    store_vis(a.vis_out, a.vis_kind, (int64_t)id * NPOL + lane, re * a.table_inv,
+                              im * a.table_inv);
+                }
             }
         }
     }
