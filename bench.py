@@ -40,8 +40,8 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
-GRID_TRAFFIC = {"sha256": "41ac9a99c32049682340a7883ca6648006a181b9a3c3367e41f8e84cbe31f04d",
-                "bytes_per_launch": 1.015117e9 + 0.266591e9,
+GRID_TRAFFIC = {"sha256": "09be8e20dcea51a3014dfe28b6584d337ddb2820f2c8b0161b4a3e154c368638",
+                "bytes_per_launch": 1.011945e9 + 0.265323e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
 
 

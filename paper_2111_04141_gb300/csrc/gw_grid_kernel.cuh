@@ -16,9 +16,10 @@
 //   polarisation.  Four slots per warp amortise each record's staged
 //   visibility over up to 4 x 32 points.
 // * A ninth, producer warp stages batches of records into shared memory
-//   (double-buffered, handed over with named barriers) and, for every record,
+//   (three buffers, handed over with named barriers) and, for every record,
 //   appends it to the list of each compute warp whose block its footprint
-//   meets, together with the range of slots its rows meet.  Compute warps
+//   meets, together with the record's table offset for the tile and the
+//   range of slots its rows meet (one 64-bit entry).  Compute warps
 //   therefore only see records that touch them.
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
 //   rows around each S x S slice, one compile-time row stride per plan), so
@@ -83,30 +84,49 @@ __device__ __forceinline__ void commit_compensated(float2* g, float2* err, float
 
 template <int NPOL, int B>
 struct Smem {
-    int rec[B][kBatch];                    // padded-table index of the tile origin for the record
     float4 v[B][kBatch][NPOL];             // (A.re, A.im, B.re, B.im) per polarisation
-    // per warp: entries meeting all four slots from the front, the others
-    // (r | j0 << 16 | j1 << 20) from the back
-    uint32_t list[B][kComputeWarps][kBatch];
+    // per warp: entries (x: padded-table index of the tile origin relative to
+    // the record, y: r | j0 << 16 | j1 << 20), those meeting all four slots
+    // from the front, the others from the back
+    uint2 list[B][kComputeWarps][kBatch];
     int cnt[B][kComputeWarps];             // entries meeting all four slots
     int cntp[B][kComputeWarps];            // entries meeting some slots
     int tile[B];                           // tile of the batch; -1 = end of work
     int last[B];                           // batch ends its work item
 };
 
+// Packed FMAs of one entry into slots J0..J1 (compile-time range).
+template <int NPOL, int J0, int J1>
+__device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const float2 (&Kc)[4],
+                                         const float4 (&V)[NPOL]) {
+#pragma unroll
+    for (int j = J0; j <= J1; ++j) {
+        const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
+        const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+#pragma unroll
+        for (int p = 0; p < NPOL; ++p) {
+            acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
+            acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+        }
+    }
+}
+
 // One warp's pass over n list entries of a batch.  Software pipeline: the
 // kernel values of entry i + 1 load while entry i's FMAs run (a ring of D
 // register sets, unrolled so no register copies are needed).  FULL: every
-// entry meets all four slots of the warp's block (no per-slot tests).
+// entry meets all four slots of the warp's block (no per-slot tests);
+// otherwise one warp-uniform jump on the entry's slot range selects code
+// for exactly the slots it meets.
 template <int NPOL, int SP, int D, bool FULL, class TE>
-__device__ __forceinline__ void run_entries(const uint32_t* lst, int n, const int* rec,
+__device__ __forceinline__ void run_entries(const uint2* lst, int n,
                                             const float4 (*vs)[NPOL],
                                             const typename TE::T* __restrict__ tab,
                                             float2 (&acc)[4][NPOL]) {
     float2 Kr[D][4];
     uint32_t er[D];
-    auto load_k = [&](uint32_t e, float2 (&K)[4]) {
-        const typename TE::T* p_ = tab + rec[e & 0xffff];
+    auto load_k = [&](uint2 en, float2 (&K)[4]) {
+        const uint32_t e = en.y;
+        const typename TE::T* p_ = tab + (int)en.x;
         if (FULL) {
             K[0] = TE::load(p_);
             K[1] = TE::load(p_ + 4 * SP);
@@ -126,8 +146,9 @@ __device__ __forceinline__ void run_entries(const uint32_t* lst, int n, const in
         er[d] = 0;
         Kr[d][0] = Kr[d][1] = Kr[d][2] = Kr[d][3] = make_float2(0.f, 0.f);
         if (d < n) {
-            er[d] = lst[d];
-            load_k(er[d], Kr[d]);
+            const uint2 en = lst[d];
+            er[d] = en.y;
+            load_k(en, Kr[d]);
         }
     }
     for (int i = 0; i < n; i += D) {
@@ -137,24 +158,30 @@ __device__ __forceinline__ void run_entries(const uint32_t* lst, int n, const in
                 const uint32_t ec = er[d];
                 const float2 Kc[4] = {Kr[d][0], Kr[d][1], Kr[d][2], Kr[d][3]};
                 if (i + d + D < n) {
-                    er[d] = lst[i + d + D];
-                    load_k(er[d], Kr[d]);
+                    const uint2 en = lst[i + d + D];
+                    er[d] = en.y;
+                    load_k(en, Kr[d]);
                 }
                 const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
                 float4 V[NPOL];
 #pragma unroll
                 for (int p = 0; p < NPOL; ++p) V[p] = vs[r][p];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (FULL || (j >= j0 && j <= j1)) {
-                        // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B
-                        const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
-                        const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
-#pragma unroll
-                        for (int p = 0; p < NPOL; ++p) {
-                            acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
-                            acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
-                        }
+                // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B, only
+                // on the slots the entry meets (one warp-uniform jump)
+                if (FULL) {
+                    slot_fma<NPOL, 0, 3>(acc, Kc, V);
+                } else {
+                    switch ((j0 << 2) | j1) {
+                        case 0: slot_fma<NPOL, 0, 0>(acc, Kc, V); break;
+                        case 1: slot_fma<NPOL, 0, 1>(acc, Kc, V); break;
+                        case 2: slot_fma<NPOL, 0, 2>(acc, Kc, V); break;
+                        case 3: slot_fma<NPOL, 0, 3>(acc, Kc, V); break;
+                        case 5: slot_fma<NPOL, 1, 1>(acc, Kc, V); break;
+                        case 6: slot_fma<NPOL, 1, 2>(acc, Kc, V); break;
+                        case 7: slot_fma<NPOL, 1, 3>(acc, Kc, V); break;
+                        case 10: slot_fma<NPOL, 2, 2>(acc, Kc, V); break;
+                        case 11: slot_fma<NPOL, 2, 3>(acc, Kc, V); break;
+                        default: slot_fma<NPOL, 3, 3>(acc, Kc, V); break;
                     }
                 }
             }
@@ -216,7 +243,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                                                   (int64_t)(S + 6) * SP;
                         // padded index of the tile origin relative to this record
                         const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                        sm.rec[buf][r] = base;
                         const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
 #pragma unroll
                         for (int p = 0; p < NPOL; ++p) {
@@ -237,7 +263,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                         for (int cv = cv0; cv <= cv1; ++cv) {
                             const int j0 = max(0, vlo - 16 * cv) >> 2;
                             const int j1 = min(15, vhi - 16 * cv) >> 2;
-                            const uint32_t e = (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20);
+                            const uint2 e = make_uint2((uint32_t)base,
+                                                       (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20));
                             const bool full = j0 == 0 && j1 == 3;
                             for (int cu = cu0; cu <= cu1; ++cu) {
                                 const int w = cv * 4 + cu;
@@ -293,12 +320,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
         if (tile < 0) break;
         const int last = sm.last[buf];
         const int nf = sm.cnt[buf][warp], np = sm.cntp[buf][warp];
-        const uint32_t* lst = sm.list[buf][warp];
+        const uint2* lst = sm.list[buf][warp];
         // entries meeting all four slots: no per-slot tests
-        run_entries<NPOL, SP, D, true, TE>(lst, nf, sm.rec[buf], sm.v[buf], tab, acc);
+        run_entries<NPOL, SP, D, true, TE>(lst, nf, sm.v[buf], tab, acc);
         // entries meeting a subset of the slots
-        run_entries<NPOL, SP, D, false, TE>(lst + kBatch - np, np, sm.rec[buf], sm.v[buf], tab,
-                                            acc);
+        run_entries<NPOL, SP, D, false, TE>(lst + kBatch - np, np, sm.v[buf], tab, acc);
         if (last) {
             // commit the tile's accumulators of this work item
             const int ltile = a.layer_tiles ? tile % a.layer_tiles : tile;
@@ -343,13 +369,14 @@ void launch_v(const GridArgs& a, int num_sms, cudaStream_t s) {
     note_launch();
 }
 
-// Two register sets of kernel values in flight and two staging buffers:
-// measured fastest on the 4-pol w-projection workload among rings of 2-4
-// entries and 2-4 buffers (deeper rings raise register pressure, more
-// buffers gave no gain).
+// Two register sets of kernel values in flight and three staging buffers of
+// 256 records: measured fastest on the 4-pol w-projection workload among
+// rings of 2-4 entries, 2-4 buffers and batches of 128-256 records (deeper
+// rings raise register pressure; a fourth buffer does not fit two CTAs per
+// SM with 64-bit list entries).
 template <int NPOL, int SP, int TK>
 void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
-    launch_v<NPOL, SP, TK, 2, 2>(a, num_sms, s);
+    launch_v<NPOL, SP, TK, 2, 3>(a, num_sms, s);
 }
 
 template <int NPOL, int TK>
