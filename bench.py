@@ -334,8 +334,7 @@ def measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
     with gw.Plan(**kw) as p2:
         g2 = p2.new_grid()
         conv_ms = timed(lambda: p2.grid(uvw, freq, vis, out=g2))
-        fine = torch.zeros((obs.npol, obs.oversample * obs.grid_n, obs.grid_n),
-                           dtype=torch.complex64, device=dev)
+        fine = torch.zeros(p2.fine_shape(), dtype=torch.complex64, device=dev)
         pruned = torch.empty((obs.npol, 2 * obs.grid_n, obs.grid_n), dtype=torch.complex64,
                              device=dev)
         hy_grid_ms = timed(lambda: p2.hybrid_grid(uvw, freq, vis, sz, out=fine))

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 3
+#define GW_API_VERSION 4
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -272,12 +272,14 @@ gw_status gw_wstack_combine(gw_plan plan, const void* layer_images, int32_t n_la
  *   gw_hybrid_grid   Gridding Step: each visibility is convolved along u with
  *                    the plan's oversampled 1-D GCF (support_min taps) and
  *                    put on the nearest of beta*N rows along v:
- *                    fine[pol][kv*beta + ov][ku + t] += c(t - ou/beta) * vis;
- *                    fine: device [npol][beta*N][N] c64, accumulated.
+ *                    fine[kv*beta + ov][ku + t][pol] += c(t - ou/beta) * vis;
+ *                    fine: device [beta*N][N][npol] c64 (polarisations
+ *                    interleaved, so one tap's updates are contiguous),
+ *                    accumulated; 16-byte aligned when npol is even.
  *   gw_hybrid_prune  Pruning Step: each column is sampled down by beta/2 onto
  *                    2N rows through the pruning GCF Z, the zeroth-order PSWF
  *                    with odd support sz on the 2x grid (normalised taps):
- *                    pruned[pol][k][u] = sum_r Z(k - 2r/beta) fine[pol][r][u];
+ *                    pruned[pol][k][u] = sum_r Z(k - 2r/beta) fine[r][u][pol];
  *                    pruned: device [npol][2N][N] c64, overwritten.
  *   gw_hybrid_shift  pruned *= (-1)^(k + u) before an unnormalised inverse FFT.
  *   gw_hybrid_image  Correction Step: keeps rows N/2 .. 3N/2 - 1 of the

@@ -1075,8 +1075,10 @@ gw_status gw_hybrid_grid(gw_plan p, const double* uvw_m, const double* freq_hz, 
     if (nrow > 0 && nchan > 0 && !vis) return fail(GW_EINVAL, "null vis");
     const int vk = p->desc.vis_dtype;
     const size_t vb = dtype_bytes(vk);
-    if ((reinterpret_cast<uintptr_t>(fine) % 8 != 0) || (reinterpret_cast<uintptr_t>(vis) % vb != 0))
-        return fail(GW_EINVAL, "fine must be 8-byte aligned and vis aligned to its element size");
+    const uintptr_t fa = (p->desc.npol % 2 == 0) ? 16 : 8;     // vector atomics over pol pairs
+    if ((reinterpret_cast<uintptr_t>(fine) % fa != 0) || (reinterpret_cast<uintptr_t>(vis) % vb != 0))
+        return fail(GW_EINVAL, "fine must be 16-byte aligned (8 for odd npol) and vis aligned to "
+                               "its element size");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");

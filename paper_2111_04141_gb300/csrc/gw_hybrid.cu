@@ -3,11 +3,16 @@
 //
 //   Gridding Step  k_hybrid_grid: each record is convolved along u with the
 //                  oversampled 1-D GCF (S taps) and put on the nearest of
-//                  beta N rows along v: fine[pol][q_v][k_u + t] += c(t - o_u/beta) V,
+//                  beta N rows along v: fine[q_v][k_u + t][pol] += c(t - o_u/beta) V,
 //                  q_v = k_v beta + o_v.  S updates per record instead of S^2.
+//                  Polarisations are interleaved in the fine grid, so the
+//                  updates of one tap are one contiguous 8 npol-byte run
+//                  (16-byte vector atomics over polarisation pairs).
 //   Pruning Step   k_prune: every column is sampled down by beta/2 onto a
 //                  2x-oversampled v axis through the pruning GCF Z (S_z taps):
-//                  pruned[pol][k][u] = sum_r Z(k - 2r/beta) fine[pol][r][u].
+//                  pruned[pol][k][u] = sum_r Z(k - 2r/beta) fine[r][u][pol];
+//                  the pruners see the fine grid as N npol columns
+//                  c = u npol + pol and write the planar pruned grid.
 //   IFFT Step      (cuFFT, on the 2N x N pruned grid after k_hybrid_shift).
 //   Correction     k_hybrid_image: keep the central N of the 2N rows, re-centre
 //                  and apply h_co(l) h_pr(m).
@@ -66,17 +71,23 @@ __global__ void __launch_bounds__(256) k_hybrid_grid(const gw_index_rec* __restr
             const int t = tt - h;
             const float w = wtab ? ws[(r.ou + hb) * S + tt]
                                  : (float)(__ldg(c1 + beta * t - r.ou - fmin) / norm);
-            const int64_t col = (int64_t)r.ku + t;
-            for (int p = 0; p < npol; ++p) {
-                float2 vv = load_vis(vis, vis_kind, i * npol + p);   // L1 broadcast over the taps
+            float2* dst = fine + ((q * N + r.ku + t) * npol);
+            auto wv = [&](int p) {                          // L1 broadcast over the taps
+                float2 vv = load_vis(vis, vis_kind, i * npol + p);
                 if (weight) {
                     const float ww = __ldg(weight + i * npol + p);
                     vv.x *= ww;
                     vv.y *= ww;
                 }
-                atomicAdd(fine + ((int64_t)p * beta * N + q) * N + col,
-                          make_float2(w * vv.x, w * vv.y));
-            }
+                return make_float2(w * vv.x, w * vv.y);
+            };
+            int p = 0;
+            if (!(npol & 1))                                // 16-byte aligned pairs
+                for (; p + 1 < npol; p += 2) {
+                    const float2 a = wv(p), b = wv(p + 1);
+                    atomicAdd(reinterpret_cast<float4*>(dst + p), make_float4(a.x, a.y, b.x, b.y));
+                }
+            for (; p < npol; ++p) atomicAdd(dst + p, wv(p));
         }
     }
 }
@@ -97,7 +108,8 @@ __global__ void k_prune(const float2* __restrict__ fine, int npol, int N, int be
         const int64_t pk = e / N;
         const int k = (int)(pk % rows2);
         const int p = (int)(pk / rows2);
-        const float2* col = fine + (int64_t)p * fr * N + u;
+        const int64_t C = (int64_t)N * npol;                    // fine-grid row length
+        const float2* col = fine + (int64_t)u * npol + p;
         float ax = 0.f, ay = 0.f;
         for (int t = -hz; t <= hz; ++t) {
             const int64_t rs = (int64_t)(k - t) * hb - beta / 4;
@@ -105,7 +117,7 @@ __global__ void k_prune(const float2* __restrict__ fine, int npol, int N, int be
             const int m1 = rs + hb > fr ? (int)(fr - rs) : hb;
             for (int m = m0; m < m1; ++m) {
                 const float wz = __ldg(z + m * sz + t + hz);
-                const float2 f = col[(rs + m) * N];
+                const float2 f = col[(rs + m) * C];
                 ax = fmaf(wz, f.x, ax);
                 ay = fmaf(wz, f.y, ay);
             }
@@ -114,8 +126,8 @@ __global__ void k_prune(const float2* __restrict__ fine, int npol, int N, int be
     }
 }
 
-// Tiled pruner: a CTA produces R output rows x 32 columns of one
-// polarisation; the fine rows they need ((R + 2 hz + 1) beta / 2 of them) and
+// Tiled pruner: a CTA produces R output rows x 32 fine-grid columns
+// (c = u npol + pol); the fine rows they need ((R + 2 hz + 1) beta / 2 of them) and
 // the Z table are staged in shared memory once, so the fine grid is read
 // from memory about once instead of once per output row.
 constexpr int kPruneCols = 32;
@@ -124,15 +136,15 @@ constexpr int kPruneZMax = 2048;            // staged Z entries (beta/2 * sz)
 constexpr int kPruneThreads = 512;          // two CTAs of 16 warps per SM
 
 __global__ void __launch_bounds__(kPruneThreads) k_prune_tiled(const float2* __restrict__ fine, int N,
-                                                    int beta, int sz, int R,
+                                                    int npol, int beta, int sz, int R,
                                                     const float* __restrict__ z,
                                                     float2* __restrict__ pruned) {
     extern __shared__ __align__(16) float2 tilebuf[];      // [rows][kPruneCols], then Z
     const int hz = sz / 2, hb = beta / 2;
-    const int u0 = blockIdx.x * kPruneCols;
+    const int c0 = blockIdx.x * kPruneCols;
     const int kstart = blockIdx.y * R;
-    const int p = blockIdx.z;
     const int64_t fr = (int64_t)beta * N;
+    const int C = N * npol;                                // fine-grid row length
     int64_t r_lo = (int64_t)(kstart - hz) * hb - beta / 4;
     int64_t r_hi = (int64_t)(kstart + R - 1 + hz) * hb - beta / 4 + hb;
     if (r_lo < 0) r_lo = 0;
@@ -140,18 +152,18 @@ __global__ void __launch_bounds__(kPruneThreads) k_prune_tiled(const float2* __r
     const int nrows = (int)(r_hi - r_lo);                  // <= kPruneRowsMax by the launch
     float* zs = reinterpret_cast<float*>(tilebuf + kPruneRowsMax * kPruneCols);
     for (int e = threadIdx.x; e < hb * sz; e += blockDim.x) zs[e] = z[e];
-    const float2* src = fine + (int64_t)p * fr * N;
     for (int e = threadIdx.x; e < nrows * kPruneCols; e += blockDim.x) {
-        const int rr = e / kPruneCols, c = e - rr * kPruneCols;
-        const int u = u0 + c;
-        tilebuf[e] = u < N ? src[(r_lo + rr) * (int64_t)N + u] : make_float2(0.f, 0.f);
+        const int rr = e / kPruneCols, cc = e - rr * kPruneCols;
+        const int cg = c0 + cc;
+        tilebuf[e] = cg < C ? fine[(r_lo + rr) * (int64_t)C + cg] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int c = threadIdx.x % kPruneCols;
-    const int u = u0 + c;
+    const int cg = c0 + c;
+    const int u = cg / npol, p = cg - u * npol;
     for (int kk = threadIdx.x / kPruneCols; kk < R; kk += blockDim.x / kPruneCols) {
         const int k = kstart + kk;
-        if (k >= 2 * N || u >= N) continue;
+        if (k >= 2 * N || cg >= C) continue;
         float ax = 0.f, ay = 0.f;
         for (int t = -hz; t <= hz; ++t) {
             const int64_t rs = (int64_t)(k - t) * hb - beta / 4;     // first row of k' = k - t
@@ -204,7 +216,8 @@ __global__ void k_hybrid_image(const float2* __restrict__ raw, int npol, int N,
 
 // Streaming pruner.  The pruning of one column is a polyphase filter: fine
 // row r (2x row k' = nearest, offset m) feeds the S_z output rows
-// k' - hz .. k' + hz.  A thread owns one column and a segment of output rows
+// k' - hz .. k' + hz.  A thread owns one fine-grid column (one polarisation
+// of one u; a warp reads 32 contiguous ones) and a segment of output rows
 // and walks the 2x rows k' in order: it reads the beta/2 fine rows of k'
 // once (coalesced across the warp, streaming loads), adds them into a ring of
 // S_z register accumulators and stores output row k' - hz, which no later k'
@@ -220,25 +233,26 @@ struct PruneZ {
 
 template <int HB>
 __device__ __forceinline__ void prune_rows(const float2* __restrict__ col, int64_t r0, int64_t fr,
-                                           int N, float2 (&f)[HB]) {
+                                           int64_t C, float2 (&f)[HB]) {
 #pragma unroll
     for (int m = 0; m < HB; ++m) {
         const int64_t r = r0 + m;
-        f[m] = (r >= 0 && r < fr) ? __ldcs(col + r * N) : make_float2(0.f, 0.f);
+        f[m] = (r >= 0 && r < fr) ? __ldcs(col + r * C) : make_float2(0.f, 0.f);
     }
 }
 
 template <int HB, int SZ>
-__global__ void __launch_bounds__(256) k_prune_stream(const float2* __restrict__ fine, int N, int L,
-                                                      const PruneZ<HB, SZ> Z,
+__global__ void __launch_bounds__(256) k_prune_stream(const float2* __restrict__ fine, int N,
+                                                      int npol, int L, const PruneZ<HB, SZ> Z,
                                                       float2* __restrict__ pruned) {
     constexpr int hz = SZ / 2;
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= N) return;
-    const int p = blockIdx.z;
+    const int64_t C = (int64_t)N * npol;           // fine-grid row length (columns c = u npol + pol)
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int u = (int)(c / npol), p = (int)(c - (int64_t)u * npol);
     const int64_t fr = (int64_t)2 * HB * N;        // beta N fine rows
     const int rows2 = 2 * N;
-    const float2* col = fine + (int64_t)p * fr * N + u;
+    const float2* col = fine + c;
     float2* out = pruned + (int64_t)p * rows2 * N + u;
     const int kb = blockIdx.y * L;                 // this thread's output rows [kb, ke)
     const int ke = min(kb + L, rows2);
@@ -255,14 +269,14 @@ __global__ void __launch_bounds__(256) k_prune_stream(const float2* __restrict__
     // beta = 8, 1 for beta = 16 to bound the registers)
     constexpr int PD = HB == 4 ? 2 : 1;
     float2 fa[HB], fb[HB];
-    prune_rows<HB>(col, (int64_t)g0 * HB - HB / 2, fr, N, fa);
-    if (PD == 2) prune_rows<HB>(col, (int64_t)(g0 + 1) * HB - HB / 2, fr, N, fb);
+    prune_rows<HB>(col, (int64_t)g0 * HB - HB / 2, fr, C, fa);
+    if (PD == 2) prune_rows<HB>(col, (int64_t)(g0 + 1) * HB - HB / 2, fr, C, fb);
     for (int g = g0; g <= glast; g += SZ) {
 #pragma unroll
         for (int i = 0; i < SZ; ++i) {
             const int kp = g + i;
             float2 fc[HB];                          // PD 2x rows ahead
-            prune_rows<HB>(col, (int64_t)(kp + PD) * HB - HB / 2, fr, N, fc);
+            prune_rows<HB>(col, (int64_t)(kp + PD) * HB - HB / 2, fr, C, fc);
 #pragma unroll
             for (int t = -hz; t <= hz; ++t) {
                 const int q = (i + t + SZ) % SZ;    // accumulator of output kp + t
@@ -305,8 +319,8 @@ void launch_prune_stream(const float2* fine, int npol, int N, const float* h_z, 
     int64_t L = (2LL * N + nseg - 1) / nseg;
     if (L < SZ) L = SZ;
     nseg = (2LL * N + L - 1) / L;
-    const dim3 grid((unsigned)((N + 255) / 256), (unsigned)nseg, (unsigned)npol);
-    k_prune_stream<HB, SZ><<<grid, 256, 0, s>>>(fine, N, (int)L, Z, pruned);
+    const dim3 grid((unsigned)((cols + 255) / 256), (unsigned)nseg, 1u);
+    k_prune_stream<HB, SZ><<<grid, 256, 0, s>>>(fine, N, npol, (int)L, Z, pruned);
 }
 
 template <int HB>
@@ -360,9 +374,9 @@ void launch_prune(const float2* fine, int npol, int N, int beta, int sz, const f
         const size_t smem = sizeof(float2) * kPruneRowsMax * kPruneCols + sizeof(float) * kPruneZMax;
         cudaFuncSetAttribute(k_prune_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        const dim3 grid((N + kPruneCols - 1) / kPruneCols, (unsigned)((2LL * N + R - 1) / R),
-                        (unsigned)npol);
-        k_prune_tiled<<<grid, kPruneThreads, smem, s>>>(fine, N, beta, sz, R, z, pruned);
+        const dim3 grid((unsigned)(((int64_t)N * npol + kPruneCols - 1) / kPruneCols),
+                        (unsigned)((2LL * N + R - 1) / R), 1u);
+        k_prune_tiled<<<grid, kPruneThreads, smem, s>>>(fine, N, npol, beta, sz, R, z, pruned);
     } else {
         k_prune<<<blocks_for((int64_t)npol * 2 * N * N), 256, 0, s>>>(fine, npol, N, beta, sz, z,
                                                                      pruned);

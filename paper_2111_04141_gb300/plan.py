@@ -283,12 +283,13 @@ class Plan:
 
     def hybrid_grid(self, uvw, freq, vis, sz, weight=None, out=None, stream=None,
                     return_dropped=False):
-        """Hybrid Gridding Step onto the fine grid [npol, beta N, N]."""
+        """Hybrid Gridding Step onto the fine grid [beta N, N, npol]
+        (polarisations interleaved)."""
         nrow, nchan = self._coords(uvw, freq)
         vis = self._vis_arg(vis, "vis", nrow, nchan)
         if weight is not None:
             _need(weight, "weight", torch.float32, self.device, (nrow, nchan, self.npol))
-        shape = (self.npol, self.desc.oversample * self.grid_n, self.grid_n)
+        shape = self.fine_shape()
         if out is None:
             out = torch.zeros(shape, dtype=torch.complex64, device=self.device)
         _need(out, "fine", torch.complex64, self.device, shape)
@@ -300,10 +301,13 @@ class Plan:
                                            _stream_ptr(stream, self.device)), "gw_hybrid_grid")
         return (out, int(nd.value)) if return_dropped else out
 
+    def fine_shape(self):
+        """Shape of the Hybrid Gridding fine grid: (beta N, N, npol)."""
+        return (self.desc.oversample * self.grid_n, self.grid_n, self.npol)
+
     def hybrid_prune(self, sz, fine, out=None, stream=None):
         shape = (self.npol, 2 * self.grid_n, self.grid_n)
-        _need(fine, "fine", torch.complex64, self.device,
-              (self.npol, self.desc.oversample * self.grid_n, self.grid_n))
+        _need(fine, "fine", torch.complex64, self.device, self.fine_shape())
         if out is None:
             out = torch.empty(shape, dtype=torch.complex64, device=self.device)
         _need(out, "pruned", torch.complex64, self.device, shape)

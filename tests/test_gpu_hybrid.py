@@ -33,10 +33,11 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-# (8, 15), (8, 7), (16, 9): streaming pruner; (8, 17): shared-memory tiled pruner
-@pytest.mark.parametrize("beta,sz", [(8, 15), (8, 7), (16, 9), (8, 17)])
-def test_hybrid_steps_match_oracle(gw, beta, sz):
-    obs = syn.small_case(n_ant=7, n_times=10, n_chan=3, npol=2, grid_n=128, s_min=7, s_max=7,
+# (8, 15), (8, 7), (16, 9): streaming pruner; (8, 17): shared-memory tiled pruner.
+# Even npol: 16-byte atomics over polarisation pairs; odd npol: 8-byte ones.
+@pytest.mark.parametrize("beta,sz,npol", [(8, 15, 2), (8, 7, 4), (16, 9, 1), (8, 17, 3)])
+def test_hybrid_steps_match_oracle(gw, beta, sz, npol):
+    obs = syn.small_case(n_ant=7, n_times=10, n_chan=3, npol=npol, grid_n=128, s_min=7, s_max=7,
                          n_w=1, diameter_m=1500.0, beta=beta)
     prm = Params(**obs.plan_kwargs())
     orc = Oracle(prm)
@@ -55,7 +56,8 @@ def test_hybrid_steps_match_oracle(gw, beta, sz):
         plan.hybrid_shift(pruned)
         raw = torch.fft.ifft2(pruned, norm="forward")
         img = plan.hybrid_image(sz, raw).cpu().numpy().astype(np.complex128)
-        fine = fine.cpu().numpy().astype(np.complex128)
+        # [beta N, N, npol] (pols interleaved) -> the oracle's [npol, beta N, N]
+        fine = np.moveaxis(fine.cpu().numpy().astype(np.complex128), 2, 0)
     assert dropped == int((~keep).sum())
     assert rel_l2(fine, fine_ref) <= 1e-5
     assert rel_l2(pr, pruned_ref) <= 1e-5
