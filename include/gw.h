@@ -246,9 +246,9 @@ gw_status gw_grid_vis_compressed(gw_plan plan, const double* uvw_m, const double
  * dw = (w_max - w_min) / (n_layers - 1), computed in FP64 like the index
  * stage (records beyond the range use the outermost layer).
  *   layers  device, [n_layers][npol][N][N] c64, accumulated (+=)
- * Other arguments as gw_grid_vis.  The image is then formed per layer
- * (gw_grid_shift, an unnormalised inverse FFT) and combined with
- * gw_wstack_combine, then gw_grid_correct(+1).  The first call allocates
+ * Other arguments as gw_grid_vis.  The image is then formed by an
+ * unnormalised inverse FFT of each layer grid, gw_wstack_combine (which
+ * applies the centring shift), then gw_grid_correct(+1).  The first call allocates
  * the plan's layered bins.  Errors: GW_EINVAL, GW_EDEVICE, GW_ENOMEM, GW_ECUDA. */
 gw_status gw_grid_vis_wstack(gw_plan plan, const double* uvw_m, const double* freq_hz,
                              int64_t nrow, int32_t nchan, const void* vis, const float* weight,
@@ -259,8 +259,12 @@ gw_status gw_grid_vis_wstack(gw_plan plan, const double* uvw_m, const double* fr
  * w_l = w_min + l dw as in gw_grid_vis_wstack, n_ij - 1 = -r^2 / (1 + sqrt(1 - r^2)),
  * r^2 = l_j^2 + m_i^2, l_j = (j - N/2) cell_rad, m_i = (i - N/2) cell_rad: the
  * w-screen correction of each layer's image (Eq. (lmwcorr)) and their sum.
- * The screen is formed in FP64.  layer_images: device [n_layers][npol][N][N]
- * c64 (the inverse transforms of the shifted layer grids); image: device
+ * n_ij - 1 and each screen's phase are formed in FP64 and reduced modulo 2 pi;
+ * the screens (a rotation recursion re-anchored every 8 layers) and the sum
+ * are FP32.  layer_images: device [n_layers][npol][N][N]
+ * c64, the unnormalised inverse FFTs of the layer grids as gridded (not
+ * shifted: the centring, a circular shift by N/2 of each transform, is
+ * applied in the read; N even); image: device
  * [npol][N][N] c64, accumulated.  Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA. */
 gw_status gw_wstack_combine(gw_plan plan, const void* layer_images, int32_t n_layers,
                             double w_min_lambda, double w_max_lambda, void* image,

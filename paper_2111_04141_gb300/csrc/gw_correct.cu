@@ -67,6 +67,21 @@ __global__ void k_zero_vis(uint32_t* __restrict__ v, int64_t n_max, int words, D
 // the screen of layer l at pixel (i, j) is exp(+j 2 pi w_l (n - 1)) with
 // n - 1 = -r^2 / (1 + sqrt(1 - r^2)), r^2 = l_j^2 + m_i^2; it is formed in
 // FP64 as screen_0 * rot^l, rot = exp(+j 2 pi dw (n - 1)).
+// exp(+j pi a) for a phase a in units of pi: a is reduced to [-1, 1] in FP64
+// (exact for the |a| of any w-screen), then evaluated in FP32.
+__device__ __forceinline__ void screen_pi(double a, float& s, float& c) {
+    const double r = a - 2.0 * rint(0.5 * a);
+    sincospif((float)r, &s, &c);
+}
+
+// Sum of the layer images times their w-screens exp(+j 2 pi w_l (n - 1)),
+// w_l = wmin + l dw.  n - 1 is computed in FP64 (w (n - 1) reaches hundreds
+// of radians); the screens follow a rotation recursion in FP32 from an
+// anchor recomputed every 8 layers, and the sum is FP32.  The layer images
+// are the inverse transforms of the unshifted layer grids: the centring
+// factor (-1)^(u + v) of the grid is the circular shift by N/2 of its
+// transform, applied here in the read (N is even).  One thread per pixel;
+// the layers are read once, coalesced, so the kernel is HBM bound.
 __global__ void k_wstack_combine(const float2* __restrict__ layers, int nlayers, double wmin,
                                  double dw, int N, int npol, double cell,
                                  float2* __restrict__ image) {
@@ -77,25 +92,28 @@ __global__ void k_wstack_combine(const float2* __restrict__ layers, int nlayers,
         const double l = (j - N / 2) * cell, m = (i - N / 2) * cell;
         const double r2 = l * l + m * m;
         const double nm1 = r2 < 1.0 ? -r2 / (1.0 + sqrt(1.0 - r2)) : 0.0;
-        double s0, c0, s1, c1;
-        sincospi(2.0 * wmin * nm1, &s0, &c0);
-        sincospi(2.0 * dw * nm1, &s1, &c1);
-        double cr = c0, ci = s0;                     // screen of layer 0
-        double acc[4][2] = {};
+        const int is = i + N / 2 < N ? i + N / 2 : i - N / 2;
+        const int js = j + N / 2 < N ? j + N / 2 : j - N / 2;
+        const int64_t es = (int64_t)is * N + js;      // pixel of the unshifted transform
+        float s1, c1;                                 // one layer step
+        screen_pi(2.0 * dw * nm1, s1, c1);
+        float acc[4][2] = {};
+        float cr = 1.f, ci = 0.f;
         for (int L = 0; L < nlayers; ++L) {
+            if ((L & 7) == 0) screen_pi(2.0 * (wmin + L * dw) * nm1, ci, cr);
             for (int p = 0; p < npol && p < 4; ++p) {
-                const float2 v = layers[((int64_t)L * npol + p) * n + e];
-                acc[p][0] += v.x * cr - v.y * ci;
-                acc[p][1] += v.x * ci + v.y * cr;
+                const float2 v = __ldcs(layers + ((int64_t)L * npol + p) * n + es);
+                acc[p][0] = fmaf(v.x, cr, fmaf(-v.y, ci, acc[p][0]));
+                acc[p][1] = fmaf(v.x, ci, fmaf(v.y, cr, acc[p][1]));
             }
-            const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
+            const float nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
             cr = nr;
             ci = ni;
         }
         for (int p = 0; p < npol && p < 4; ++p) {
             float2 o = image[(int64_t)p * n + e];
-            o.x += (float)acc[p][0];
-            o.y += (float)acc[p][1];
+            o.x += acc[p][0];
+            o.y += acc[p][1];
             image[(int64_t)p * n + e] = o;
         }
     }

@@ -55,13 +55,12 @@ def model_vis(plan, uvw, freq, image: torch.Tensor, stream=None) -> torch.Tensor
 def dirty_image_wstack(plan, uvw, freq, vis, n_layers: int, w_min: float, w_max: float,
                        normalise: bool = True, stream=None) -> torch.Tensor:
     """Dirty image by w-stacking (Section 1.7.1): a 2-D plan grids every
-    visibility onto the grid of its w-layer; each layer grid is shifted and
-    inverse transformed, multiplied by its w-screen exp(+j 2 pi w_l (n - 1))
-    and summed (gw_wstack_combine); the sum is corrected once."""
+    visibility onto the grid of its w-layer; each layer grid is inverse
+    transformed, re-centred, multiplied by its w-screen
+    exp(+j 2 pi w_l (n - 1)) and summed (gw_wstack_combine, which also does
+    the re-centring); the sum is corrected once."""
     layers, dropped = plan.grid_wstack(uvw, freq, vis, n_layers, w_min, w_max, stream=stream,
                                        return_dropped=True)
-    for l in range(layers.shape[0]):
-        plan.shift(layers[l], stream=stream)
     imgs = torch.fft.ifft2(layers, norm="forward")
     del layers
     img = plan.new_grid()

@@ -68,9 +68,12 @@ def test_wstacked_image_matches_oracle(gw):
     assert rel_l2(img[:, c, c].astype(np.complex128), ref[:, c, c]) <= 2e-5
 
 
-def test_wstacked_image_matches_direct_sum_for_layer_exact_records(gw):
+# (3000, 17): w-screen phases beyond 100 rad and a screen recursion that
+# crosses two re-anchoring layers
+@pytest.mark.parametrize("w_max,L", [(300.0, 5), (3000.0, 17)])
+def test_wstacked_image_matches_direct_sum_for_layer_exact_records(gw, w_max, L):
     from paper_2111_04141_gb300.imaging import dirty_image_wstack
-    N, w_max, L = 64, 300.0, 5
+    N = 64
     kw = dict(grid_n=N, cell_rad=0.3 / N, support_min=15, support_max=15, oversample=8,
               n_wplanes=1, w_max_lambda=0.0, npol=1)
     prm_w = Params(**{**kw, "n_wplanes": 2, "w_max_lambda": w_max})
