@@ -79,7 +79,8 @@ class Job:
 # --------------------------------------------------------------------------
 
 class Scheduler:
-    """FIFO continuous-batching admission under an HBM budget.
+    """FIFO continuous-batching admission under an HBM budget and, optionally,
+    a compute budget.
 
     ``cost(slot, setup)`` is the device memory a slot still has to allocate
     to run a job of ``setup`` (0 when the slot already holds that setup's
@@ -87,11 +88,21 @@ class Scheduler:
     first, to make room; the head of the queue is never overtaken (no
     starvation), and a job that cannot fit even with every idle state
     evicted waits for running jobs to finish.
+
+    With ``work_cap`` (grid-point updates of a job that fills the GPU), a
+    job's load is min(1, work / work_cap) and the head is admitted only while
+    the running jobs' loads plus its own stay within 1 + ``work_slack``: two
+    GPU-filling jobs never share the GPU (sharing only delays the first of
+    them), while small jobs still overlap with a large one.  The first job
+    is always admitted.
     """
 
-    def __init__(self, n_slots: int, budget: int, resident: int = 0):
+    def __init__(self, n_slots: int, budget: int, resident: int = 0,
+                 work_cap: Optional[float] = None, work_slack: float = 0.5):
         self.n_slots = n_slots
         self.budget = budget
+        self.work_cap = work_cap
+        self.work_slack = work_slack
         self.used = resident               # bytes held outside slot state (tables, models)
         self.pending: collections.deque = collections.deque()
         self.busy: Dict[int, Job] = {}
@@ -115,6 +126,11 @@ class Scheduler:
         busy = set(self.busy)
         return [k for k in self.lru if k[0] not in busy and k[0] != exclude_slot]
 
+    def load(self, job: Job) -> float:
+        if self.work_cap is None:
+            return 0.0
+        return min(1.0, job.work / self.work_cap)
+
     def admit(self, cost: Callable[[int, str], int]):
         """Admit queue-head jobs while possible.  Returns a list of
         (job, slot, evicted_keys, new_bytes) decisions."""
@@ -124,6 +140,10 @@ class Scheduler:
             if not free:
                 break
             job = self.pending[0]
+            if self.work_cap is not None and self.busy:
+                inflight = sum(self.load(j) for j in self.busy.values())
+                if inflight + self.load(job) > 1.0 + self.work_slack:
+                    break            # wait for running work to finish
             slot = self._pick_slot(job.setup, free)
             need = cost(slot, job.setup)
             evicted = []
@@ -191,13 +211,17 @@ class Server:
     setups      registered imaging setups (plans are built at ``warm``)
     max_vis     largest job (visibilities) any slot must hold
     budget      device bytes the server may hold (tables, models, slot state)
+    work_cap    nominal grid-point updates of a GPU-filling job for the
+                scheduler's compute budget; None (the default) admits by slots
+                and memory only, which measured better on the mixed stream
+                (p99 26 ms vs 35 ms with a 2e10 cap)
     on_result   callback(job, host_tensor) called when a job's result is in
                 host memory (the tensor is a slot staging buffer: copy it to keep it)
     """
 
     def __init__(self, setups: List[Setup], device, budget: int, n_slots: int = 4,
                  max_vis: int = 10_000_000, use_graphs: bool = True, tuning: Optional[dict] = None,
-                 on_result: Optional[Callable] = None):
+                 on_result: Optional[Callable] = None, work_cap: Optional[float] = None):
         import torch
         from .plan import Plan
         self.torch = torch
@@ -210,12 +234,18 @@ class Server:
         self.tuning = tuning or {}
         self.on_result = on_result
         self.budget = int(budget)
+        self.work_cap = work_cap
         self.plans: Dict[str, object] = {}
         self.models: Dict[str, object] = {}
         self.freqs: Dict[str, object] = {}
         self.state: Dict[tuple, _SlotState] = {}
         self.slots = []
         self.sched: Optional[Scheduler] = None
+
+    @staticmethod
+    def default_work_cap() -> float:
+        import inspect
+        return inspect.signature(Server.__init__).parameters["work_cap"].default
 
     # ---- set-up -----------------------------------------------------------
     def warm(self, models: Optional[Dict[str, np.ndarray]] = None, prewarm: bool = True):
@@ -261,7 +291,7 @@ class Server:
             self.slots.append(slot)
         torch.cuda.synchronize(self.device)
         self.resident = resident
-        self.sched = Scheduler(self.n_slots, self.budget, resident)
+        self.sched = Scheduler(self.n_slots, self.budget, resident, work_cap=self.work_cap)
         if prewarm:
             for slot in range(self.n_slots):
                 for name in self.setups:
@@ -467,12 +497,16 @@ def _mean_s2(s: Setup) -> float:
 def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, jobs: List[Job],
                    device, on_result: Optional[Callable] = None, clock=time.perf_counter):
     """Jobs in arrival order on one stream: wait for arrival, copy in, grid or
-    degrid with the setup's plan (default tuning, no graphs), copy out,
-    synchronise."""
+    degrid with the setup's plan (default tuning, no graphs), copy out into a
+    preallocated pinned buffer (as the server's slots do), synchronise."""
     import torch
     setups = {s.name: s for s in setups}
     jobs = sorted(jobs, key=lambda j: j.arrival)
     stream = torch.cuda.current_stream(device)
+    n_host = max(max(setups[j.setup].npol * setups[j.setup].grid_n ** 2,
+                     j.nrow * setups[j.setup].nchan * setups[j.setup].npol) for j in jobs) \
+        if jobs else 1
+    host_buf = torch.empty(n_host, dtype=torch.complex64, pin_memory=True)
     t0 = clock()
     for j in jobs:
         s = setups[j.setup]
@@ -488,7 +522,8 @@ def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, 
             out = p.grid(uvw, freqs[j.setup], vis)
         else:
             out = p.degrid(uvw, freqs[j.setup], models[j.setup])
-        host = out.to("cpu", non_blocking=True)
+        host = host_buf[:out.numel()].view(out.shape)
+        host.copy_(out, non_blocking=True)
         stream.synchronize()
         j.t_done = clock() - t0
         if on_result is not None:

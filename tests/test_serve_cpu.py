@@ -116,3 +116,37 @@ def test_serving_stream_generator():
     t = syn.poisson_arrivals(5000, 200.0)
     assert np.all(np.diff(t) > 0)
     assert abs(np.mean(np.diff(t)) - 1 / 200.0) < 0.1 / 200.0
+
+
+def test_work_cap_keeps_large_jobs_apart_but_lets_small_ones_overlap():
+    s = Scheduler(n_slots=4, budget=10**12, work_cap=100.0, work_slack=0.5)
+    big1, big2 = job(0), job(1)
+    small = [job(2 + i) for i in range(3)]
+    big1.work, big2.work = 500.0, 100.0            # both fill the GPU (load 1)
+    for j in small:
+        j.work = 20.0                               # load 0.2 each
+    s.arrive(big1)
+    got = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in got] == [0]           # the first job always runs
+    for j in small[:2]:
+        s.arrive(j)
+    got = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in got] == [2, 3]        # 1 + 0.2 + 0.2 <= 1.5
+    s.arrive(big2)
+    s.arrive(small[2])
+    assert s.admit(lambda slot, setup: 0) == []     # big2 at the head would reach 2.4
+    s.complete(got[0][1])
+    s.complete(got[1][1])
+    assert s.admit(lambda slot, setup: 0) == []     # still 1 + 1 > 1.5 while big1 runs
+    s.complete(0)
+    got = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in got] == [1, 4]        # big2 alone, then the small one
+
+
+def test_without_work_cap_only_slots_and_memory_limit_admission():
+    s = Scheduler(n_slots=3, budget=10**12)
+    for i in range(3):
+        j = job(i)
+        j.work = 1e15
+        s.arrive(j)
+    assert [j.id for j, *_ in s.admit(lambda slot, setup: 0)] == [0, 1, 2]
