@@ -43,16 +43,18 @@ __global__ void k_index(const double* __restrict__ uvw, const double* __restrict
                         int64_t nrow, const int64_t* __restrict__ d_nrow, int nchan,
                         IndexParams p, gw_index_rec* __restrict__ out,
                         unsigned long long* __restrict__ dropped) {
-    // [nc] channel factors f / c0, then [P - 1] plane thresholds
+    // [nc] channel factors f / c0, then [P - 1] plane thresholds as bit
+    // patterns: non-negative finite doubles order like their int64 bits, so
+    // the search compares integers (exactly the FP64 comparison)
     extern __shared__ double sh[];
     const int nc = min(nchan, kChanCache);
     const int nthr = p.P > 1 ? p.P - 1 : 0;
     double* sc = sh;
-    double* thr = sh + nc;
+    long long* thr = reinterpret_cast<long long*>(sh + nc);
     for (int c = threadIdx.x; c < nc; c += blockDim.x) sc[c] = __ddiv_rn(__ldg(freq + c), kC0);
     for (int j = threadIdx.x; j < nthr; j += blockDim.x) {
         const double t = __ddiv_rn((double)j + 0.5, p.Pm1_d);      // (j + 1) - 1/2, exact
-        thr[j] = __dmul_rn(__dmul_rn(t, t), p.wmax);
+        thr[j] = __double_as_longlong(__dmul_rn(__dmul_rn(t, t), p.wmax));
     }
     __syncthreads();
     if (d_nrow) nrow = min(nrow, *d_nrow);     // row count read on the device
@@ -78,7 +80,7 @@ __global__ void k_index(const double* __restrict__ uvw, const double* __restrict
             okw = isfinite(wl);
             if (okw) {
                 // number of thresholds <= |w| (first index with thr > |w|)
-                const double a = fabs(wl);
+                const long long a = __double_as_longlong(fabs(wl));
                 int lo = 0, hi = nthr;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
