@@ -163,6 +163,28 @@ gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream
 gw_status gw_plan_set_tuning(gw_plan plan, const gw_tuning* tuning);
 gw_status gw_plan_get_tuning(gw_plan plan, gw_tuning* out);
 
+/* Test hooks (no thesis counterpart).  gw_debug_fail_alloc(n), n > 0: the
+ * n-th allocation the library makes from now on (device memory, or the host
+ * objects of a plan) fails as if the device or host were out of memory, and
+ * the hook switches itself off; n = 0 switches it off.  The failing call
+ * returns GW_ENOMEM after freeing what it had allocated; nothing reaches the
+ * GPU.  Process-wide, not thread-safe with concurrent plan calls; meant for
+ * tests of the error paths.  gw_debug_live_plans(): plans (and clones)
+ * created and not yet destroyed in this process; gw_debug_live_bytes(): bytes
+ * of device memory the library has allocated and not freed. */
+gw_status gw_debug_fail_alloc(int64_t n);
+int64_t gw_debug_live_plans(void);
+int64_t gw_debug_live_bytes(void);
+
+/* Synchronises `cuda_stream` and reads the plan's device status word (no
+ * thesis counterpart): GW_ETIMEDOUT if, since the last check, a bounded
+ * device-side wait of the gridding kernel gave up (its producer / consumer
+ * hand-over waits at most about two seconds; the kernel then returns and
+ * that call's grid is incomplete), else GW_OK.  The word is cleared when
+ * read.  Calls that return n_dropped check it the same way.
+ * Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA, GW_ETIMEDOUT. */
+gw_status gw_plan_device_status(gw_plan plan, void* cuda_stream);
+
 /* Free all device memory of the plan.  NULL is accepted.  The caller must
  * ensure no work using the plan is still in flight. */
 gw_status gw_plan_destroy(gw_plan plan);
@@ -321,12 +343,16 @@ gw_status gw_degrid_vis(gw_plan plan, const double* uvw_m, const double* freq_hz
  * process whose device memory is all handed to another allocator at
  * start-up, or a loop that must not take the driver's allocation lock).
  * Same contract and result as gw_degrid_vis, but its scratch (index records
- * and centre-tile bins) lives in one file-scope device array of about 2.5 MiB
- * that every GPU loading the library holds until exit; nothing is allocated.
+ * and centre-tile bins) lives in one file-scope device array of about
+ * 2.25 MiB (2,360,320 bytes) that every GPU loading the library holds until
+ * exit; nothing is allocated.  The driver allocates that array when it loads
+ * the library module that holds it, which gw_plan_create does (together with
+ * every kernel this call launches), so a process that creates its plans
+ * before handing its device memory to another allocator can call this
+ * without any allocation.  Each call looks up the array's device address
+ * (cudaGetSymbolAddress, no allocation once loaded).
  * Limits: nrow * nchan <= 65536 and grid_n <= 8192, else GW_EINVAL with the
- * limit in gw_last_error().  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  All calls share the one array and each call overwrites
+ * limit in gw_last_error().  All calls share the one array and each call overwrites
  * it: calls whose GPU work overlaps (different streams, or different plans
  * on the same device) race; serialise them. */
 gw_status gw_degrid_vis_static(gw_plan plan, const double* uvw_m, const double* freq_hz,

@@ -93,6 +93,10 @@ _SIGS = {
     "gw_plan_timing_enable": (c_i32, [c_vp, c_i32]),
     "gw_plan_timing_get": (c_i32, [c_vp, ctypes.POINTER(Timing)]),
     "gw_debug_bins": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp]),
+    "gw_debug_fail_alloc": (c_i32, [c_i64]),
+    "gw_debug_live_plans": (c_i64, []),
+    "gw_debug_live_bytes": (c_i64, []),
+    "gw_plan_device_status": (c_i32, [c_vp, c_vp]),
 }
 
 EXPORTED = tuple(_SIGS)

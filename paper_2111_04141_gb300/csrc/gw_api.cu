@@ -2,6 +2,9 @@
 // See include/gw.h for the contract of every entry point.
 #include "gw_internal.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +17,52 @@ namespace gw {
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Allocation-failure injection (gw_debug_fail_alloc): > 0 counts down the
+// allocations still allowed to succeed plus one; the allocation that takes
+// it from 1 to 0 fails.  0 = off.
+static std::atomic<int64_t> g_fail_countdown{0};
+static std::atomic<int64_t> g_live_plans{0};
+
+bool alloc_fault() {
+    int64_t k = g_fail_countdown.load();
+    while (k > 0) {
+        if (g_fail_countdown.compare_exchange_weak(k, k - 1)) return k == 1;
+    }
+    return false;
+}
+
+// Live device allocations of the library (gw_debug_live_bytes).
+static std::mutex g_alloc_mutex;
+static std::unordered_map<void*, size_t> g_allocs;
+static int64_t g_live_bytes = 0;
+
+cudaError_t dev_alloc(void** ptr, size_t bytes) {
+    if (alloc_fault()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        g_allocs[*ptr] = bytes;
+        g_live_bytes += (int64_t)bytes;
+    }
+    return e;
+}
+
+void dev_free(void* ptr) {
+    if (!ptr) return;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        auto it = g_allocs.find(ptr);
+        if (it != g_allocs.end()) {
+            g_live_bytes -= (int64_t)it->second;
+            g_allocs.erase(it);
+        }
+    }
+    cudaFree(ptr);
+}
 
 static thread_local std::string t_last_error;
 
@@ -29,7 +78,13 @@ static gw_status fail(gw_status st, const char* fmt, ...) {
 }
 
 static gw_status cuda_fail(cudaError_t e, const char* where) {
-    return fail(GW_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? GW_ENOMEM : GW_ECUDA, "%s: %s (%s)", where,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+template <class T>
+static T* host_new() {
+    return alloc_fault() ? nullptr : new (std::nothrow) T;
 }
 
 }  // namespace gw
@@ -118,45 +173,45 @@ namespace {
 
 void free_tables(float2* table, uint32_t* table16, void* ptable, int64_t* d_pplane_off,
                  int64_t* d_plane_off, int* d_support, double* d_h, float* d_hf) {
-    cudaFree(table);
-    cudaFree(table16);
-    cudaFree(ptable);
-    cudaFree(d_pplane_off);
-    cudaFree(d_plane_off);
-    cudaFree(d_support);
-    cudaFree(d_h);
-    cudaFree(d_hf);
+    dev_free(table);
+    dev_free(table16);
+    dev_free(ptable);
+    dev_free(d_pplane_off);
+    dev_free(d_plane_off);
+    dev_free(d_support);
+    dev_free(d_h);
+    dev_free(d_hf);
 }
 
 void plan_free(gw_plan p) {
     if (!p) return;
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
-    cudaFree(p->sc.work);
-    cudaFree(p->sc.wvis);
-    cudaFree(p->cs.keys);
-    cudaFree(p->cs.acc);
-    cudaFree(p->cs.rec);
-    cudaFree(p->cs.vis);
-    cudaFree(p->cs.count);
-    cudaFree(p->ws_count);
-    cudaFree(p->ws_offsets);
-    cudaFree(p->ws_cursor);
-    cudaFree(p->ws_item_off);
-    cudaFree(p->ws_items);
+    dev_free(p->sc.work);
+    dev_free(p->sc.wvis);
+    dev_free(p->cs.keys);
+    dev_free(p->cs.acc);
+    dev_free(p->cs.rec);
+    dev_free(p->cs.vis);
+    dev_free(p->cs.count);
+    dev_free(p->ws_count);
+    dev_free(p->ws_offsets);
+    dev_free(p->ws_cursor);
+    dev_free(p->ws_item_off);
+    dev_free(p->ws_items);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(p->h_uvw[b]);
-        cudaFree(p->h_vis[b]);
-        cudaFree(p->h_wt[b]);
+        dev_free(p->h_uvw[b]);
+        dev_free(p->h_vis[b]);
+        dev_free(p->h_wt[b]);
         if (p->h_ready[b]) cudaEventDestroy(p->h_ready[b]);
         if (p->h_free[b]) cudaEventDestroy(p->h_free[b]);
     }
-    cudaFree(p->h_freq);
+    dev_free(p->h_freq);
     if (p->h_copy) cudaStreamDestroy(p->h_copy);
-    cudaFree(p->d_c1);
-    cudaFree(p->d_z);
-    cudaFree(p->d_hpr);
-    cudaFree(p->d_hprf);
+    dev_free(p->d_c1);
+    dev_free(p->d_z);
+    dev_free(p->d_hpr);
+    dev_free(p->d_hprf);
     if (p->tabs) {
         TableSet* t = p->tabs;
         if (t->refs.fetch_sub(1) == 1) {
@@ -168,15 +223,15 @@ void plan_free(gw_plan p) {
         free_tables(p->table, p->table16, p->ptable, p->d_pplane_off, p->d_plane_off,
                     p->d_support, p->d_h, p->d_hf);
     }
-    cudaFree(p->sc.rec);
-    cudaFree(p->sc.count);
-    cudaFree(p->sc.offsets);
-    cudaFree(p->sc.cursor);
-    cudaFree(p->sc.item_off);
-    cudaFree(p->sc.entries);
-    cudaFree(p->sc.items);
-    cudaFree(p->sc.counters);
-    cudaFree(p->sc.dropped);
+    dev_free(p->sc.rec);
+    dev_free(p->sc.count);
+    dev_free(p->sc.offsets);
+    dev_free(p->sc.cursor);
+    dev_free(p->sc.item_off);
+    dev_free(p->sc.entries);
+    dev_free(p->sc.items);
+    dev_free(p->sc.counters);
+    dev_free(p->sc.dropped);
     delete p;
 }
 
@@ -218,7 +273,7 @@ gw_status check_device(gw_plan p) {
 
 template <class T>
 cudaError_t dmalloc(T** ptr, size_t n) {
-    return cudaMalloc((void**)ptr, sizeof(T) * (n ? n : 1));
+    return dev_alloc((void**)ptr, sizeof(T) * (n ? n : 1));
 }
 
 // Per-plan scratch sized by the plan's chunk (gw_plan_clone gives each clone its own).
@@ -243,6 +298,9 @@ gw_status alloc_scratch(gw_plan p) {
     GW_ALLOC(sc.work, 2);
 #undef GW_ALLOC
     p->scratch_bytes = bytes;
+    // counters[1] is the device status word (a bounded device wait gave up)
+    e = cudaMemset(sc.counters, 0, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");
     return GW_OK;
 }
 
@@ -307,6 +365,19 @@ int64_t rows_per_chunk(gw_plan p, int nchan) {
     return r < 1 ? 1 : r;
 }
 
+// Reads (and clears) the plan's device status word; the stream must have
+// been synchronised.  GW_ETIMEDOUT when a bounded device wait gave up.
+gw_status read_device_status(gw_plan p) {
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpy(&st, p->sc.counters + 1, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+    if (st == 0) return GW_OK;
+    e = cudaMemset(p->sc.counters + 1, 0, sizeof st);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");
+    return fail(GW_ETIMEDOUT, "a bounded device wait gave up (status 0x%x); the results of the "
+                "calls since the last check are incomplete", st);
+}
+
 gw_status finish_dropped(gw_plan p, int64_t* n_dropped, cudaStream_t s) {
     if (!n_dropped) return GW_OK;
     unsigned long long h = 0;
@@ -314,7 +385,7 @@ gw_status finish_dropped(gw_plan p, int64_t* n_dropped, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "reading the drop count");
     *n_dropped = (int64_t)h;
-    return GW_OK;
+    return read_device_status(p);
 }
 
 gw_status common_checks(gw_plan p, const double* uvw, const double* freq, int64_t nrow, int nchan) {
@@ -357,7 +428,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     gw_status st = check_desc(desc);
     if (st != GW_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    gw_plan p = new (std::nothrow) gw_plan_s;
+    gw_plan p = host_new<gw_plan_s>();
     if (!p) return fail(GW_ENOMEM, "host allocation failed");
     p->desc = *desc;
     cudaError_t e = cudaGetDevice(&p->device);
@@ -490,7 +561,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "padding kernel tables"); }
-    TableSet* t = new (std::nothrow) TableSet;
+    TableSet* t = host_new<TableSet>();
     if (!t) { plan_free(p); return fail(GW_ENOMEM, "host allocation failed"); }
     t->table = p->table;
     t->table16 = p->table16;
@@ -506,7 +577,13 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
                (int64_t)(2 * sizeof(int64_t) + sizeof(int)) * (P + 1) +
                (int64_t)(sizeof(double) + sizeof(float)) * N;
     p->tabs = t;
+    // the allocation-free degridding path allocates nothing when called: its
+    // module (static scratch) and kernels are loaded now, while allocating is
+    // still allowed
+    e = static_path_prepare(desc->npol, desc->table_dtype);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "loading the allocation-free path"); }
     apply_tuning(p);
+    g_live_plans.fetch_add(1);
     *out = p;
     return GW_OK;
 }
@@ -518,7 +595,7 @@ gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream
     gw_status st = check_device(src);
     if (st != GW_OK) return st;
     if (max_vis_per_call < 0) return fail(GW_EINVAL, "max_vis_per_call must be >= 0");
-    gw_plan p = new (std::nothrow) gw_plan_s;
+    gw_plan p = host_new<gw_plan_s>();
     if (!p) return fail(GW_ENOMEM, "host allocation failed");
     p->desc = src->desc;
     p->desc.max_vis_per_call = max_vis_per_call;
@@ -571,6 +648,7 @@ gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream
                         (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaMemsetAsync"); }
     apply_tuning(p);
+    g_live_plans.fetch_add(1);
     *out = p;
     return GW_OK;
 }
@@ -592,9 +670,32 @@ gw_status gw_plan_get_tuning(gw_plan p, gw_tuning* out) {
     return GW_OK;
 }
 
+gw_status gw_plan_device_status(gw_plan p, void* cuda_stream) {
+    if (!p) return fail(GW_EINVAL, "null plan");
+    gw_status st = check_device(p);
+    if (st != GW_OK) return st;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return read_device_status(p);
+}
+
 gw_status gw_plan_destroy(gw_plan plan) {
+    if (plan) g_live_plans.fetch_sub(1);
     plan_free(plan);
     return GW_OK;
+}
+
+gw_status gw_debug_fail_alloc(int64_t n) {
+    if (n < 0) return fail(GW_EINVAL, "n must be >= 0");
+    g_fail_countdown.store(n);
+    return GW_OK;
+}
+
+int64_t gw_debug_live_plans(void) { return g_live_plans.load(); }
+
+int64_t gw_debug_live_bytes(void) {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    return g_live_bytes;
 }
 
 gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
@@ -657,7 +758,7 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
         a.weight = nullptr;
         if (weight) {
             if (!p->sc.wvis) {
-                e = cudaMalloc(&p->sc.wvis, sizeof(float2) * (size_t)p->chunk * npol);
+                e = dev_alloc((void**)&p->sc.wvis, sizeof(float2) * (size_t)p->chunk * npol);
                 if (e != cudaSuccess) {
                     p->sc.wvis = nullptr;
                     return fail(GW_ENOMEM, "allocating weighted-visibility scratch");
@@ -715,24 +816,37 @@ static gw_status ensure_host_pipe(gw_plan p, int64_t rows, int nchan) {
     }
     if (p->h_rows < rows || p->h_freq_n < nchan) {
         for (int b = 0; b < 2; ++b) {
-            cudaFree(p->h_uvw[b]);
-            cudaFree(p->h_vis[b]);
-            cudaFree(p->h_wt[b]);
+            dev_free(p->h_uvw[b]);
+            dev_free(p->h_vis[b]);
+            dev_free(p->h_wt[b]);
             p->h_uvw[b] = nullptr;
             p->h_vis[b] = nullptr;
             p->h_wt[b] = nullptr;
         }
-        cudaFree(p->h_freq);
+        dev_free(p->h_freq);
         p->h_freq = nullptr;
         p->h_rows = 0;
         const int64_t r = std::max(rows, p->h_rows), c = std::max<int64_t>(nchan, p->h_freq_n);
         for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-            e = cudaMalloc(&p->h_uvw[b], sizeof(double) * 3 * r);
-            if (e == cudaSuccess) e = cudaMalloc(&p->h_vis[b], vb * r * c * npol);
-            if (e == cudaSuccess) e = cudaMalloc(&p->h_wt[b], sizeof(float) * r * c * npol);
+            e = dev_alloc((void**)&p->h_uvw[b], sizeof(double) * 3 * r);
+            if (e == cudaSuccess) e = dev_alloc(&p->h_vis[b], vb * r * c * npol);
+            if (e == cudaSuccess) e = dev_alloc((void**)&p->h_wt[b], sizeof(float) * r * c * npol);
         }
-        if (e == cudaSuccess) e = cudaMalloc(&p->h_freq, sizeof(double) * c);
-        if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating host-pipeline staging");
+        if (e == cudaSuccess) e = dev_alloc((void**)&p->h_freq, sizeof(double) * c);
+        if (e != cudaSuccess) {
+            // leave no partial staging behind: the next call starts afresh
+            for (int b = 0; b < 2; ++b) {
+                dev_free(p->h_uvw[b]);
+                dev_free(p->h_vis[b]);
+                dev_free(p->h_wt[b]);
+                p->h_uvw[b] = nullptr;
+                p->h_vis[b] = nullptr;
+                p->h_wt[b] = nullptr;
+            }
+            dev_free(p->h_freq);
+            p->h_freq = nullptr;
+            return fail(GW_ENOMEM, "allocating host-pipeline staging");
+        }
         p->h_rows = r;
         p->h_freq_n = c;
     }
@@ -814,8 +928,8 @@ static gw_status ensure_compress(gw_plan p, cudaStream_t s) {
     const int npol = p->desc.npol;
     cudaError_t e = cudaSuccess;
 #define GW_CALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { \
-        cudaFree(cs.keys); cudaFree(cs.acc); cudaFree(cs.rec); cudaFree(cs.vis); \
-        cudaFree(cs.count); cs = CompressScratch{}; \
+        dev_free(cs.keys); dev_free(cs.acc); dev_free(cs.rec); dev_free(cs.vis); \
+        dev_free(cs.count); cs = CompressScratch{}; \
         return fail(GW_ENOMEM, "allocating compression scratch (%s)", #x); } } while (0)
     GW_CALLOC(cs.keys, (size_t)cap);
     GW_CALLOC(cs.acc, (size_t)cap * npol);
@@ -907,11 +1021,11 @@ gw_status gw_grid_vis_compressed(gw_plan p, const double* uvw_m, const double* f
 
 static gw_status ensure_wstack(gw_plan p, int nlayers) {
     if (p->ws_layers >= nlayers) return GW_OK;
-    cudaFree(p->ws_count);
-    cudaFree(p->ws_offsets);
-    cudaFree(p->ws_cursor);
-    cudaFree(p->ws_item_off);
-    cudaFree(p->ws_items);
+    dev_free(p->ws_count);
+    dev_free(p->ws_offsets);
+    dev_free(p->ws_cursor);
+    dev_free(p->ws_item_off);
+    dev_free(p->ws_items);
     p->ws_count = p->ws_offsets = p->ws_cursor = p->ws_item_off = nullptr;
     p->ws_items = nullptr;
     p->ws_layers = 0;
@@ -923,7 +1037,16 @@ static gw_status ensure_wstack(gw_plan p, int nlayers) {
     if (e == cudaSuccess) e = dmalloc(&p->ws_cursor, (size_t)nt);
     if (e == cudaSuccess) e = dmalloc(&p->ws_item_off, (size_t)nt + 1);
     if (e == cudaSuccess) e = dmalloc(&p->ws_items, (size_t)icap);
-    if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating w-stacking bins");
+    if (e != cudaSuccess) {
+        dev_free(p->ws_count);
+        dev_free(p->ws_offsets);
+        dev_free(p->ws_cursor);
+        dev_free(p->ws_item_off);
+        dev_free(p->ws_items);
+        p->ws_count = p->ws_offsets = p->ws_cursor = p->ws_item_off = nullptr;
+        p->ws_items = nullptr;
+        return fail(GW_ENOMEM, "allocating w-stacking bins");
+    }
     p->ws_layers = nlayers;
     p->ws_items_cap = icap;
     return GW_OK;
@@ -1044,9 +1167,9 @@ static gw_status hybrid_checks(gw_plan p, int32_t sz) {
 
 static gw_status ensure_prune(gw_plan p, int32_t sz, cudaStream_t s) {
     if (p->hy_sz == sz) return GW_OK;
-    cudaFree(p->d_z);
-    cudaFree(p->d_hpr);
-    cudaFree(p->d_hprf);
+    dev_free(p->d_z);
+    dev_free(p->d_hpr);
+    dev_free(p->d_hprf);
     p->d_z = nullptr;
     p->d_hpr = nullptr;
     p->d_hprf = nullptr;
@@ -1055,7 +1178,15 @@ static gw_status ensure_prune(gw_plan p, int32_t sz, cudaStream_t s) {
     cudaError_t e = dmalloc(&p->d_z, (size_t)(beta / 2) * sz);
     if (e == cudaSuccess) e = dmalloc(&p->d_hpr, (size_t)N);
     if (e == cudaSuccess) e = dmalloc(&p->d_hprf, (size_t)N);
-    if (e != cudaSuccess) return fail(GW_ENOMEM, "allocating the pruner");
+    if (e != cudaSuccess) {
+        dev_free(p->d_z);
+        dev_free(p->d_hpr);
+        dev_free(p->d_hprf);
+        p->d_z = nullptr;
+        p->d_hpr = nullptr;
+        p->d_hprf = nullptr;
+        return fail(GW_ENOMEM, "allocating the pruner");
+    }
     e = build_prune(sz, beta, N, p->d_z, p->d_hpr, p->d_hprf, s);
     if (e != cudaSuccess) return cuda_fail(e, "building the pruner");
     p->h_z.assign((size_t)(beta / 2) * sz, 0.f);
@@ -1342,7 +1473,7 @@ gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* fre
                     "holds %d (grid_n <= 8192)", p->desc.grid_n, g.ntu * g.ntv,
                     static_scratch_max_tiles());
     Scratch sc;
-    cudaError_t e = static_scratch_view(p->device, &sc);
+    cudaError_t e = static_scratch_view(&sc);
     if (e != cudaSuccess) return cuda_fail(e, "locating the static scratch (cudaGetSymbolAddress)");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // the array keeps the previous call's contents: reset what must start at zero

@@ -290,4 +290,15 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
     }
 }
 
+cudaError_t preload_bin_kernels() {
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, k_count);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_count_sm);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scan);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scatter);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scatter_sm);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_items);
+    return e;
+}
+
 }  // namespace gw

@@ -257,6 +257,26 @@ void launch_k(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
 
 int degrid_staged_tile() { return kStagedTile; }
 
+cudaError_t preload_degrid_kernel(int npol, int table_kind) {
+    cudaFuncAttributes attr;
+    auto get = [&](auto f) { return cudaFuncGetAttributes(&attr, f); };
+    const int tk = table_kind == GW_BF16X2 ? 1 : (table_kind == GW_F16X2 ? 2 : 0);
+    switch (npol * 3 + tk) {
+        case 3: return get(k_degrid<1, GW_C64>);
+        case 4: return get(k_degrid<1, GW_BF16X2>);
+        case 5: return get(k_degrid<1, GW_F16X2>);
+        case 6: return get(k_degrid<2, GW_C64>);
+        case 7: return get(k_degrid<2, GW_BF16X2>);
+        case 8: return get(k_degrid<2, GW_F16X2>);
+        case 9: return get(k_degrid<3, GW_C64>);
+        case 10: return get(k_degrid<3, GW_BF16X2>);
+        case 11: return get(k_degrid<3, GW_F16X2>);
+        case 13: return get(k_degrid<4, GW_BF16X2>);
+        case 14: return get(k_degrid<4, GW_F16X2>);
+        default: return get(k_degrid<4, GW_C64>);
+    }
+}
+
 bool degrid_staged_fits(int hmax, int npol) {
     const int RS = kStagedTile + 2 * hmax;
     return (size_t)RS * RS * npol * sizeof(float2) <= kStagedSmemMax;

@@ -16,16 +16,28 @@
 //   polarisation.  Four slots per warp amortise each record's staged
 //   visibility over up to 4 x 32 points.
 // * A ninth, producer warp stages batches of records into shared memory
-//   (three buffers, handed over with named barriers) and, for every record,
-//   appends it to the list of each compute warp whose block its footprint
-//   meets, together with the record's table offset for the tile and the
-//   range of slots its rows meet (one 64-bit entry).  Compute warps
-//   therefore only see records that touch them.
+//   (three buffers) and, for every record, appends it to the list of each
+//   compute warp whose block its footprint meets, together with the record's
+//   table offset for the tile and the slots its rows meet (one 64-bit entry):
+//   entries meeting all four slots in one list, the others in a second.
+//   Compute warps therefore only see records that touch them.
+// * Hand-over through mbarriers: a compute warp waits only for the batch it
+//   needs and releases it when done, so the eight compute warps run
+//   independently (a warp with a short list goes on to the next batch
+//   instead of waiting for the others); the producer waits until all eight
+//   have released a buffer before refilling it.  Every wait is bounded: a
+//   wait that gives up sets the plan's device status word and the kernel
+//   returns.
+// * The producer pads both lists of every warp to a multiple of the load
+//   ring depth R and appends R more null entries (a valid table address, the
+//   all-zero visibility row), so the compute loops have no tail tests and
+//   always load R entries ahead: the kernel values of entry i + R are loaded
+//   into the registers entry i has just used (a ring of R register sets, no
+//   copies).
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
 //   rows around each S x S slice, one compile-time row stride per plan), so
 //   lanes outside the footprint read zeros and slot addresses are immediate
-//   offsets; loads for the next record are issued before the multiply-adds
-//   of the current one.
+//   offsets.
 // * Per tap and polarisation the update is two packed FP32x2 FMAs (Blackwell
 //   FFMA2) on the (re, im) accumulator pair:
 //     acc += (K.re, K.re) (.) A + (K.im, K.im) (.) B
@@ -47,17 +59,58 @@ namespace {
 constexpr int kComputeWarps = 8;
 constexpr int kThreads = (kComputeWarps + 1) * 32;
 constexpr int kBatch = 256;
+constexpr int kPerLane = kBatch / 32;   // records staged by each producer lane per batch
+
+// entry.y: record row in the batch (bits 0-8), slot case (bits 16-19), mask
+// of the slots to load (bits 20-23)
+constexpr uint32_t kZeroRow = kBatch;   // staged visibility row that is always zero
+__host__ __device__ constexpr int slot_case(int j0, int j1) {
+    // (0,0)=0 (0,1)=1 (0,2)=2 (1,1)=3 (1,2)=4 (1,3)=5 (2,2)=6 (2,3)=7 (3,3)=8
+    return j0 == 0 ? j1 : (j0 == 1 ? 2 + j1 : (j0 == 2 ? 4 + j1 : 8));
+}
 
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
     int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
     return *reinterpret_cast<gw_index_rec*>(&v);
 }
 
-__device__ __forceinline__ void bar_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+// ---- mbarriers (shared memory, CTA scope) ----------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void bar_arrive(int id, int n) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the completion of the barrier phase of the given parity; gives
+// up after about two seconds (a batch hand-over takes microseconds).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
 }
 
 // Commit with the rounding error kept: the vector atomic returns the value
@@ -82,17 +135,20 @@ __device__ __forceinline__ void commit_compensated(float2* g, float2* err, float
     if (e.x != 0.f || e.y != 0.f) atomicAdd(err, e);
 }
 
-template <int NPOL, int B>
+template <int R>
+constexpr int list_cap() { return kBatch + 4 * R; }
+
+template <int NPOL, int B, int R>
 struct Smem {
-    float4 v[B][kBatch][NPOL];             // (A.re, A.im, B.re, B.im) per polarisation
-    // per warp: entries (x: padded-table index of the tile origin relative to
-    // the record, y: r | j0 << 16 | j1 << 20), those meeting all four slots
-    // from the front, the others from the back
-    uint2 list[B][kComputeWarps][kBatch];
-    int cnt[B][kComputeWarps];             // entries meeting all four slots
-    int cntp[B][kComputeWarps];            // entries meeting some slots
+    float4 v[B][kBatch + 1][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation; row kBatch = 0
+    // per warp: full entries from the front, partial entries below the top
+    // R null entries (see the producer)
+    uint2 list[B][kComputeWarps][list_cap<R>()];
+    int cnt[B][kComputeWarps];             // full entries, padded to a multiple of R
+    int cntp[B][kComputeWarps];            // partial entries, padded to a multiple of R
     int tile[B];                           // tile of the batch; -1 = end of work
     int last[B];                           // batch ends its work item
+    unsigned long long full[B], empty[B];  // mbarriers
 };
 
 // Packed FMAs of one entry into slots J0..J1 (compile-time range).
@@ -104,106 +160,127 @@ __device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const float2 (&
         const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
         const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
 #pragma unroll
-        for (int p = 0; p < NPOL; ++p) {
+        for (int p = 0; p < NPOL; ++p)
             acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
+#pragma unroll
+        for (int p = 0; p < NPOL; ++p)
             acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+    }
+}
+
+template <int NPOL>
+__device__ __forceinline__ void load_v(float4 (&V)[NPOL], const float4 (*vs)[NPOL], uint32_t ey) {
+#pragma unroll
+    for (int p = 0; p < NPOL; ++p) V[p] = vs[ey & 0x1ff][p];
+}
+
+// Entries meeting all four slots of the warp's block.  n is a multiple of
+// R and R null entries follow the last one.
+template <int NPOL, int SP, int R, class TE>
+__device__ __forceinline__ void run_full(const uint2* lst, int n, const float4 (*vs)[NPOL],
+                                         const typename TE::T* __restrict__ tab,
+                                         float2 (&K)[R][4], float2 (&acc)[4][NPOL]) {
+    if (n == 0) return;
+    uint32_t ey[R];
+#pragma unroll
+    for (int d = 0; d < R; ++d) {
+        const uint2 en = lst[d];
+        ey[d] = en.y;
+        const typename TE::T* p_ = tab + (int)en.x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) K[d][j] = TE::load(p_ + 4 * j * SP);
+    }
+    for (int i = 0; i < n; i += R) {
+#pragma unroll
+        for (int d = 0; d < R; ++d) {
+            float4 V[NPOL];
+            load_v<NPOL>(V, vs, ey[d]);
+            slot_fma<NPOL, 0, 3>(acc, K[d], V);
+            const uint2 en = lst[i + R + d];
+            ey[d] = en.y;
+            const typename TE::T* p_ = tab + (int)en.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) K[d][j] = TE::load(p_ + 4 * j * SP);
         }
     }
 }
 
-// One warp's pass over n list entries of a batch.  Software pipeline: the
-// kernel values of entry i + 1 load while entry i's FMAs run (a ring of D
-// register sets, unrolled so no register copies are needed).  FULL: every
-// entry meets all four slots of the warp's block (no per-slot tests);
-// otherwise one warp-uniform jump on the entry's slot range selects code
-// for exactly the slots it meets.
-template <int NPOL, int SP, int D, bool FULL, class TE>
-__device__ __forceinline__ void run_entries(const uint2* lst, int n,
-                                            const float4 (*vs)[NPOL],
-                                            const typename TE::T* __restrict__ tab,
-                                            float2 (&acc)[4][NPOL]) {
-    float2 Kr[D][4];
-    uint32_t er[D];
-    auto load_k = [&](uint2 en, float2 (&K)[4]) {
-        const uint32_t e = en.y;
+// Entries meeting some of the slots: loads only of the slots in the entry's
+// mask, one warp-uniform jump to the code for its slot range.
+template <int NPOL, int SP, int R, class TE>
+__device__ __forceinline__ void run_part(const uint2* lst, int n, const float4 (*vs)[NPOL],
+                                         const typename TE::T* __restrict__ tab,
+                                         float2 (&K)[R][4], float2 (&acc)[4][NPOL]) {
+    if (n == 0) return;
+    uint32_t ey[R];
+    auto load_masked = [&](const uint2 en, float2 (&Kd)[4]) {
+        const uint32_t m = en.y >> 20;
         const typename TE::T* p_ = tab + (int)en.x;
-        if (FULL) {
-            K[0] = TE::load(p_);
-            K[1] = TE::load(p_ + 4 * SP);
-            K[2] = TE::load(p_ + 8 * SP);
-            K[3] = TE::load(p_ + 12 * SP);
-        } else {
-            const int j0_ = (e >> 16) & 15, j1_ = (e >> 20) & 15;
-            K[0] = K[1] = K[2] = K[3] = make_float2(0.f, 0.f);
-            if (0 >= j0_ && 0 <= j1_) K[0] = TE::load(p_);
-            if (1 >= j0_ && 1 <= j1_) K[1] = TE::load(p_ + 4 * SP);
-            if (2 >= j0_ && 2 <= j1_) K[2] = TE::load(p_ + 8 * SP);
-            if (3 >= j0_ && 3 <= j1_) K[3] = TE::load(p_ + 12 * SP);
-        }
+        if (m & 1u) Kd[0] = TE::load(p_);
+        if (m & 2u) Kd[1] = TE::load(p_ + 4 * SP);
+        if (m & 4u) Kd[2] = TE::load(p_ + 8 * SP);
+        if (m & 8u) Kd[3] = TE::load(p_ + 12 * SP);
     };
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-        er[d] = 0;
-        Kr[d][0] = Kr[d][1] = Kr[d][2] = Kr[d][3] = make_float2(0.f, 0.f);
-        if (d < n) {
-            const uint2 en = lst[d];
-            er[d] = en.y;
-            load_k(en, Kr[d]);
-        }
+    for (int d = 0; d < R; ++d) {
+        const uint2 en = lst[d];
+        ey[d] = en.y;
+        load_masked(en, K[d]);
     }
-    for (int i = 0; i < n; i += D) {
+    for (int i = 0; i < n; i += R) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            if (i + d < n) {
-                const uint32_t ec = er[d];
-                const float2 Kc[4] = {Kr[d][0], Kr[d][1], Kr[d][2], Kr[d][3]};
-                if (i + d + D < n) {
-                    const uint2 en = lst[i + d + D];
-                    er[d] = en.y;
-                    load_k(en, Kr[d]);
-                }
-                const int r = ec & 0xffff, j0 = (ec >> 16) & 15, j1 = (ec >> 20) & 15;
-                float4 V[NPOL];
-#pragma unroll
-                for (int p = 0; p < NPOL; ++p) V[p] = vs[r][p];
-                // packed FP32x2: acc += (K.x, K.x) (.) A + (K.y, K.y) (.) B, only
-                // on the slots the entry meets (one warp-uniform jump)
-                if (FULL) {
-                    slot_fma<NPOL, 0, 3>(acc, Kc, V);
-                } else {
-                    switch ((j0 << 2) | j1) {
-                        case 0: slot_fma<NPOL, 0, 0>(acc, Kc, V); break;
-                        case 1: slot_fma<NPOL, 0, 1>(acc, Kc, V); break;
-                        case 2: slot_fma<NPOL, 0, 2>(acc, Kc, V); break;
-                        case 3: slot_fma<NPOL, 0, 3>(acc, Kc, V); break;
-                        case 5: slot_fma<NPOL, 1, 1>(acc, Kc, V); break;
-                        case 6: slot_fma<NPOL, 1, 2>(acc, Kc, V); break;
-                        case 7: slot_fma<NPOL, 1, 3>(acc, Kc, V); break;
-                        case 10: slot_fma<NPOL, 2, 2>(acc, Kc, V); break;
-                        case 11: slot_fma<NPOL, 2, 3>(acc, Kc, V); break;
-                        default: slot_fma<NPOL, 3, 3>(acc, Kc, V); break;
-                    }
-                }
+        for (int d = 0; d < R; ++d) {
+            float4 V[NPOL];
+            load_v<NPOL>(V, vs, ey[d]);
+            switch ((ey[d] >> 16) & 15u) {
+                case 0: slot_fma<NPOL, 0, 0>(acc, K[d], V); break;
+                case 1: slot_fma<NPOL, 0, 1>(acc, K[d], V); break;
+                case 2: slot_fma<NPOL, 0, 2>(acc, K[d], V); break;
+                case 3: slot_fma<NPOL, 1, 1>(acc, K[d], V); break;
+                case 4: slot_fma<NPOL, 1, 2>(acc, K[d], V); break;
+                case 5: slot_fma<NPOL, 1, 3>(acc, K[d], V); break;
+                case 6: slot_fma<NPOL, 2, 2>(acc, K[d], V); break;
+                case 7: slot_fma<NPOL, 2, 3>(acc, K[d], V); break;
+                default: slot_fma<NPOL, 3, 3>(acc, K[d], V); break;
             }
+            const uint2 en = lst[i + R + d];
+            ey[d] = en.y;
+            load_masked(en, K[d]);
         }
     }
 }
 
-// Named barriers: FULL(b) = 1 + b (batch b staged), EMPTY(b) = 1 + B + b (consumed).
-template <int NPOL, int SP, int TK, int D, int B>
+template <int NPOL, int SP, int TK, int B, int R>
 __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
     using TE = TabElem<TK>;
-    constexpr int kBufs = B;
+    constexpr int kCap = list_cap<R>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<NPOL, B>& sm = *reinterpret_cast<Smem<NPOL, B>*>(smem_raw);
+    Smem<NPOL, B, R>& sm = *reinterpret_cast<Smem<NPOL, B, R>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int side = a.ntiles_u;
     const int hb = a.beta / 2;
 
+    // one-time set-up: barriers, the zero visibility row, the top R null
+    // entries of every partial list
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < B; ++b) {
+            mbar_init(&sm.full[b], 32);
+            mbar_init(&sm.empty[b], kComputeWarps * 32);
+        }
+    }
+    for (int t = threadIdx.x; t < B * NPOL; t += kThreads)
+        sm.v[t / NPOL][kZeroRow][t % NPOL] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = threadIdx.x; t < B * kComputeWarps * R; t += kThreads) {
+        const int b = t / (kComputeWarps * R), w = (t / R) % kComputeWarps, k = t % R;
+        const int xnull = -(((w >> 2) * 16) * SP + (w & 3) * 8);
+        sm.list[b][w][kCap - R + k] = make_uint2((uint32_t)xnull, kZeroRow | (8u << 16));
+    }
+    __syncthreads();
+
     if (warp == kComputeWarps) {
         // ------------------------------------------------------------ producer
         const uint32_t nitems = *a.item_count;
-        int buf = 0, uses = 0;
+        uint32_t nbatch = 0;
         for (;;) {
             uint32_t it = 0;
             if (lane == 0) it = atomicAdd(a.queue, 1u);
@@ -213,7 +290,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
             if (!done) item = a.items[it];
             const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
             for (int b = 0; b < nb_total; ++b) {
-                if (uses >= kBufs) bar_sync(1 + kBufs + buf, kThreads);  // wait until consumed
+                const int buf = nbatch % B;
+                if (nbatch >= (uint32_t)B &&
+                    !mbar_wait(&sm.empty[buf], ((nbatch / B) - 1) & 1)) {
+                    if (lane == 0) atomicOr(a.queue + 1, 1u);
+                    return;
+                }
                 if (lane < kComputeWarps) {
                     sm.cnt[buf][lane] = 0;
                     sm.cntp[buf][lane] = 0;
@@ -231,9 +313,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                     const int tv0 = (ltile / side) * kTile;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
-                    for (int r = lane; r < nb; r += 32) {
-                        const uint32_t id = __ldg(a.entries + item.start + b0 + r);
-                        const gw_index_rec rc = load_rec(a.rec, id);
+                    // all ids, then all records of this lane's rows in flight at once
+                    uint32_t ids[kPerLane];
+                    gw_index_rec rcs[kPerLane];
+#pragma unroll
+                    for (int k = 0; k < kPerLane; ++k) {
+                        const int r = k * 32 + lane;
+                        ids[k] = r < nb ? __ldg(a.entries + item.start + b0 + r) : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kPerLane; ++k) {
+                        const int r = k * 32 + lane;
+                        if (r < nb) rcs[k] = load_rec(a.rec, ids[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < kPerLane; ++k) {
+                        const int r = k * 32 + lane;
+                        if (r >= nb) break;
+                        const uint32_t id = ids[k];
+                        const gw_index_rec rc = rcs[k];
                         // w-stacking records carry their layer in `plane`; the
                         // kernel is the plan's single (w = 0) plane
                         const int plane = a.layer_tiles ? 0 : rc.plane;
@@ -263,9 +361,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                         for (int cv = cv0; cv <= cv1; ++cv) {
                             const int j0 = max(0, vlo - 16 * cv) >> 2;
                             const int j1 = min(15, vhi - 16 * cv) >> 2;
-                            const uint2 e = make_uint2((uint32_t)base,
-                                                       (uint32_t)r | ((uint32_t)j0 << 16) | ((uint32_t)j1 << 20));
-                            const bool full = j0 == 0 && j1 == 3;
+                            const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
+                            const uint2 e = make_uint2(
+                                (uint32_t)base, (uint32_t)r | ((uint32_t)slot_case(j0, j1) << 16) |
+                                                    (mask << 20));
+                            const bool full = mask == 15u;
                             for (int cu = cu0; cu <= cu1; ++cu) {
                                 const int w = cv * 4 + cu;
                                 if (full) {
@@ -273,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                                     sm.list[buf][w][pos] = e;
                                 } else {
                                     const int pos = atomicAdd(&sm.cntp[buf][w], 1);
-                                    sm.list[buf][w][kBatch - 1 - pos] = e;
+                                    sm.list[buf][w][kCap - R - 1 - pos] = e;
                                 }
                             }
                         }
@@ -284,19 +384,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                     }
                 }
                 __syncwarp();
-                __threadfence_block();
-                bar_arrive(1 + buf, kThreads);  // batch ready
-                buf = (buf + 1 == kBufs) ? 0 : buf + 1;
-                ++uses;
+                // pad every warp's lists to a multiple of R and put R null
+                // entries after the full list (the partial list's are fixed)
+                if (lane < kComputeWarps) {
+                    const int w = lane;
+                    const uint32_t xnull = (uint32_t)(-(((w >> 2) * 16) * SP + (w & 3) * 8));
+                    const int nf = sm.cnt[buf][w], np = sm.cntp[buf][w];
+                    const int nfp = (nf + R - 1) / R * R, npp = (np + R - 1) / R * R;
+                    const uint2 zf = make_uint2(xnull, kZeroRow | (15u << 20) | (9u << 16));
+                    const uint2 zp = make_uint2(xnull, kZeroRow | (8u << 16));
+                    for (int k = nf; k < nfp + R; ++k) sm.list[buf][w][k] = zf;
+                    for (int k = np; k < npp; ++k) sm.list[buf][w][kCap - R - 1 - k] = zp;
+                    sm.cnt[buf][w] = nfp;
+                    sm.cntp[buf][w] = npp;
+                }
+                __syncwarp();
+                mbar_arrive(&sm.full[buf]);  // batch ready (every producer lane)
+                ++nbatch;
             }
-            if (done) {
-                // complete the consumers' releases of the batches whose
-                // buffers were not reused, so every barrier generation is
-                // balanced before exit (the end-of-work batch is not released)
-                for (int q = max(0, uses - kBufs); q <= uses - 2; ++q)
-                    bar_sync(1 + kBufs + q % kBufs, kThreads);
-                break;
-            }
+            if (done) break;
         }
         return;
     }
@@ -312,19 +418,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int p = 0; p < NPOL; ++p) acc[j][p] = make_float2(0.f, 0.f);
+    // kernel-value ring; finite values only (zero, then table values), so the
+    // null entries' zero visibility row contributes exact zeros
+    float2 K[R][4];
+#pragma unroll
+    for (int d = 0; d < R; ++d)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) K[d][j] = make_float2(0.f, 0.f);
 
-    int buf = 0;
+    uint32_t nbatch = 0;
     for (;;) {
-        bar_sync(1 + buf, kThreads);  // wait for the batch
+        const int buf = nbatch % B;
+        if (!mbar_wait(&sm.full[buf], (nbatch / B) & 1)) {
+            if (lane == 0) atomicOr(a.queue + 1, 1u);
+            return;
+        }
         const int tile = sm.tile[buf];
         if (tile < 0) break;
         const int last = sm.last[buf];
         const int nf = sm.cnt[buf][warp], np = sm.cntp[buf][warp];
         const uint2* lst = sm.list[buf][warp];
-        // entries meeting all four slots: no per-slot tests
-        run_entries<NPOL, SP, D, true, TE>(lst, nf, sm.v[buf], tab, acc);
-        // entries meeting a subset of the slots
-        run_entries<NPOL, SP, D, false, TE>(lst + kBatch - np, np, sm.v[buf], tab, acc);
+        run_full<NPOL, SP, R, TE>(lst, nf, sm.v[buf], tab, K, acc);
+        run_part<NPOL, SP, R, TE>(lst + kCap - R - np, np, sm.v[buf], tab, K, acc);
+        mbar_arrive(&sm.empty[buf]);  // buffer free (every lane, after its reads)
+        ++nbatch;
         if (last) {
             // commit the tile's accumulators of this work item
             const int ltile = a.layer_tiles ? tile % a.layer_tiles : tile;
@@ -351,32 +468,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                 }
             }
         }
-        bar_arrive(1 + kBufs + buf, kThreads);  // buffer free
-        buf = (buf + 1 == kBufs) ? 0 : buf + 1;
     }
 }
 
-template <int NPOL, int SP, int TK, int D, int B>
+template <int NPOL, int SP, int TK, int B, int R>
 void launch_v(const GridArgs& a, int num_sms, cudaStream_t s) {
-    const size_t smem = sizeof(Smem<NPOL, B>);
-    cudaFuncSetAttribute(k_grid<NPOL, SP, TK, D, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = sizeof(Smem<NPOL, B, R>);
+    cudaFuncSetAttribute(k_grid<NPOL, SP, TK, B, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP, TK, D, B>, kThreads,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid<NPOL, SP, TK, B, R>, kThreads,
                                                   smem);
     if (per_sm < 1) per_sm = 1;
-    k_grid<NPOL, SP, TK, D, B><<<num_sms * per_sm, kThreads, smem, s>>>(a);
+    k_grid<NPOL, SP, TK, B, R><<<num_sms * per_sm, kThreads, smem, s>>>(a);
     note_launch();
 }
 
-// Two register sets of kernel values in flight and three staging buffers of
-// 256 records: measured fastest on the 4-pol w-projection workload among
-// rings of 2-4 entries, 2-4 buffers and batches of 128-256 records (deeper
-// rings raise register pressure; a fourth buffer does not fit two CTAs per
-// SM with 64-bit list entries).
+// Three staging buffers of 256 records and a ring of GW_GRID_RING kernel-value
+// register sets per compute warp.
+#ifndef GW_GRID_RING
+#define GW_GRID_RING 2
+#endif
 template <int NPOL, int SP, int TK>
 void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
-    launch_v<NPOL, SP, TK, 2, 3>(a, num_sms, s);
+    launch_v<NPOL, SP, TK, 3, GW_GRID_RING>(a, num_sms, s);
 }
 
 template <int NPOL, int TK>

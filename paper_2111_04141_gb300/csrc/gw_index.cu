@@ -145,4 +145,9 @@ void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan
     note_launch();
 }
 
+cudaError_t preload_index_kernels() {
+    cudaFuncAttributes attr;
+    return cudaFuncGetAttributes(&attr, k_index);
+}
+
 }  // namespace gw

@@ -126,6 +126,15 @@ struct Scratch {
 // ---- launch counting -----------------------------------------------------
 void note_launch(int n = 1);
 
+// ---- allocations -----------------------------------------------------------
+// Every device allocation of the library goes through dev_alloc and every
+// host allocation of a plan object checks alloc_fault(), so a test can make
+// the n-th allocation from now fail on the host (gw_debug_fail_alloc)
+// without touching the GPU.
+bool alloc_fault();
+cudaError_t dev_alloc(void** ptr, size_t bytes);
+void dev_free(void* ptr);   // frees a dev_alloc allocation (null accepted)
+
 // Row count read on the device when kernels run (graph replays with any
 // count up to the captured maximum); nrow == null: the host count is used.
 struct DevCount {
@@ -198,7 +207,8 @@ struct GridArgs {
     const uint32_t* entries;
     const Item* items;
     const uint32_t* item_count;  // device scalar: item_off[ntiles]
-    uint32_t* queue;             // device scalar: work queue head (zeroed before launch)
+    uint32_t* queue;             // device words: [0] work queue head (zeroed before launch),
+                                 // [1] status (bit 0 set when a bounded device wait gave up)
     float2* grid;                // [npol][N][N]
     float2* grid_err;            // [npol][N][N] commit rounding errors, or null (plain commits)
     int N, npol, beta, ntiles_u;  // ntiles_u: gridder tiles along u
@@ -287,9 +297,19 @@ void launch_hybrid_image(const float2* raw, int npol, int N, const float* hco, c
 cudaError_t measure_ffma_peak(int num_sms, int iters, double* tflops, cudaStream_t s);
 
 // ---- allocation-free scratch (gw_noalloc.cu) ------------------------------
-// View of the file-scope static scratch on `device` (current); looks up the
-// symbol's device address on first use per device.
-cudaError_t static_scratch_view(int device, Scratch* sc);
+// View of the file-scope static scratch on the current device: the symbol's
+// device address is looked up on every call (no allocation once the module
+// is loaded).
+cudaError_t static_scratch_view(Scratch* sc);
+// Loads, on the current device, the module holding the static scratch (the
+// driver allocates the array then) and every kernel the allocation-free
+// degridding path launches for (npol, table_kind), so that its calls need
+// no allocation under lazy module loading.
+cudaError_t static_path_prepare(int npol, int table_kind);
+// Kernel preloading (cudaFuncGetAttributes) of the stages that path uses.
+cudaError_t preload_index_kernels();
+cudaError_t preload_bin_kernels();
+cudaError_t preload_degrid_kernel(int npol, int table_kind);
 int64_t static_scratch_max_vis();
 int static_scratch_max_tiles();
 

@@ -6,12 +6,14 @@
 // not take the driver's allocation lock between iterations.  For them this
 // entry point degrids with the same kernels as gw_degrid_vis but takes its
 // scratch (index records and centre-tile bins) from one file-scope device
-// array, sized once when the library is loaded, instead of from memory the
-// plan allocates per chunk.  The plan still supplies the kernel tables; the
-// caller still supplies inputs and outputs.
+// array of kStaticBytes (about 2.25 MiB) instead of from memory the plan
+// allocates per chunk.  The plan still supplies the kernel tables; the
+// caller still supplies inputs and outputs.  The driver allocates the array
+// when it loads this file's module; with lazy module loading (the CUDA
+// default) that would be the first allocation-free call itself, so plan
+// creation loads the module and every kernel the path launches
+// (static_path_prepare) while the caller can still allocate.
 #include "gw_internal.cuh"
-
-#include <mutex>
 
 namespace gw {
 
@@ -35,23 +37,16 @@ static_assert(kStaticBytes <= 4u * 1024u * 1024u, "static scratch stays modest (
 // The scratch itself: every GPU that loads the library holds it until exit.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-unsigned char* g_dev_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on `device` (which must be current).
-// Looked up once per device; in host code the symbol name is only a host-side
-// stand-in, so kernels must be given this address instead.
-cudaError_t static_scratch(int device, unsigned char** out) {
-    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_dev_addr[device]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_dev_addr[device] = static_cast<unsigned char*>(ptr);
-    }
-    *out = g_dev_addr[device];
+// Device address of g_static_scratch on the current device.  In host code
+// the symbol name is only a host-side stand-in, so kernels must be given this
+// address instead.  Looked up on every call: once the module is loaded the
+// lookup allocates nothing, and nothing cached can go stale when a context
+// is torn down and created again.
+cudaError_t static_scratch(unsigned char** out) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char*>(ptr);
     return cudaSuccess;
 }
 
@@ -60,9 +55,18 @@ cudaError_t static_scratch(int device, unsigned char** out) {
 int64_t static_scratch_max_vis() { return kStaticMaxVis; }
 int static_scratch_max_tiles() { return kStaticMaxTiles; }
 
-cudaError_t static_scratch_view(int device, Scratch* sc) {
+cudaError_t static_path_prepare(int npol, int table_kind) {
     unsigned char* base = nullptr;
-    cudaError_t e = static_scratch(device, &base);
+    cudaError_t e = static_scratch(&base);
+    if (e == cudaSuccess) e = preload_index_kernels();
+    if (e == cudaSuccess) e = preload_bin_kernels();
+    if (e == cudaSuccess) e = preload_degrid_kernel(npol, table_kind);
+    return e;
+}
+
+cudaError_t static_scratch_view(Scratch* sc) {
+    unsigned char* base = nullptr;
+    cudaError_t e = static_scratch(&base);
     if (e != cudaSuccess) return e;
     *sc = Scratch{};
     sc->rec = reinterpret_cast<gw_index_rec*>(base + kOffRec);

@@ -382,18 +382,18 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_tabl
     int exp2 = 0;   // storage exponent of the 16-bit table
     cudaError_t err = cudaSuccess;
 #define GW_TRY(x) do { err = (x); if (err != cudaSuccess) goto done; } while (0)
-    GW_TRY(cudaMalloc(&coef, sizeof(double) * K));
-    GW_TRY(cudaMalloc(&chi, sizeof(double)));
-    GW_TRY(cudaMalloc(&th, sizeof(double) * Qhmax));
-    GW_TRY(cudaMalloc(&wm, sizeof(double) * Qhmax));
-    GW_TRY(cudaMalloc(&tw, sizeof(double) * Qhmax));
-    GW_TRY(cudaMalloc(&Cm, sizeof(double) * (size_t)Fmax * Qhmax));
-    GW_TRY(cudaMalloc(&A, sizeof(double2) * (size_t)Qhmax * Qhmax));
-    GW_TRY(cudaMalloc(&Bt, sizeof(double2) * (size_t)Fmax * Qhmax));
-    GW_TRY(cudaMalloc(&Kf, sizeof(double2) * (size_t)Fmax * Fmax));
-    GW_TRY(cudaMalloc(&Kf0, sizeof(double2) * (size_t)(beta * tb.support[0]) * (beta * tb.support[0])));
-    GW_TRY(cudaMalloc(&scale, 2 * sizeof(double)));
-    GW_TRY(cudaMalloc(&C1, sizeof(double) * (size_t)beta * tb.support[0]));
+    GW_TRY(dev_alloc((void**)&coef, sizeof(double) * K));
+    GW_TRY(dev_alloc((void**)&chi, sizeof(double)));
+    GW_TRY(dev_alloc((void**)&th, sizeof(double) * Qhmax));
+    GW_TRY(dev_alloc((void**)&wm, sizeof(double) * Qhmax));
+    GW_TRY(dev_alloc((void**)&tw, sizeof(double) * Qhmax));
+    GW_TRY(dev_alloc((void**)&Cm, sizeof(double) * (size_t)Fmax * Qhmax));
+    GW_TRY(dev_alloc((void**)&A, sizeof(double2) * (size_t)Qhmax * Qhmax));
+    GW_TRY(dev_alloc((void**)&Bt, sizeof(double2) * (size_t)Fmax * Qhmax));
+    GW_TRY(dev_alloc((void**)&Kf, sizeof(double2) * (size_t)Fmax * Fmax));
+    GW_TRY(dev_alloc((void**)&Kf0, sizeof(double2) * (size_t)(beta * tb.support[0]) * (beta * tb.support[0])));
+    GW_TRY(dev_alloc((void**)&scale, 2 * sizeof(double)));
+    GW_TRY(dev_alloc((void**)&C1, sizeof(double) * (size_t)beta * tb.support[0]));
 
     k_pswf<<<1, 1, 0, s>>>(c, K, coef, chi);
     note_launch();
@@ -450,8 +450,8 @@ cudaError_t build_tables(const TableBuild& tb, float2* d_table, uint32_t* d_tabl
     *h_exp2 = exp2;
 done:
 #undef GW_TRY
-    cudaFree(coef); cudaFree(chi); cudaFree(th); cudaFree(wm); cudaFree(tw); cudaFree(Cm);
-    cudaFree(A); cudaFree(Bt); cudaFree(Kf); cudaFree(Kf0); cudaFree(scale); cudaFree(C1);
+    dev_free(coef); dev_free(chi); dev_free(th); dev_free(wm); dev_free(tw); dev_free(Cm);
+    dev_free(A); dev_free(Bt); dev_free(Kf); dev_free(Kf0); dev_free(scale); dev_free(C1);
     return err;
 }
 
@@ -511,11 +511,11 @@ cudaError_t build_prune(int sz, int beta, int N, float* d_z, double* d_hpr, floa
     double *coef = nullptr, *chi = nullptr, *x = nullptr, *ones = nullptr, *psi = nullptr;
     cudaError_t err = cudaSuccess;
 #define GW_TRY(x_) do { err = (x_); if (err != cudaSuccess) goto done; } while (0)
-    GW_TRY(cudaMalloc(&coef, sizeof(double) * K));
-    GW_TRY(cudaMalloc(&chi, sizeof(double)));
-    GW_TRY(cudaMalloc(&x, sizeof(double) * np));
-    GW_TRY(cudaMalloc(&ones, sizeof(double) * np));
-    GW_TRY(cudaMalloc(&psi, sizeof(double) * np));
+    GW_TRY(dev_alloc((void**)&coef, sizeof(double) * K));
+    GW_TRY(dev_alloc((void**)&chi, sizeof(double)));
+    GW_TRY(dev_alloc((void**)&x, sizeof(double) * np));
+    GW_TRY(dev_alloc((void**)&ones, sizeof(double) * np));
+    GW_TRY(dev_alloc((void**)&psi, sizeof(double) * np));
     {
         std::vector<double> h1(np, 1.0);
         GW_TRY(cudaMemcpyAsync(ones, h1.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
@@ -530,7 +530,7 @@ cudaError_t build_prune(int sz, int beta, int N, float* d_z, double* d_hpr, floa
     }
 done:
 #undef GW_TRY
-    cudaFree(coef); cudaFree(chi); cudaFree(x); cudaFree(ones); cudaFree(psi);
+    dev_free(coef); dev_free(chi); dev_free(x); dev_free(ones); dev_free(psi);
     return err;
 }
 

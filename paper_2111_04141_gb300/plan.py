@@ -484,6 +484,13 @@ class Plan:
                   "gw_plan_copy_corrector")
         return h
 
+    def device_status(self, stream=None):
+        """Synchronise the stream and raise GwError (GW_ETIMEDOUT) if a
+        bounded device-side wait gave up since the last check."""
+        with torch.cuda.device(self.device):
+            check(self._lib.gw_plan_device_status(self._h, _stream_ptr(stream, self.device)),
+                  "gw_plan_device_status")
+
     def timing(self, enable=None):
         """With ``enable`` set, switch stage timing on/off; otherwise return and
         reset the accumulated per-stage timings and work counters as a dict."""
@@ -525,3 +532,18 @@ def ffma_peak(iters: int = 4096, stream=None) -> float:
 
 def launch_count() -> int:
     return int(_lib.load().gw_launch_count())
+
+
+def debug_fail_alloc(n: int) -> None:
+    """Test hook: the n-th library allocation from now fails (0 = off)."""
+    check(_lib.load().gw_debug_fail_alloc(int(n)), "gw_debug_fail_alloc")
+
+
+def live_plans() -> int:
+    """Plans and clones created and not yet destroyed in this process."""
+    return int(_lib.load().gw_debug_live_plans())
+
+
+def live_bytes() -> int:
+    """Device bytes the library has allocated and not freed (all plans)."""
+    return int(_lib.load().gw_debug_live_bytes())

@@ -68,6 +68,8 @@ class Job:
     t_admit: float = math.nan
     t_done: float = math.nan
     slot: int = -1
+    cancelled: bool = False   # set before admission: the job is dropped, no GPU work
+    error: Optional[str] = None  # why a job finished without running (rejected or cancelled)
 
     @property
     def latency(self):
@@ -87,7 +89,11 @@ class Scheduler:
     state).  Slot state that is idle may be evicted, least recently used
     first, to make room; the head of the queue is never overtaken (no
     starvation), and a job that cannot fit even with every idle state
-    evicted waits for running jobs to finish.
+    evicted waits for running jobs to finish.  A job that could not fit even
+    with no slot state at all (``resident + cost > budget``) would wait
+    forever: it is rejected instead, as is a job whose ``cancelled`` flag is
+    set when it reaches the head; both leave the queue with ``error`` set and
+    no GPU work, and ``take_rejected`` hands them to the caller.
 
     With ``work_cap`` (grid-point updates of a job that fills the GPU), a
     job's load is min(1, work / work_cap) and the head is admitted only while
@@ -103,7 +109,9 @@ class Scheduler:
         self.budget = budget
         self.work_cap = work_cap
         self.work_slack = work_slack
-        self.used = resident               # bytes held outside slot state (tables, models)
+        self.resident = resident           # bytes held outside slot state (tables, models)
+        self.used = resident
+        self.rejected: List[Job] = []
         self.pending: collections.deque = collections.deque()
         self.busy: Dict[int, Job] = {}
         self.state: Dict[tuple, int] = {}  # (slot, setup) -> bytes held
@@ -111,6 +119,24 @@ class Scheduler:
 
     def arrive(self, job: Job):
         self.pending.append(job)
+
+    def cancel(self, job_id: int) -> bool:
+        """Cancel a job that has not been admitted yet; False if it is not
+        pending (already running, finished or unknown)."""
+        for j in self.pending:
+            if j.id == job_id:
+                j.cancelled = True
+                return True
+        return False
+
+    def take_rejected(self) -> List[Job]:
+        out, self.rejected = self.rejected, []
+        return out
+
+    def _reject(self, job: Job, why: str):
+        self.pending.popleft()
+        job.error = why
+        self.rejected.append(job)
 
     def free_slots(self) -> List[int]:
         return [s for s in range(self.n_slots) if s not in self.busy]
@@ -136,16 +162,24 @@ class Scheduler:
         (job, slot, evicted_keys, new_bytes) decisions."""
         out = []
         while self.pending:
+            job = self.pending[0]
+            if job.cancelled:
+                self._reject(job, "cancelled before admission")
+                continue
             free = self.free_slots()
             if not free:
                 break
-            job = self.pending[0]
             if self.work_cap is not None and self.busy:
                 inflight = sum(self.load(j) for j in self.busy.values())
                 if inflight + self.load(job) > 1.0 + self.work_slack:
                     break            # wait for running work to finish
             slot = self._pick_slot(job.setup, free)
             need = cost(slot, job.setup)
+            if self.resident + need > self.budget:
+                self._reject(job, f"needs {need} bytes of slot state but the budget leaves "
+                                  f"{self.budget - self.resident} beside the resident "
+                                  f"{self.resident}")
+                continue
             evicted = []
             if self.used + need > self.budget:
                 # evict idle state (LRU) until the job fits, if it can
@@ -216,7 +250,9 @@ class Server:
                 and memory only, which measured better on the mixed stream
                 (p99 26 ms vs 35 ms with a 2e10 cap)
     on_result   callback(job, host_tensor) called when a job's result is in
-                host memory (the tensor is a slot staging buffer: copy it to keep it)
+                host memory (the tensor is a slot staging buffer: copy it to keep it);
+                a job that was rejected or cancelled without running gets
+                host_tensor None and its reason in job.error
     """
 
     def __init__(self, setups: List[Setup], device, budget: int, n_slots: int = 4,
@@ -447,20 +483,35 @@ class Server:
         with admission and completion times filled in."""
         jobs = sorted(jobs, key=lambda j: j.arrival)
         for j in jobs:
-            j.work = self._job_work(j)
+            j.work = self._job_work(j) if j.setup in self.setups else 0.0
         t0 = clock()
         i = 0
         done = []
+
+        def finish_unrun(job):
+            job.t_admit = job.t_done = clock() - t0
+            done.append(job)
+            if self.on_result is not None:
+                self.on_result(job, None)
+
         while len(done) < len(jobs):
             now = clock() - t0
             while i < len(jobs) and jobs[i].arrival <= now:
-                self.sched.arrive(jobs[i])
+                j = jobs[i]
                 i += 1
+                why = self._check(j)
+                if why:
+                    j.error = why
+                    finish_unrun(j)
+                else:
+                    self.sched.arrive(j)
             for job, slot, evicted, _ in self.sched.admit(self._cost):
                 for key in evicted:
                     self._drop_state(key)
                 job.t_admit = clock() - t0
                 self._launch(job, slot)
+            for job in self.sched.take_rejected():
+                finish_unrun(job)
             progressed = False
             for slot in list(self.sched.busy):
                 if self.slots[slot]["event"].query():
@@ -471,6 +522,19 @@ class Server:
                 if wait > 2e-4 and not self.sched.busy:
                     time.sleep(wait - 1e-4)
         return done
+
+    def _check(self, job: Job) -> Optional[str]:
+        """Why a job cannot run on this server (checked on arrival, before
+        any GPU work), or None."""
+        s = self.setups.get(job.setup)
+        if s is None:
+            return f"unknown setup {job.setup!r}"
+        if job.kind not in ("grid", "degrid"):
+            return f"unknown job kind {job.kind!r}"
+        if job.nrow < 0 or job.nrow * s.nchan > self.max_vis:
+            return (f"{job.nrow} rows x {s.nchan} channels exceed the server's max_vis "
+                    f"({self.max_vis})")
+        return None
 
     def _job_work(self, job: Job) -> float:
         """Nominal grid-point pol-updates of a job: visibilities x npol x the

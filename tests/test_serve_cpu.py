@@ -47,12 +47,75 @@ def test_budget_blocks_until_memory_is_released():
 
 
 def test_head_of_line_is_not_overtaken():
-    s = Scheduler(n_slots=2, budget=50, resident=0)
-    s.arrive(job(0, "big"))
+    s = Scheduler(n_slots=3, budget=100, resident=0)
+    s.arrive(job(0, "a"))
+    cost = lambda slot, setup: 0 if (slot, setup) in s.state else {"a": 60, "big": 70,
+                                                                    "small": 1}[setup]
+    first = s.admit(cost)                               # a runs and holds 60
+    assert [j.id for j, *_ in first] == [0]
+    s.arrive(job(1, "big"))
+    s.arrive(job(2, "small"))
+    assert s.admit(cost) == []          # big fits only once a's state is idle; small waits too
+    assert [j.id for j in s.pending] == [1, 2]
+    s.complete(first[0][1])
+    got = s.admit(cost)
+    assert [j.id for j, *_ in got] == [1, 2]
+
+
+def test_job_that_can_never_fit_is_rejected_not_waited_for():
+    # resident 40 + a state of 70 > budget 100 even with no other state: the
+    # job would wait forever (and block the queue behind it), so it leaves
+    # the queue with an error and the next job runs
+    s = Scheduler(n_slots=2, budget=100, resident=40)
+    s.arrive(job(0, "huge"))
     s.arrive(job(1, "small"))
-    cost = lambda slot, setup: {"big": 60, "small": 1}[setup]
-    assert s.admit(cost) == []                          # big can never fit now; small waits too
-    assert [j.id for j in s.pending] == [0, 1]
+    cost = lambda slot, setup: {"huge": 70, "small": 10}[setup]
+    got = s.admit(cost)
+    assert [j.id for j, *_ in got] == [1]
+    rej = s.take_rejected()
+    assert [j.id for j in rej] == [0] and "budget" in rej[0].error
+    assert s.used == 50 and not s.pending
+    assert s.take_rejected() == []
+
+
+def test_cancelled_job_leaves_the_queue_without_running():
+    s = Scheduler(n_slots=1, budget=10**9)
+    for i in range(3):
+        s.arrive(job(i))
+    first = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in first] == [0]
+    assert s.cancel(1) is True
+    assert s.cancel(0) is False                         # running: cannot be cancelled
+    assert s.cancel(99) is False
+    assert s.admit(lambda slot, setup: 0) == []         # no free slot yet
+    s.complete(first[0][1])
+    got = s.admit(lambda slot, setup: 0)
+    assert [j.id for j, *_ in got] == [2]
+    rej = s.take_rejected()
+    assert [j.id for j in rej] == [1] and rej[0].error == "cancelled before admission"
+
+
+def test_server_rejects_invalid_jobs_before_any_gpu_work():
+    # a Server whose jobs are all invalid never touches the device: the
+    # checks run on arrival and the jobs finish with an error and no result
+    import torch
+    from paper_2111_04141_gb300.serve import Server, Setup
+    st = Setup("s", dict(grid_n=64, cell_rad=1e-3, support_min=7, support_max=7, oversample=8,
+                         n_wplanes=1, w_max_lambda=0.0, npol=1), np.array([1.4e8, 1.5e8]))
+    results = []
+    srv = Server([st], "cpu", budget=1 << 30, n_slots=2, max_vis=1000,
+                 on_result=lambda j, out: results.append((j.id, out)))
+    srv.sched = Scheduler(2, 1 << 30)
+    jobs = [Job(id=0, kind="grid", setup="s", nrow=501, arrival=0.0),      # 1002 > max_vis
+            Job(id=1, kind="grid", setup="nope", nrow=1, arrival=0.0),
+            Job(id=2, kind="transpose", setup="s", nrow=1, arrival=0.0)]
+    done = srv.run(jobs)
+    assert sorted(j.id for j in done) == [0, 1, 2]
+    assert all(j.error for j in done)
+    assert "max_vis" in jobs[0].error and "unknown setup" in jobs[1].error
+    assert "kind" in jobs[2].error
+    assert sorted(results) == [(0, None), (1, None), (2, None)]
+    assert not srv.sched.busy and not srv.sched.pending
 
 
 def test_slot_affinity_reuses_a_slot_holding_the_setup():
