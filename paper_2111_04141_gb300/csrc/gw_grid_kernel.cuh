@@ -7,42 +7,47 @@
 //     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
 //
 // Design (GB300):
-// * A CTA owns one 32 x 32 tile of the grid for a work item (a run of that
-//   tile's bin) and keeps the tile's accumulators in registers, so each grid
-//   point is committed once per work item (vector atomics, red.global).
-//   Two CTAs run per SM.
+// * A CTA (one per SM) owns one 32 x 32 tile of the grid for a work item (a
+//   run of that tile's bin) and keeps the tile's accumulators in registers,
+//   so each grid point is committed once per work item (vector atomics,
+//   red.global).
 // * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
 //   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
 //   polarisation.  Four slots per warp amortise each record's staged
 //   visibility over up to 4 x 32 points.
-// * A ninth, producer warp stages batches of records into shared memory
-//   (three buffers) and, for every record, appends it to the list of each
-//   compute warp whose block its footprint meets, together with the record's
-//   table offset for the tile and the slots its rows meet (one 64-bit entry):
-//   entries meeting all four slots in one list, the others in a second.
-//   Compute warps therefore only see records that touch them.
+// * The work is bound by the gathers of kernel values from L2 (each a
+//   4-row x 64-byte window of a table slice per slot), so the design keeps
+//   many of them in flight: one CTA of 12 warps per SM leaves 168 registers
+//   per thread, and each compute warp keeps the kernel values of the next R
+//   list entries in a ring of registers.
+// * Four producer warps (one warpgroup) stage batches of 256 records into
+//   shared memory: the record ids and index records are loaded for all rows
+//   at once, the visibilities are copied straight into shared memory with
+//   cp.async (or widened / weighted in registers for 16-bit or weighted
+//   input), and every record is appended to the list of each compute warp
+//   whose block its footprint meets, with the record's table offset for the
+//   tile and the slots its rows meet (one 64-bit entry).  Compute warps
+//   therefore only see records that touch them.
 // * Hand-over through mbarriers: a compute warp waits only for the batch it
 //   needs and releases it when done, so the eight compute warps run
-//   independently (a warp with a short list goes on to the next batch
-//   instead of waiting for the others); the producer waits until all eight
-//   have released a buffer before refilling it.  Every wait is bounded: a
-//   wait that gives up sets the plan's device status word and the kernel
-//   returns.
-// * The producer pads both lists of every warp to a multiple of the load
-//   ring depth R and appends R more null entries (a valid table address, the
-//   all-zero visibility row), so the compute loops have no tail tests and
-//   always load R entries ahead: the kernel values of entry i + R are loaded
-//   into the registers entry i has just used (a ring of R register sets, no
-//   copies).
+//   independently; the producers wait until all eight have released a
+//   buffer before refilling it.  Every wait is bounded: a wait that gives up
+//   sets the plan's device status word and the kernel returns.
+// * The producers pad every warp's list to a multiple of R and append R more
+//   null entries (no loads, the all-zero visibility row), so the compute loop
+//   has no tail tests: the kernel values of entry i + R are loaded into the
+//   registers entry i has just used.  An entry loads the slots its record
+//   meets and zeros for the others, and always updates all four slots (one
+//   loop body, no per-entry jump: the code stays small at ring depth R).
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
 //   rows around each S x S slice, one compile-time row stride per plan), so
 //   lanes outside the footprint read zeros and slot addresses are immediate
 //   offsets.
 // * Per tap and polarisation the update is two packed FP32x2 FMAs (Blackwell
 //   FFMA2) on the (re, im) accumulator pair:
-//     acc += (K.re, K.re) (.) A + (K.im, K.im) (.) B
-//   with A = V and B = (-V.im, V.re), or (V.im, -V.re) for the conjugate
-//   kernel (w < 0), precomputed per record.
+//     acc += (K.re, K.re) (.) (V.re, V.im) + (K.im, K.im) (.) s (-V.im, V.re)
+//   with s = -1 for the conjugate kernel (w < 0); the staged visibility is
+//   the plain (weighted) value, the second operand is formed in registers.
 // * Storage precision: the table element type is a template parameter
 //   (complex FP32, or bfloat16 / float16 pairs widened to FP32 on load);
 //   visibilities of any kind are widened to FP32 when staged; all
@@ -57,18 +62,17 @@ namespace gw {
 namespace {
 
 constexpr int kComputeWarps = 8;
-constexpr int kThreads = (kComputeWarps + 1) * 32;
+constexpr int kProducerWarps = 4;
+constexpr int kProducerThreads = kProducerWarps * 32;
+constexpr int kThreads = (kComputeWarps + kProducerWarps) * 32;
 constexpr int kBatch = 256;
-constexpr int kPerLane = kBatch / 32;   // records staged by each producer lane per batch
+constexpr int kPerLane = kBatch / kProducerThreads;   // rows staged by each producer thread
+constexpr int kProducerBar = 1;                        // named barrier of the producer warps
 
-// entry.y: record row in the batch (bits 0-8), slot case (bits 16-19), mask
-// of the slots to load (bits 20-23)
+// entry.y: record row in the batch (bits 0-8), conjugate kernel (bit 19),
+// mask of the slots the record's rows meet (bits 20-23)
 constexpr uint32_t kZeroRow = kBatch;   // staged visibility row that is always zero
-__host__ __device__ constexpr int slot_case(int j0, int j1) {
-    // (0,0)=0 (0,1)=1 (0,2)=2 (1,1)=3 (1,2)=4 (1,3)=5 (2,2)=6 (2,3)=7 (3,3)=8
-    return j0 == 0 ? j1 : (j0 == 1 ? 2 + j1 : (j0 == 2 ? 4 + j1 : 8));
-}
-
+constexpr uint32_t kConjBit = 1u << 19;
 __device__ __forceinline__ gw_index_rec load_rec(const gw_index_rec* rec, uint32_t i) {
     int4 v = __ldg(reinterpret_cast<const int4*>(rec) + i);
     return *reinterpret_cast<gw_index_rec*>(&v);
@@ -112,6 +116,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
         if (global_ns() - t0 > 2000000000ull) return false;
     }
 }
+__device__ __forceinline__ void producer_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kProducerBar), "n"(kProducerThreads) : "memory");
+}
+
+// ---- asynchronous global -> shared copies ----------------------------------
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
 
 // Commit with the rounding error kept: the vector atomic returns the value
 // it added to, so the exact error of the (round-to-nearest) sum it stored is
@@ -136,90 +156,77 @@ __device__ __forceinline__ void commit_compensated(float2* g, float2* err, float
 }
 
 template <int R>
-constexpr int list_cap() { return kBatch + 4 * R; }
+constexpr int list_cap() { return kBatch + 2 * R; }
 
 template <int NPOL, int B, int R>
 struct Smem {
-    float4 v[B][kBatch + 1][NPOL];         // (A.re, A.im, B.re, B.im) per polarisation; row kBatch = 0
-    // per warp: full entries from the front, partial entries below the top
-    // R null entries (see the producer)
+    float2 v[B][kBatch + 1][NPOL];          // weighted visibilities; row kBatch = 0
+    // per warp: list entries, padded to a multiple of R, then R null entries
     uint2 list[B][kComputeWarps][list_cap<R>()];
-    int cnt[B][kComputeWarps];             // full entries, padded to a multiple of R
-    int cntp[B][kComputeWarps];            // partial entries, padded to a multiple of R
+    int cnt[B][kComputeWarps];             // entries, padded to a multiple of R
     int tile[B];                           // tile of the batch; -1 = end of work
     int last[B];                           // batch ends its work item
+    Item item;                             // producers: the current work item
+    int done;                              // producers: no work item left
     unsigned long long full[B], empty[B];  // mbarriers
 };
 
-// Packed FMAs of one entry into slots J0..J1 (compile-time range).
+// Packed FMAs of one entry into slots J0..J1 (compile-time range); A = V,
+// Bv = s (-V.im, V.re).
 template <int NPOL, int J0, int J1>
 __device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const float2 (&Kc)[4],
-                                         const float4 (&V)[NPOL]) {
+                                         const float2 (&A)[NPOL], const float2 (&Bv)[NPOL]) {
 #pragma unroll
     for (int j = J0; j <= J1; ++j) {
         const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
         const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
 #pragma unroll
-        for (int p = 0; p < NPOL; ++p)
-            acc[j][p] = __ffma2_rn(kxx, make_float2(V[p].x, V[p].y), acc[j][p]);
+        for (int p = 0; p < NPOL; ++p) acc[j][p] = __ffma2_rn(kxx, A[p], acc[j][p]);
 #pragma unroll
-        for (int p = 0; p < NPOL; ++p)
-            acc[j][p] = __ffma2_rn(kyy, make_float2(V[p].z, V[p].w), acc[j][p]);
+        for (int p = 0; p < NPOL; ++p) acc[j][p] = __ffma2_rn(kyy, Bv[p], acc[j][p]);
     }
 }
 
+// Staged visibility of an entry and the second FMA operand s (-V.im, V.re).
 template <int NPOL>
-__device__ __forceinline__ void load_v(float4 (&V)[NPOL], const float4 (*vs)[NPOL], uint32_t ey) {
+__device__ __forceinline__ void load_v(float2 (&A)[NPOL], float2 (&Bv)[NPOL],
+                                       const float2 (*vs)[NPOL], uint32_t ey) {
+    const float2* row = vs[ey & 0x1ff];
+    if (NPOL % 2 == 0) {
 #pragma unroll
-    for (int p = 0; p < NPOL; ++p) V[p] = vs[ey & 0x1ff][p];
-}
-
-// Entries meeting all four slots of the warp's block.  n is a multiple of
-// R and R null entries follow the last one.
-template <int NPOL, int SP, int R, class TE>
-__device__ __forceinline__ void run_full(const uint2* lst, int n, const float4 (*vs)[NPOL],
-                                         const typename TE::T* __restrict__ tab,
-                                         float2 (&K)[R][4], float2 (&acc)[4][NPOL]) {
-    if (n == 0) return;
-    uint32_t ey[R];
-#pragma unroll
-    for (int d = 0; d < R; ++d) {
-        const uint2 en = lst[d];
-        ey[d] = en.y;
-        const typename TE::T* p_ = tab + (int)en.x;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) K[d][j] = TE::load(p_ + 4 * j * SP);
-    }
-    for (int i = 0; i < n; i += R) {
-#pragma unroll
-        for (int d = 0; d < R; ++d) {
-            float4 V[NPOL];
-            load_v<NPOL>(V, vs, ey[d]);
-            slot_fma<NPOL, 0, 3>(acc, K[d], V);
-            const uint2 en = lst[i + R + d];
-            ey[d] = en.y;
-            const typename TE::T* p_ = tab + (int)en.x;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) K[d][j] = TE::load(p_ + 4 * j * SP);
+        for (int p = 0; p < NPOL; p += 2) {
+            const float4 q = *reinterpret_cast<const float4*>(row + p);
+            A[p] = make_float2(q.x, q.y);
+            A[p + 1] = make_float2(q.z, q.w);
         }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NPOL; ++p) A[p] = row[p];
     }
+    const float s = (ey & kConjBit) ? -1.f : 1.f;
+#pragma unroll
+    for (int p = 0; p < NPOL; ++p) Bv[p] = make_float2(-s * A[p].y, s * A[p].x);
 }
 
-// Entries meeting some of the slots: loads only of the slots in the entry's
-// mask, one warp-uniform jump to the code for its slot range.
+// The warp's list entries of a batch.  n is a multiple of R and R null
+// entries follow the last one.  Each entry loads the kernel values of the
+// slots in its mask (zero for the others) and updates all four slots: the
+// FMAs of the slots outside the mask add zeros, which costs spare FMA issue
+// but keeps one short loop body per ring position (no per-entry jump).
 template <int NPOL, int SP, int R, class TE>
-__device__ __forceinline__ void run_part(const uint2* lst, int n, const float4 (*vs)[NPOL],
-                                         const typename TE::T* __restrict__ tab,
-                                         float2 (&K)[R][4], float2 (&acc)[4][NPOL]) {
+__device__ __forceinline__ void run_entries(const uint2* lst, int n, const float2 (*vs)[NPOL],
+                                            const typename TE::T* __restrict__ tab,
+                                            float2 (&K)[R][4], float2 (&acc)[4][NPOL]) {
     if (n == 0) return;
     uint32_t ey[R];
     auto load_masked = [&](const uint2 en, float2 (&Kd)[4]) {
         const uint32_t m = en.y >> 20;
         const typename TE::T* p_ = tab + (int)en.x;
-        if (m & 1u) Kd[0] = TE::load(p_);
-        if (m & 2u) Kd[1] = TE::load(p_ + 4 * SP);
-        if (m & 4u) Kd[2] = TE::load(p_ + 8 * SP);
-        if (m & 8u) Kd[3] = TE::load(p_ + 12 * SP);
+        const float2 z = make_float2(0.f, 0.f);
+        Kd[0] = (m & 1u) ? TE::load(p_) : z;
+        Kd[1] = (m & 2u) ? TE::load(p_ + 4 * SP) : z;
+        Kd[2] = (m & 4u) ? TE::load(p_ + 8 * SP) : z;
+        Kd[3] = (m & 8u) ? TE::load(p_ + 12 * SP) : z;
     };
 #pragma unroll
     for (int d = 0; d < R; ++d) {
@@ -230,19 +237,9 @@ __device__ __forceinline__ void run_part(const uint2* lst, int n, const float4 (
     for (int i = 0; i < n; i += R) {
 #pragma unroll
         for (int d = 0; d < R; ++d) {
-            float4 V[NPOL];
-            load_v<NPOL>(V, vs, ey[d]);
-            switch ((ey[d] >> 16) & 15u) {
-                case 0: slot_fma<NPOL, 0, 0>(acc, K[d], V); break;
-                case 1: slot_fma<NPOL, 0, 1>(acc, K[d], V); break;
-                case 2: slot_fma<NPOL, 0, 2>(acc, K[d], V); break;
-                case 3: slot_fma<NPOL, 1, 1>(acc, K[d], V); break;
-                case 4: slot_fma<NPOL, 1, 2>(acc, K[d], V); break;
-                case 5: slot_fma<NPOL, 1, 3>(acc, K[d], V); break;
-                case 6: slot_fma<NPOL, 2, 2>(acc, K[d], V); break;
-                case 7: slot_fma<NPOL, 2, 3>(acc, K[d], V); break;
-                default: slot_fma<NPOL, 3, 3>(acc, K[d], V); break;
-            }
+            float2 A[NPOL], Bv[NPOL];
+            load_v<NPOL>(A, Bv, vs, ey[d]);
+            slot_fma<NPOL, 0, 3>(acc, K[d], A, Bv);
             const uint2 en = lst[i + R + d];
             ey[d] = en.y;
             load_masked(en, K[d]);
@@ -251,87 +248,109 @@ __device__ __forceinline__ void run_part(const uint2* lst, int n, const float4 (
 }
 
 template <int NPOL, int SP, int TK, int B, int R>
-__global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     using TE = TabElem<TK>;
-    constexpr int kCap = list_cap<R>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<NPOL, B, R>& sm = *reinterpret_cast<Smem<NPOL, B, R>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int side = a.ntiles_u;
     const int hb = a.beta / 2;
 
-    // one-time set-up: barriers, the zero visibility row, the top R null
-    // entries of every partial list
+    // one-time set-up: barriers, the zero visibility row
     if (threadIdx.x == 0) {
         for (int b = 0; b < B; ++b) {
-            mbar_init(&sm.full[b], 32);
+            mbar_init(&sm.full[b], kProducerThreads);
             mbar_init(&sm.empty[b], kComputeWarps * 32);
         }
     }
     for (int t = threadIdx.x; t < B * NPOL; t += kThreads)
-        sm.v[t / NPOL][kZeroRow][t % NPOL] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int t = threadIdx.x; t < B * kComputeWarps * R; t += kThreads) {
-        const int b = t / (kComputeWarps * R), w = (t / R) % kComputeWarps, k = t % R;
-        const int xnull = -(((w >> 2) * 16) * SP + (w & 3) * 8);
-        sm.list[b][w][kCap - R + k] = make_uint2((uint32_t)xnull, kZeroRow | (8u << 16));
-    }
+        sm.v[t / NPOL][kZeroRow][t % NPOL] = make_float2(0.f, 0.f);
     __syncthreads();
 
-    if (warp == kComputeWarps) {
-        // ------------------------------------------------------------ producer
+    if (warp >= kComputeWarps) {
+        // ----------------------------------------------------------- producers
+        const int pt = threadIdx.x - kComputeWarps * 32;   // 0 .. kProducerThreads - 1
+        const int pw = pt >> 5;
         const uint32_t nitems = *a.item_count;
+        // visibilities copied as they are: FP32 pairs without weights, with
+        // the 16-byte alignment the 16-byte copies need (pairs of polarisations)
+        const bool copy_vis = a.vis_kind == GW_C64 && a.weight == nullptr &&
+                              (NPOL % 2 == 1 || reinterpret_cast<uintptr_t>(a.vis) % 16 == 0);
         uint32_t nbatch = 0;
         for (;;) {
-            uint32_t it = 0;
-            if (lane == 0) it = atomicAdd(a.queue, 1u);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            const bool done = it >= nitems;
+            int b = 0, nb_total = 1;
+            bool done = false;
             Item item{};
-            if (!done) item = a.items[it];
-            const int nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
-            for (int b = 0; b < nb_total; ++b) {
+            for (;;) {   // batches of the current work item
                 const int buf = nbatch % B;
                 if (nbatch >= (uint32_t)B &&
                     !mbar_wait(&sm.empty[buf], ((nbatch / B) - 1) & 1)) {
                     if (lane == 0) atomicOr(a.queue + 1, 1u);
                     return;
                 }
-                if (lane < kComputeWarps) {
-                    sm.cnt[buf][lane] = 0;
-                    sm.cntp[buf][lane] = 0;
-                }
-                __syncwarp();
-                if (done) {
-                    if (lane == 0) {
-                        sm.tile[buf] = -1;
-                        sm.last[buf] = 1;
+                if (pw == 0) {
+                    if (b == 0 && lane == 0) {
+                        const uint32_t it = atomicAdd(a.queue, 1u);
+                        sm.done = it >= nitems;
+                        if (it < nitems) sm.item = a.items[it];
                     }
-                } else {
+                    if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
+                }
+                producer_sync();
+                if (b == 0) {
+                    done = sm.done != 0;
+                    if (!done) item = sm.item;
+                    nb_total = done ? 1 : (item.len + kBatch - 1) / kBatch;
+                }
+                if (!done) {
                     // with w-layers (w-stacking) a tile id is layer * layer_tiles + tile
                     const int ltile = a.layer_tiles ? item.tile % a.layer_tiles : item.tile;
                     const int tu0 = (ltile % side) * kTile;
                     const int tv0 = (ltile / side) * kTile;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
-                    // all ids, then all records of this lane's rows in flight at once
+                    // all ids, then all index records of this thread's rows in flight
                     uint32_t ids[kPerLane];
                     gw_index_rec rcs[kPerLane];
 #pragma unroll
                     for (int k = 0; k < kPerLane; ++k) {
-                        const int r = k * 32 + lane;
+                        const int r = k * kProducerThreads + pt;
                         ids[k] = r < nb ? __ldg(a.entries + item.start + b0 + r) : 0u;
                     }
 #pragma unroll
                     for (int k = 0; k < kPerLane; ++k) {
-                        const int r = k * 32 + lane;
+                        const int r = k * kProducerThreads + pt;
                         if (r < nb) rcs[k] = load_rec(a.rec, ids[k]);
                     }
 #pragma unroll
                     for (int k = 0; k < kPerLane; ++k) {
-                        const int r = k * 32 + lane;
+                        const int r = k * kProducerThreads + pt;
                         if (r >= nb) break;
                         const uint32_t id = ids[k];
                         const gw_index_rec rc = rcs[k];
+                        if (copy_vis) {
+                            const float2* src = reinterpret_cast<const float2*>(a.vis) +
+                                                (int64_t)id * NPOL;
+                            if (NPOL % 2 == 0) {
+#pragma unroll
+                                for (int p = 0; p < NPOL; p += 2)
+                                    cp_async16(&sm.v[buf][r][p], src + p);
+                            } else {
+#pragma unroll
+                                for (int p = 0; p < NPOL; ++p) cp_async8(&sm.v[buf][r][p], src + p);
+                            }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < NPOL; ++p) {
+                                float2 v = load_vis(a.vis, a.vis_kind, (int64_t)id * NPOL + p);
+                                if (a.weight) {
+                                    const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
+                                    v.x *= w;
+                                    v.y *= w;
+                                }
+                                sm.v[buf][r][p] = v;
+                            }
+                        }
                         // w-stacking records carry their layer in `plane`; the
                         // kernel is the plan's single (w = 0) plane
                         const int plane = a.layer_tiles ? 0 : rc.plane;
@@ -341,18 +360,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                                                   (int64_t)(S + 6) * SP;
                         // padded index of the tile origin relative to this record
                         const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
-                        const bool conj = (rc.flags & GW_FLAG_CONJ) != 0;
-#pragma unroll
-                        for (int p = 0; p < NPOL; ++p) {
-                            float2 v = load_vis(a.vis, a.vis_kind, (int64_t)id * NPOL + p);
-                            if (a.weight) {
-                                const float w = __ldg(a.weight + (int64_t)id * NPOL + p);
-                                v.x *= w;
-                                v.y *= w;
-                            }
-                            sm.v[buf][r][p] = conj ? make_float4(v.x, v.y, v.y, -v.x)
-                                                   : make_float4(v.x, v.y, -v.y, v.x);
-                        }
+                        const uint32_t conj = (rc.flags & GW_FLAG_CONJ) ? kConjBit : 0u;
                         // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
                         const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
                         const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
@@ -362,45 +370,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
                             const int j0 = max(0, vlo - 16 * cv) >> 2;
                             const int j1 = min(15, vhi - 16 * cv) >> 2;
                             const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
-                            const uint2 e = make_uint2(
-                                (uint32_t)base, (uint32_t)r | ((uint32_t)slot_case(j0, j1) << 16) |
-                                                    (mask << 20));
-                            const bool full = mask == 15u;
+                            const uint2 e = make_uint2((uint32_t)base,
+                                                       (uint32_t)r | (mask << 20) | conj);
                             for (int cu = cu0; cu <= cu1; ++cu) {
                                 const int w = cv * 4 + cu;
-                                if (full) {
-                                    const int pos = atomicAdd(&sm.cnt[buf][w], 1);
-                                    sm.list[buf][w][pos] = e;
-                                } else {
-                                    const int pos = atomicAdd(&sm.cntp[buf][w], 1);
-                                    sm.list[buf][w][kCap - R - 1 - pos] = e;
-                                }
+                                const int pos = atomicAdd(&sm.cnt[buf][w], 1);
+                                sm.list[buf][w][pos] = e;
                             }
                         }
                     }
-                    if (lane == 0) {
-                        sm.tile[buf] = item.tile;
-                        sm.last[buf] = (b == nb_total - 1);
+                    if (copy_vis) cp_async_wait_all();
+                }
+                producer_sync();   // all rows staged, all list appends done
+                if (pw == 0) {
+                    // pad every warp's list to a multiple of R and put R null
+                    // entries (no slots loaded, the zero visibility row) after it
+                    if (lane < kComputeWarps) {
+                        const int w = lane;
+                        const int nf = sm.cnt[buf][w];
+                        const int nfp = (nf + R - 1) / R * R;
+                        const uint2 z = make_uint2(0u, kZeroRow);
+                        for (int k = nf; k < nfp + R; ++k) sm.list[buf][w][k] = z;
+                        sm.cnt[buf][w] = nfp;
                     }
+                    if (lane == 0) {
+                        sm.tile[buf] = done ? -1 : item.tile;
+                        sm.last[buf] = done ? 1 : (b == nb_total - 1);
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
-                // pad every warp's lists to a multiple of R and put R null
-                // entries after the full list (the partial list's are fixed)
-                if (lane < kComputeWarps) {
-                    const int w = lane;
-                    const uint32_t xnull = (uint32_t)(-(((w >> 2) * 16) * SP + (w & 3) * 8));
-                    const int nf = sm.cnt[buf][w], np = sm.cntp[buf][w];
-                    const int nfp = (nf + R - 1) / R * R, npp = (np + R - 1) / R * R;
-                    const uint2 zf = make_uint2(xnull, kZeroRow | (15u << 20) | (9u << 16));
-                    const uint2 zp = make_uint2(xnull, kZeroRow | (8u << 16));
-                    for (int k = nf; k < nfp + R; ++k) sm.list[buf][w][k] = zf;
-                    for (int k = np; k < npp; ++k) sm.list[buf][w][kCap - R - 1 - k] = zp;
-                    sm.cnt[buf][w] = nfp;
-                    sm.cntp[buf][w] = npp;
-                }
-                __syncwarp();
-                mbar_arrive(&sm.full[buf]);  // batch ready (every producer lane)
+                mbar_arrive(&sm.full[buf]);  // batch ready (every producer thread)
                 ++nbatch;
+                if (++b == nb_total) break;
             }
             if (done) break;
         }
@@ -436,10 +437,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_grid(GridArgs a) {
         const int tile = sm.tile[buf];
         if (tile < 0) break;
         const int last = sm.last[buf];
-        const int nf = sm.cnt[buf][warp], np = sm.cntp[buf][warp];
-        const uint2* lst = sm.list[buf][warp];
-        run_full<NPOL, SP, R, TE>(lst, nf, sm.v[buf], tab, K, acc);
-        run_part<NPOL, SP, R, TE>(lst + kCap - R - np, np, sm.v[buf], tab, K, acc);
+        run_entries<NPOL, SP, R, TE>(sm.list[buf][warp], sm.cnt[buf][warp], sm.v[buf], tab, K,
+                                     acc);
         mbar_arrive(&sm.empty[buf]);  // buffer free (every lane, after its reads)
         ++nbatch;
         if (last) {
@@ -484,14 +483,17 @@ void launch_v(const GridArgs& a, int num_sms, cudaStream_t s) {
     note_launch();
 }
 
-// Three staging buffers of 256 records and a ring of GW_GRID_RING kernel-value
-// register sets per compute warp.
+// GW_GRID_BUFS staging buffers of 256 records and a ring of GW_GRID_RING
+// kernel-value register sets per compute warp.
 #ifndef GW_GRID_RING
-#define GW_GRID_RING 2
+#define GW_GRID_RING 10
+#endif
+#ifndef GW_GRID_BUFS
+#define GW_GRID_BUFS 4
 #endif
 template <int NPOL, int SP, int TK>
 void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
-    launch_v<NPOL, SP, TK, 3, GW_GRID_RING>(a, num_sms, s);
+    launch_v<NPOL, SP, TK, GW_GRID_BUFS, GW_GRID_RING>(a, num_sms, s);
 }
 
 template <int NPOL, int TK>
