@@ -36,7 +36,8 @@
 // * The producers pad every warp's list to a multiple of R and append R more
 //   null entries (no loads, the all-zero visibility row), so the compute loop
 //   has no tail tests: the kernel values of entry i + R are loaded into the
-//   registers entry i has just used.  An entry loads the slots its record
+//   registers entry i has just used, and the last pass over a batch loads the
+//   first entries of the next batch (the ring never drains between batches).  An entry loads the slots its record
 //   meets and zeros for the others, and always updates all four slots (one
 //   loop body, no per-entry jump: the code stays small at ring depth R).
 // * Kernel values come from zero-padded slices (7 zero columns and 3 zero
@@ -208,42 +209,48 @@ __device__ __forceinline__ void load_v(float2 (&A)[NPOL], float2 (&Bv)[NPOL],
     for (int p = 0; p < NPOL; ++p) Bv[p] = make_float2(-s * A[p].y, s * A[p].x);
 }
 
-// The warp's list entries of a batch.  n is a multiple of R and R null
-// entries follow the last one.  Each entry loads the kernel values of the
-// slots in its mask (zero for the others) and updates all four slots: the
-// FMAs of the slots outside the mask add zeros, which costs spare FMA issue
-// but keeps one short loop body per ring position (no per-entry jump).
-template <int NPOL, int SP, int R, class TE>
-__device__ __forceinline__ void run_entries(const uint2* lst, int n, const float2 (*vs)[NPOL],
-                                            const typename TE::T* __restrict__ tab,
-                                            float2 (&K)[R][4], float2 (&acc)[4][NPOL]) {
-    if (n == 0) return;
-    uint32_t ey[R];
-    auto load_masked = [&](const uint2 en, float2 (&Kd)[4]) {
-        const uint32_t m = en.y >> 20;
-        const typename TE::T* p_ = tab + (int)en.x;
-        const float2 z = make_float2(0.f, 0.f);
-        Kd[0] = (m & 1u) ? TE::load(p_) : z;
-        Kd[1] = (m & 2u) ? TE::load(p_ + 4 * SP) : z;
-        Kd[2] = (m & 4u) ? TE::load(p_ + 8 * SP) : z;
-        Kd[3] = (m & 8u) ? TE::load(p_ + 12 * SP) : z;
-    };
+// Kernel values of one list entry: the slots in its mask, zero for the others.
+template <int SP, class TE>
+__device__ __forceinline__ void load_masked(const typename TE::T* __restrict__ tab, const uint2 en,
+                                            float2 (&Kd)[4]) {
+    const uint32_t m = en.y >> 20;
+    const typename TE::T* p_ = tab + (int)en.x;
+    const float2 z = make_float2(0.f, 0.f);
+    Kd[0] = (m & 1u) ? TE::load(p_) : z;
+    Kd[1] = (m & 2u) ? TE::load(p_ + 4 * SP) : z;
+    Kd[2] = (m & 4u) ? TE::load(p_ + 8 * SP) : z;
+    Kd[3] = (m & 8u) ? TE::load(p_ + 12 * SP) : z;
+}
+
+// Fills the ring with the first R entries of a list.
+template <int SP, int R, class TE>
+__device__ __forceinline__ void ring_fill(const uint2* lst, const typename TE::T* __restrict__ tab,
+                                          float2 (&K)[R][4], uint32_t (&ey)[R]) {
 #pragma unroll
     for (int d = 0; d < R; ++d) {
         const uint2 en = lst[d];
         ey[d] = en.y;
-        load_masked(en, K[d]);
+        load_masked<SP, TE>(tab, en, K[d]);
     }
-    for (int i = 0; i < n; i += R) {
+}
+
+// One ring pass: the FMAs of the R entries in the ring, each followed by the
+// loads of the entry R positions later, taken from `next`.  Every entry
+// updates all four slots; the slots outside its mask add zeros (spare FMA
+// issue, but one short loop body per ring position and no per-entry jump).
+template <int NPOL, int SP, int R, class TE>
+__device__ __forceinline__ void ring_pass(const uint2* next, const float2 (*vs)[NPOL],
+                                          const typename TE::T* __restrict__ tab,
+                                          float2 (&K)[R][4], uint32_t (&ey)[R],
+                                          float2 (&acc)[4][NPOL]) {
 #pragma unroll
-        for (int d = 0; d < R; ++d) {
-            float2 A[NPOL], Bv[NPOL];
-            load_v<NPOL>(A, Bv, vs, ey[d]);
-            slot_fma<NPOL, 0, 3>(acc, K[d], A, Bv);
-            const uint2 en = lst[i + R + d];
-            ey[d] = en.y;
-            load_masked(en, K[d]);
-        }
+    for (int d = 0; d < R; ++d) {
+        float2 A[NPOL], Bv[NPOL];
+        load_v<NPOL>(A, Bv, vs, ey[d]);
+        slot_fma<NPOL, 0, 3>(acc, K[d], A, Bv);
+        const uint2 en = next[d];
+        ey[d] = en.y;
+        load_masked<SP, TE>(tab, en, K[d]);
     }
 }
 
@@ -422,23 +429,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     // kernel-value ring; finite values only (zero, then table values), so the
     // null entries' zero visibility row contributes exact zeros
     float2 K[R][4];
+    uint32_t ey[R];
 #pragma unroll
     for (int d = 0; d < R; ++d)
 #pragma unroll
         for (int j = 0; j < 4; ++j) K[d][j] = make_float2(0.f, 0.f);
 
+    // The ring runs across batches: the last pass over a batch's list loads
+    // the first R entries of the next batch, so no batch starts with an empty
+    // ring.  Lists are padded to a multiple of R and followed by R null
+    // entries (the end-of-work batch has only those).
+    if (!mbar_wait(&sm.full[0], 0)) {
+        if (lane == 0) atomicOr(a.queue + 1, 1u);
+        return;
+    }
+    ring_fill<SP, R, TE>(sm.list[0][warp], tab, K, ey);
     uint32_t nbatch = 0;
     for (;;) {
         const int buf = nbatch % B;
-        if (!mbar_wait(&sm.full[buf], (nbatch / B) & 1)) {
-            if (lane == 0) atomicOr(a.queue + 1, 1u);
-            return;
-        }
         const int tile = sm.tile[buf];
         if (tile < 0) break;
         const int last = sm.last[buf];
-        run_entries<NPOL, SP, R, TE>(sm.list[buf][warp], sm.cnt[buf][warp], sm.v[buf], tab, K,
-                                     acc);
+        const int n = sm.cnt[buf][warp];
+        const uint2* lst = sm.list[buf][warp];
+        const int nbuf = (nbatch + 1) % B;
+        const uint2* nlst = sm.list[nbuf][warp];
+        for (int i = 0;; i += R) {
+            const bool tail = i + R >= n;
+            if (tail && !mbar_wait(&sm.full[nbuf], ((nbatch + 1) / B) & 1)) {
+                if (lane == 0) atomicOr(a.queue + 1, 1u);
+                return;
+            }
+            if (n == 0) {   // nothing of this batch for this warp
+                ring_fill<SP, R, TE>(nlst, tab, K, ey);
+                break;
+            }
+            ring_pass<NPOL, SP, R, TE>(tail ? nlst : lst + i + R, sm.v[buf], tab, K, ey, acc);
+            if (tail) break;
+        }
         mbar_arrive(&sm.empty[buf]);  // buffer free (every lane, after its reads)
         ++nbatch;
         if (last) {
@@ -486,7 +514,7 @@ void launch_v(const GridArgs& a, int num_sms, cudaStream_t s) {
 // GW_GRID_BUFS staging buffers of 256 records and a ring of GW_GRID_RING
 // kernel-value register sets per compute warp.
 #ifndef GW_GRID_RING
-#define GW_GRID_RING 10
+#define GW_GRID_RING 8
 #endif
 #ifndef GW_GRID_BUFS
 #define GW_GRID_BUFS 4
