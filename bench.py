@@ -160,22 +160,50 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(obs, rows):
-    """The FP64 oracle on a bounded sample of the workload (host cores)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_baseline(obs, rows, rows_single):
+    """The FP64 oracle on bounded samples of the workload (host cores): the
+    same stages as the GPU step, index selection and gridding, timed
+    together; all host threads on `rows` rows, one thread on `rows_single`."""
     import numpy as np
     from oracle.cgrid import Oracle, default_threads
     from oracle.wkernel import Params, plane_support
     prm = Params(**obs.plan_kwargs())
     orc = Oracle(prm)
-    sub = slice(0, rows)
-    idx = orc.index(obs.uvw_m[sub], obs.freq_hz)
     S = plane_support(prm)
-    taps = int(np.sum(S[idx["plane"]][idx["valid"]] ** 2))
+
+    def timed(nr, th):
+        sub = slice(0, nr)
+        t0 = time.perf_counter()
+        idx = orc.index(obs.uvw_m[sub], obs.freq_hz)
+        orc.grid(obs.uvw_m[sub], obs.freq_hz, obs.vis[sub], idx=idx, nthreads=th)
+        dt = time.perf_counter() - t0
+        taps = int(np.sum(S[idx["plane"]][idx["valid"]] ** 2))
+        return taps * prm.npol / dt, dt
+
     th = default_threads()
-    t0 = time.perf_counter()
-    orc.grid(obs.uvw_m[sub], obs.freq_hz, obs.vis[sub], idx=idx, nthreads=th)
-    dt = time.perf_counter() - t0
-    return taps * prm.npol / dt, th, dt, taps
+    v, dt = timed(rows, th)
+    v1, dt1 = timed(rows_single, 1)
+    return {"value": v, "threads": th, "seconds": dt, "single_thread_value": v1,
+            "single_thread_seconds": dt1, "single_thread_rows": rows_single}
 
 
 def run_reference(args, world, rank):
@@ -195,25 +223,27 @@ def run_reference(args, world, rank):
     for step in range(args.warmup + args.steps):
         r0 = (step * rows) % (obs.nrow - rows)
         sub = slice(r0, r0 + rows)
-        idx = orc.index(obs.uvw_m[sub], obs.freq_hz)
-        taps = int(np.sum(S[idx["plane"]][idx["valid"]] ** 2))
+        # the GPU step's stages: index selection, then gridding
         t0 = time.perf_counter()
+        idx = orc.index(obs.uvw_m[sub], obs.freq_hz)
         orc.grid(obs.uvw_m[sub], obs.freq_hz, obs.vis[sub], idx=idx, nthreads=th)
         dt = time.perf_counter() - t0
+        taps = int(np.sum(S[idx["plane"]][idx["valid"]] ** 2))
         if step >= args.warmup:
             times.append(dt)
             taps_tot += taps
     value = taps_tot * prm.npol / sum(times)
     sample = (f"{rows} consecutive rows (1/64 of the workload's rows, all 16 channels) per step, "
-              f"FP64 C oracle, {th} threads")
+              f"FP64 oracle index selection (numpy) + gridding (C, {th} threads)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": obs.name, "rows_per_step": rows},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "threads": th,
+                         "kind": "oracle", "includes": "index+grid", "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -663,10 +693,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = args.cpu_sample_rows or obs.nrow // 8
-        v, th, dt, taps = cpu_baseline(obs, rows)
-        cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+        rows1 = max(1, rows // 8)
+        cb = cpu_baseline(obs, rows, rows1)
+        cpu = {"value": cb["value"], "unit": UNIT, "cores": cb["threads"],
+               "threads": cb["threads"], "kind": "oracle", "includes": "index+grid",
+               "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+               "single_thread_value": cb["single_thread_value"],
                "sample": f"first {rows} rows (1/{obs.nrow // rows} of the workload, all "
-                         f"{obs.nchan} channels), FP64 C oracle, {dt:.1f} s"}
+                         f"{obs.nchan} channels): FP64 oracle index selection (numpy) + "
+                         f"gridding (C, {cb['threads']} threads), {cb['seconds']:.1f} s; "
+                         f"single thread on the first {rows1} rows, "
+                         f"{cb['single_thread_seconds']:.1f} s"}
 
     if rank == 0:
         line = {

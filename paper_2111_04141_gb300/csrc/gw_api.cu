@@ -24,6 +24,22 @@ void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_re
 static std::atomic<int64_t> g_fail_countdown{0};
 static std::atomic<int64_t> g_live_plans{0};
 
+int current_sm_count() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < kMaxDev) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+        return 1;
+    if (dev < kMaxDev) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 bool alloc_fault() {
     int64_t k = g_fail_countdown.load();
     while (k > 0) {

@@ -260,7 +260,7 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
     }
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > current_sm_count() * 8) blocks = current_sm_count() * 8;
     if (blocks < 1) blocks = 1;
     if (nvis > 0) {
         if (sm_blocks > 0)

@@ -99,7 +99,7 @@ __global__ void k_compact(unsigned long long* __restrict__ keys, float2* __restr
 
 unsigned blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > current_sm_count() * 16) b = current_sm_count() * 16;
     return (unsigned)std::max<int64_t>(b, 1);
 }
 

@@ -121,7 +121,7 @@ __global__ void k_wstack_combine(const float2* __restrict__ layers, int nlayers,
 
 unsigned blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > current_sm_count() * 32) b = current_sm_count() * 32;
     return (unsigned)std::max<int64_t>(b, 1);
 }
 

@@ -44,7 +44,7 @@ __global__ void k_weight_vis(const void* __restrict__ vis, int kind, const float
 void launch_weight_vis(const void* vis, int kind, const float* w, int64_t n, float2* out,
                        cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > current_sm_count() * 16) blocks = current_sm_count() * 16;
     if (blocks < 1) blocks = 1;
     k_weight_vis<<<(unsigned)blocks, 256, 0, s>>>(vis, kind, w, n, out);
     note_launch();

@@ -137,7 +137,7 @@ void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan
     if (nvis <= 0) return;
     const int threads = 256;
     int64_t blocks = (nvis + threads - 1) / threads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > current_sm_count() * 16) blocks = current_sm_count() * 16;
     const size_t smem = sizeof(double) * (size_t)(std::min(nchan, kChanCache) +
                                                   (prm.P > 1 ? prm.P - 1 : 0));
     k_index<<<(unsigned)blocks, threads, smem, s>>>(uvw, freq, nrow, d_nrow, nchan, prm, out,

@@ -126,6 +126,10 @@ struct Scratch {
 // ---- launch counting -----------------------------------------------------
 void note_launch(int n = 1);
 
+// SM count of the current device (cached per device); grid-stride kernels
+// size their grids as a multiple of it.
+int current_sm_count();
+
 // ---- allocations -----------------------------------------------------------
 // Every device allocation of the library goes through dev_alloc and every
 // host allocation of a plan object checks alloc_fault(), so a test can make
