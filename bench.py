@@ -74,6 +74,8 @@ def parse():
                     help="skip the dirty-image pipeline and R(X) measurements")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 16-bit-storage and compensated-commit measurements")
+    ap.add_argument("--no-c5", action="store_true",
+                    help="skip the 8192^2, 128-plane (C5) storage-precision timing")
     ap.add_argument("--cpu-sample-rows", type=int, default=0,
                     help="rows of the workload in the CPU-baseline sample (0 = 1/8 of rows)")
     ap.add_argument("--times", type=int, default=256,
@@ -342,6 +344,92 @@ def measure_imaging(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
             "R_X": {"max_X_le_32": float(r[:33].max()), "max_all": float(r.max()),
                     "X": list(range(64)), "R": [float(t) for t in r],
                     "setup": "16 antennas, 3,840 vis, 128^2, support 7, oversampling 128"}}
+
+
+def grid_roofline(tm, calls, npol, peak):
+    """FP32-FMA roofline of the gridding kernel from a plan's stage timing."""
+    ms = tm["grid_ms"] / max(1, tm["grid_calls"])
+    flop = tm["taps"] / max(1, calls) * npol * FLOP_PER_UPDATE / max(1, tm["grid_calls"] / calls)
+    tf = flop / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel_ms": ms, "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+            "frac": tf / peak}
+
+
+def measure_c5(gw, dev, stream, steps, peak):
+    """The 8192^2 x 4, 128-plane, support 7->127 workload (133.7M visibilities
+    x 4 pols; tables far larger than L2): one gridding step (index, bin, grid)
+    with FP32 storage and with bfloat16 / float16 tables and visibilities.
+    Visibilities are CN(0, 1) drawn on the device (seeded); uvw, channels and
+    imaging parameters come from the synthetic generator."""
+    import torch
+    import synthetic as syn
+    from paper_2111_04141_gb300.plan import to_storage
+    obs = syn.config_precision(with_vis=False)
+    uvw = torch.from_numpy(obs.uvw_m).to(dev)
+    freq = torch.from_numpy(obs.freq_hz).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(20211108)
+    vis = torch.randn((obs.nrow, obs.nchan, obs.npol), dtype=torch.complex64, device=dev,
+                      generator=gen)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": obs.name, "nvis": obs.nvis, "npol": obs.npol, "grid_n": obs.grid_n,
+           "n_wplanes": obs.n_wplanes, "support": f"{obs.support_min}->{obs.support_max}",
+           "vis": "CN(0,1) drawn on the device (torch, seeded)"}
+    for kind in ("c64", "bf16", "f16"):
+        with gw.Plan.from_observation(obs, table_dtype=kind, vis_dtype=kind) as p:
+            v = vis if kind == "c64" else to_storage(vis, kind)
+            g = p.new_grid()
+            p.grid(uvw, freq, v, out=g)
+            torch.cuda.synchronize(dev)
+            p.timing(True)
+            p.timing()
+            e0.record(stream)
+            for _ in range(steps):
+                p.grid(uvw, freq, v, out=g)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            tm = p.timing()
+            info = p.info
+            out[kind] = {"value": tm["taps"] / steps * obs.npol / (ms * 1e-3), "unit": UNIT,
+                         "ms_per_step": ms, "roofline": grid_roofline(tm, steps, obs.npol, peak),
+                         "stage_ms_per_step": {k: tm[f"{k}_ms"] / steps
+                                               for k in ("index", "bin", "grid")},
+                         "table_bytes": int(info.table_bytes),
+                         "mean_S2": tm["taps"] / max(1, tm["valid_vis"])}
+            del g
+            if kind != "c64":
+                del v
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_c1(gw, dev, stream, steps, peak):
+    """The 2-D workload (16 antennas, 3,840 visibilities, 256^2, support 7,
+    1 pol): one gridding step; small enough to be bound by launches."""
+    import torch
+    import synthetic as syn
+    obs = syn.config_2d()
+    uvw = torch.from_numpy(obs.uvw_m).to(dev)
+    freq = torch.from_numpy(obs.freq_hz).to(dev)
+    vis = torch.from_numpy(obs.vis).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with gw.Plan.from_observation(obs) as p:
+        g = p.new_grid()
+        for _ in range(3):
+            p.grid(uvw, freq, vis, out=g)
+        torch.cuda.synchronize(dev)
+        p.timing(True)
+        p.timing()
+        e0.record(stream)
+        for _ in range(steps):
+            p.grid(uvw, freq, vis, out=g)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        tm = p.timing()
+    return {"workload": obs.name, "nvis": obs.nvis, "value": tm["taps"] / steps * obs.npol /
+            (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "roofline": grid_roofline(tm, steps, obs.npol, peak)}
 
 
 def measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
@@ -689,6 +777,8 @@ def main():
         gw, plan, obs, uvw, freq, vis, dev, stream, nd))
     variants = optional(not args.no_variants, lambda: measure_next(
         gw, plan, obs, uvw, freq, vis, dev, stream, 3))
+    c1 = optional(True, lambda: measure_c1(gw, dev, stream, 50, peak))
+    c5 = optional(not args.no_c5, lambda: measure_c5(gw, dev, stream, 3, peak))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -724,7 +814,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "paper_context": PAPER_CONTEXT,
             "clocks": clocks, "degrid": degrid, "precision": precision, "imaging": imaging,
-            "variants": variants,
+            "variants": variants, "c1": c1, "c5": c5,
             "serving": serving,
         }
         print(json.dumps(line))

@@ -174,13 +174,14 @@ struct Smem {
 
 // Packed FMAs of one entry into slots J0..J1 (compile-time range); A = V,
 // Bv = s (-V.im, V.re).
-template <int NPOL, int J0, int J1>
-__device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const float2 (&Kc)[4],
+template <int NPOL, int J0, int J1, class TE>
+__device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const typename TE::T (&Kr)[4],
                                          const float2 (&A)[NPOL], const float2 (&Bv)[NPOL]) {
 #pragma unroll
     for (int j = J0; j <= J1; ++j) {
-        const float2 kxx = make_float2(Kc[j].x, Kc[j].x);
-        const float2 kyy = make_float2(Kc[j].y, Kc[j].y);
+        const float2 kc = TE::cvt(Kr[j]);   // 16-bit pairs are widened here, at their use
+        const float2 kxx = make_float2(kc.x, kc.x);
+        const float2 kyy = make_float2(kc.y, kc.y);
 #pragma unroll
         for (int p = 0; p < NPOL; ++p) acc[j][p] = __ffma2_rn(kxx, A[p], acc[j][p]);
 #pragma unroll
@@ -209,23 +210,25 @@ __device__ __forceinline__ void load_v(float2 (&A)[NPOL], float2 (&Bv)[NPOL],
     for (int p = 0; p < NPOL; ++p) Bv[p] = make_float2(-s * A[p].y, s * A[p].x);
 }
 
-// Kernel values of one list entry: the slots in its mask, zero for the others.
+// Kernel values of one list entry, as stored: the slots in its mask, zero
+// (all bits clear, +0 in every storage kind) for the others.
 template <int SP, class TE>
 __device__ __forceinline__ void load_masked(const typename TE::T* __restrict__ tab, const uint2 en,
-                                            float2 (&Kd)[4]) {
+                                            typename TE::T (&Kd)[4]) {
+    using T = typename TE::T;
     const uint32_t m = en.y >> 20;
-    const typename TE::T* p_ = tab + (int)en.x;
-    const float2 z = make_float2(0.f, 0.f);
-    Kd[0] = (m & 1u) ? TE::load(p_) : z;
-    Kd[1] = (m & 2u) ? TE::load(p_ + 4 * SP) : z;
-    Kd[2] = (m & 4u) ? TE::load(p_ + 8 * SP) : z;
-    Kd[3] = (m & 8u) ? TE::load(p_ + 12 * SP) : z;
+    const T* p_ = tab + (int)en.x;
+    const T z{};
+    Kd[0] = (m & 1u) ? __ldg(p_) : z;
+    Kd[1] = (m & 2u) ? __ldg(p_ + 4 * SP) : z;
+    Kd[2] = (m & 4u) ? __ldg(p_ + 8 * SP) : z;
+    Kd[3] = (m & 8u) ? __ldg(p_ + 12 * SP) : z;
 }
 
 // Fills the ring with the first R entries of a list.
 template <int SP, int R, class TE>
 __device__ __forceinline__ void ring_fill(const uint2* lst, const typename TE::T* __restrict__ tab,
-                                          float2 (&K)[R][4], uint32_t (&ey)[R]) {
+                                          typename TE::T (&K)[R][4], uint32_t (&ey)[R]) {
 #pragma unroll
     for (int d = 0; d < R; ++d) {
         const uint2 en = lst[d];
@@ -241,13 +244,13 @@ __device__ __forceinline__ void ring_fill(const uint2* lst, const typename TE::T
 template <int NPOL, int SP, int R, class TE>
 __device__ __forceinline__ void ring_pass(const uint2* next, const float2 (*vs)[NPOL],
                                           const typename TE::T* __restrict__ tab,
-                                          float2 (&K)[R][4], uint32_t (&ey)[R],
+                                          typename TE::T (&K)[R][4], uint32_t (&ey)[R],
                                           float2 (&acc)[4][NPOL]) {
 #pragma unroll
     for (int d = 0; d < R; ++d) {
         float2 A[NPOL], Bv[NPOL];
         load_v<NPOL>(A, Bv, vs, ey[d]);
-        slot_fma<NPOL, 0, 3>(acc, K[d], A, Bv);
+        slot_fma<NPOL, 0, 3, TE>(acc, K[d], A, Bv);
         const uint2 en = next[d];
         ey[d] = en.y;
         load_masked<SP, TE>(tab, en, K[d]);
@@ -426,14 +429,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int p = 0; p < NPOL; ++p) acc[j][p] = make_float2(0.f, 0.f);
-    // kernel-value ring; finite values only (zero, then table values), so the
-    // null entries' zero visibility row contributes exact zeros
-    float2 K[R][4];
+    // kernel-value ring, in the table's storage kind; finite values only
+    // (zero, then table values), so the null entries' zero visibility row
+    // contributes exact zeros
+    typename TE::T K[R][4];
     uint32_t ey[R];
 #pragma unroll
     for (int d = 0; d < R; ++d)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) K[d][j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; ++j) K[d][j] = typename TE::T{};
 
     // The ring runs across batches: the last pass over a batch's list loads
     // the first R entries of the next batch, so no batch starts with an empty

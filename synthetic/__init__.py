@@ -158,13 +158,15 @@ def w_extent(uvw_m: np.ndarray, freq_hz: np.ndarray) -> float:
 # --------------------------------------------------------------------------
 
 def _observation(name, enu, n_times, freq, npol, grid_n, s_min, s_max, beta, n_w,
-                 rng, row_subsample=None, dec_deg=-30.0, lat_deg=-30.0):
+                 rng, row_subsample=None, dec_deg=-30.0, lat_deg=-30.0, with_vis=True):
     uvw = uvw_tracks(baselines(enu), n_times, dec_deg=dec_deg, lat_deg=lat_deg)
     cell = fit_cell(uvw, freq, grid_n, s_max)
     wmax = w_extent(uvw, freq) if n_w > 1 else 0.0
     if row_subsample is not None:
         uvw = uvw[row_subsample]
-    vis = cn_vis(uvw.shape[0], freq.shape[0], npol, rng)
+    # without visibilities (vis None) a caller draws its own CN(0, 1) values,
+    # e.g. on the device for a large timing workload
+    vis = cn_vis(uvw.shape[0], freq.shape[0], npol, rng) if with_vis else None
     return Observation(name=name, uvw_m=uvw, freq_hz=freq, vis=vis, grid_n=grid_n,
                        cell_rad=cell, support_min=s_min, support_max=s_max,
                        oversample=beta, n_wplanes=n_w, w_max_lambda=wmax, npol=npol)
@@ -199,14 +201,14 @@ def config_autograd(seed_offset: int = 0, n_times: int = 516) -> Observation:
 
 
 def config_precision(seed_offset: int = 0, n_times: int = 512, n_chan: int = 8,
-                     row_subsample=None) -> Observation:
+                     row_subsample=None, with_vis: bool = True) -> Observation:
     """Mixed precision at scale: 256 antennas spiral+core over 20 km, 512 times x
     8 channels, 4 pols; 8192^2 x 4 grid, 128 w-planes, support 7->127."""
     rng = np.random.default_rng(BASE_SEED + 4 + seed_offset)
     enu = antennas_spiral_core(256, 20000.0, rng)
     freq = np.linspace(120e6, 180e6, n_chan)
     return _observation("precision-8192-P128-S7to127-4pol", enu, n_times, freq, 4, 8192, 7,
-                        127, 8, 128, rng, row_subsample=row_subsample)
+                        127, 8, 128, rng, row_subsample=row_subsample, with_vis=with_vis)
 
 
 def small_case(n_ant: int = 8, n_times: int = 12, n_chan: int = 3, npol: int = 4,
