@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 4
+#define GW_API_VERSION 5
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -132,6 +132,10 @@ typedef struct {
                                0 = 1024, else 64 .. 2^20 (smaller items spread small
                                jobs over more SMs, larger ones commit less often) */
     int32_t degrid_kernel;  /* 0 = automatic, 1 = shared-memory staged, 2 = global gather */
+    int32_t grid_kernel;    /* gw_grid_vis / _compensated: 0 = automatic (direct for chunks of
+                               at most 16,384 visibilities and 2^22 tap updates, else
+                               binned), 1 = binned register-tile gridder, 2 = direct
+                               (one global atomic per tap and polarisation, no bins) */
 } gw_tuning;
 
 /* ------------------------------------------------------------------------

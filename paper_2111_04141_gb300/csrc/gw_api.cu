@@ -246,6 +246,7 @@ void plan_free(gw_plan p) {
     dev_free(p->sc.item_off);
     dev_free(p->sc.entries);
     dev_free(p->sc.items);
+    dev_free(p->sc.scan_tmp);
     dev_free(p->sc.counters);
     dev_free(p->sc.dropped);
     delete p;
@@ -309,6 +310,8 @@ gw_status alloc_scratch(gw_plan p) {
     GW_ALLOC(sc.item_off, (size_t)p->ntiles + 1);
     GW_ALLOC(sc.entries, (size_t)sc.entries_cap);
     GW_ALLOC(sc.items, (size_t)sc.items_cap);
+    GW_ALLOC(sc.scan_tmp, (size_t)scan_tmp_words(p->ntiles));
+    sc.scan_tmp_bins = p->ntiles;
     GW_ALLOC(sc.counters, 4);
     GW_ALLOC(sc.dropped, 1);
     GW_ALLOC(sc.work, 2);
@@ -675,6 +678,8 @@ gw_status gw_plan_set_tuning(gw_plan p, const gw_tuning* t) {
         return fail(GW_EINVAL, "item_max must be 0 or in [%d, 2^20]", kItemMin);
     if (t->degrid_kernel < 0 || t->degrid_kernel > 2)
         return fail(GW_EINVAL, "degrid_kernel must be 0 (auto), 1 (staged) or 2 (gather)");
+    if (t->grid_kernel < 0 || t->grid_kernel > 2)
+        return fail(GW_EINVAL, "grid_kernel must be 0 (auto), 1 (binned) or 2 (direct)");
     p->tuning = *t;
     apply_tuning(p);
     return GW_OK;
@@ -738,6 +743,15 @@ gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
     return GW_OK;
 }
 
+// Direct (unbinned) gridding of a chunk of nvis visibilities: forced by the
+// tuning, or automatic for inputs small enough that launches dominate.
+static bool use_direct(gw_plan p, int64_t nvis) {
+    if (p->tuning.grid_kernel == 1) return false;
+    if (p->tuning.grid_kernel == 2) return true;
+    const int64_t smax = p->support.empty() ? 1 : p->support.back();
+    return nvis <= kDirectMaxVis && nvis * smax * smax * p->desc.npol <= kDirectMaxTaps;
+}
+
 static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz, int64_t nrow,
                            int32_t nchan, const void* vis, const float* weight, void* grid,
                            void* grid_err, int64_t* n_dropped, void* cuda_stream,
@@ -763,6 +777,36 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
     for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
         const int64_t nr = std::min(rpc, nrow - r0);
         const int64_t v0 = r0 * nchan;
+        if (use_direct(p, nr * nchan)) {
+            // small input: index, then direct gridding (weights applied in the kernel)
+            {
+                StageTimer t(p, kStIndex, s);
+                launch_index(uvw_m + 3 * r0, freq_hz, nr, nchan, p->ip, p->sc.rec, p->sc.dropped,
+                             s);
+            }
+            GridArgs a;
+            a.rec = p->sc.rec;
+            a.vis = static_cast<const char*>(vis) + (size_t)v0 * npol * vb;
+            a.vis_kind = vk;
+            a.weight = weight ? weight + v0 * npol : nullptr;
+            a.table_kind = p->desc.table_dtype;
+            a.table_inv = p->table_inv;
+            a.plane_off = p->d_plane_off;
+            a.support = p->d_support;
+            a.grid = reinterpret_cast<float2*>(grid);
+            a.grid_err = reinterpret_cast<float2*>(grid_err);
+            a.N = p->desc.grid_n;
+            a.npol = npol;
+            a.beta = p->desc.oversample;
+            {
+                StageTimer t(p, kStGrid, s);
+                launch_grid_direct(a, p->table16 ? (const void*)p->table16 : (const void*)p->table,
+                                   nr * nchan, p->sc.work, s);
+            }
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "grid launch");
+            continue;
+        }
         st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, p->geom_grid, s);
         if (st != GW_OK) return st;
         GridArgs a;

@@ -117,6 +117,107 @@ __global__ void k_scan(const uint32_t* __restrict__ count, int n, int item_max,
     }
 }
 
+// Segmented scans for many bins: segments of kScanSeg bins, one CTA each.
+// Pass 0 writes each segment's totals (bins and work items); k_scan_top scans
+// the totals in one CTA; pass 1 writes offsets, item offsets and zeroed
+// cursors with the segment's base.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanSeg = kScanThreads * kScanPer;
+constexpr int kScanSingleMax = 65536;
+
+__device__ __forceinline__ void block_excl_scan2(uint32_t& a, uint32_t& b, uint32_t* sa,
+                                                 uint32_t* sb) {
+    // exclusive scan of (a, b) over the CTA (kScanThreads threads)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t ia = a, ib = b;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t xa = __shfl_up_sync(0xffffffffu, ia, d);
+        const uint32_t xb = __shfl_up_sync(0xffffffffu, ib, d);
+        if (lane >= d) { ia += xa; ib += xb; }
+    }
+    if (lane == 31) { sa[warp] = ia; sb[warp] = ib; }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wa = sa[lane], wb = sb[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t xa = __shfl_up_sync(0xffffffffu, wa, d);
+            const uint32_t xb = __shfl_up_sync(0xffffffffu, wb, d);
+            if (lane >= d) { wa += xa; wb += xb; }
+        }
+        sa[lane] = wa;
+        sb[lane] = wb;
+    }
+    __syncthreads();
+    const uint32_t ba = warp ? sa[warp - 1] : 0u, bb = warp ? sb[warp - 1] : 0u;
+    a = ba + ia - a;
+    b = bb + ib - b;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_seg(
+    const uint32_t* __restrict__ count, int n, int item_max, int pass,
+    uint32_t* __restrict__ seg_tot, uint32_t* __restrict__ offsets,
+    uint32_t* __restrict__ item_off, uint32_t* __restrict__ cursor) {
+    __shared__ uint32_t sa[32], sb[32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanSeg + (int64_t)threadIdx.x * kScanPer;
+    uint32_t c[kScanPer];
+    uint32_t ta = 0, tb = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        c[k] = i0 + k < n ? count[i0 + k] : 0u;
+        ta += c[k];
+        tb += (c[k] + item_max - 1) / item_max;
+    }
+    uint32_t ea = ta, eb = tb;
+    block_excl_scan2(ea, eb, sa, sb);
+    if (pass == 0) {
+        if (threadIdx.x == kScanThreads - 1) {
+            seg_tot[2 * blockIdx.x] = ea + ta;
+            seg_tot[2 * blockIdx.x + 1] = eb + tb;
+        }
+        return;
+    }
+    uint32_t ra = seg_tot[2 * blockIdx.x] + ea, rb = seg_tot[2 * blockIdx.x + 1] + eb;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (i0 + k < n) {
+            offsets[i0 + k] = ra;
+            item_off[i0 + k] = rb;
+            cursor[i0 + k] = 0;
+        }
+        ra += c[k];
+        rb += (c[k] + item_max - 1) / item_max;
+    }
+}
+
+// Exclusive scan of the segment totals in place (one CTA, nseg <= 32 * 1024);
+// writes the grand totals to offsets[n] and item_off[n].
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* __restrict__ seg_tot, int nseg,
+                                                           int n, uint32_t* __restrict__ offsets,
+                                                           uint32_t* __restrict__ item_off) {
+    __shared__ uint32_t sa[32], sb[32];
+    const int per = (nseg + kScanThreads - 1) / kScanThreads;
+    const int lo = min(nseg, (int)threadIdx.x * per), hi = min(nseg, lo + per);
+    uint32_t ta = 0, tb = 0;
+    for (int i = lo; i < hi; ++i) {
+        ta += seg_tot[2 * i];
+        tb += seg_tot[2 * i + 1];
+    }
+    uint32_t ea = ta, eb = tb;
+    block_excl_scan2(ea, eb, sa, sb);
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t xa = seg_tot[2 * i], xb = seg_tot[2 * i + 1];
+        seg_tot[2 * i] = ea;
+        seg_tot[2 * i + 1] = eb;
+        ea += xa;
+        eb += xb;
+    }
+    if (threadIdx.x == kScanThreads - 1) {
+        offsets[n] = ea;
+        item_off[n] = eb;
+    }
+}
+
 __global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, DevCount dc,
                           BinGeom g, int P, int smin, int smax,
                           const uint32_t* __restrict__ offsets, uint32_t* __restrict__ cursor,
@@ -271,8 +372,20 @@ void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, 
                                                          sc.work);
         note_launch();
     }
-    k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, g.item_max, sc.offsets, sc.item_off, sc.cursor);
-    note_launch();
+    // one CTA scans up to 64 bins per thread quickly; beyond that, segments
+    if (ntiles <= kScanSingleMax || !sc.scan_tmp || ntiles > sc.scan_tmp_bins) {
+        k_scan<<<1, 1024, 0, s>>>(sc.count, ntiles, g.item_max, sc.offsets, sc.item_off,
+                                  sc.cursor);
+        note_launch();
+    } else {
+        const int nseg = (ntiles + kScanSeg - 1) / kScanSeg;
+        k_scan_seg<<<nseg, kScanThreads, 0, s>>>(sc.count, ntiles, g.item_max, 0, sc.scan_tmp,
+                                                 sc.offsets, sc.item_off, sc.cursor);
+        k_scan_top<<<1, kScanThreads, 0, s>>>(sc.scan_tmp, nseg, ntiles, sc.offsets, sc.item_off);
+        k_scan_seg<<<nseg, kScanThreads, 0, s>>>(sc.count, ntiles, g.item_max, 1, sc.scan_tmp,
+                                                 sc.offsets, sc.item_off, sc.cursor);
+        note_launch(3);
+    }
     if (nvis > 0) {
         if (sm_blocks > 0)
             k_scatter_sm<<<sm_blocks, kBinSmThreads, hsm, s>>>(rec, nvis, dc, g, P, smin, smax,
@@ -298,7 +411,11 @@ cudaError_t preload_bin_kernels() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scatter);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scatter_sm);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_items);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scan_seg);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, k_scan_top);
     return e;
 }
+
+int64_t scan_tmp_words(int64_t ntiles) { return 2 * ((ntiles + kScanSeg - 1) / kScanSeg) + 2; }
 
 }  // namespace gw

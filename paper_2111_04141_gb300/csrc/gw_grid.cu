@@ -39,7 +39,115 @@ __global__ void k_weight_vis(const void* __restrict__ vis, int kind, const float
     }
 }
 
+// Direct gridding for small inputs: no binning, one warp per record, lanes
+// over the flattened S x S taps of its (unpadded) kernel slice, one global
+// vector atomic per tap and polarisation.  Two launches per call (index and
+// this) instead of the binned path's six, which is what small jobs pay for.
+// Also accumulates the work counters the binner would (valid records, sum
+// of S^2).
+template <int NPOL, int TK>
+__global__ void __launch_bounds__(256) k_grid_direct(GridArgs a, const void* __restrict__ table,
+                                                     int64_t nvis,
+                                                     unsigned long long* __restrict__ work) {
+    using TE = TabElem<TK>;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int hb = a.beta / 2, N = a.N;
+    unsigned long long n_valid = 0, n_taps = 0;
+    for (int64_t i = warp0; i < nvis; i += nwarps) {
+        int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + i);
+        const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
+        if (!(rc.flags & GW_FLAG_VALID)) continue;
+        const int plane = a.layer_tiles ? 0 : rc.plane;
+        const int S = __ldg(a.support + plane), h = S >> 1;
+        if (lane == 0) {
+            ++n_valid;
+            n_taps += (unsigned long long)(S * S);
+        }
+        const typename TE::T* K = reinterpret_cast<const typename TE::T*>(table) +
+                                  __ldg(a.plane_off + plane) +
+                                  ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+        const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
+        float2 V[NPOL];
+#pragma unroll
+        for (int p = 0; p < NPOL; ++p) {
+            V[p] = load_vis(a.vis, a.vis_kind, i * NPOL + p);
+            if (a.weight) {
+                const float w = __ldg(a.weight + i * NPOL + p);
+                V[p].x *= w;
+                V[p].y *= w;
+            }
+        }
+        float2* const gbase = a.grid + (a.layer_tiles ? (int64_t)rc.plane * a.layer_stride : 0);
+        for (int t = lane; t < S * S; t += 32) {
+            const int tv = t / S, tu = t - tv * S;
+            const float2 k = TE::load(K + t);
+            const float kr = k.x * a.table_inv, ki = sg * k.y * a.table_inv;
+            const int64_t pix = (int64_t)(rc.kv - h + tv) * N + (rc.ku - h + tu);
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) {
+                const float2 val = make_float2(kr * V[p].x - ki * V[p].y, kr * V[p].y + ki * V[p].x);
+                const int64_t off = (int64_t)p * N * N + pix;
+                if (a.grid_err) {
+                    const float2 old = atomicAdd(gbase + off, val);
+                    // compensated commit, as in the binned kernel
+                    float2 e;
+                    {
+                        const float s_ = __fadd_rn(old.x, val.x);
+                        const float bv = __fsub_rn(s_, old.x);
+                        const float av = __fsub_rn(s_, bv);
+                        e.x = __fadd_rn(__fsub_rn(old.x, av), __fsub_rn(val.x, bv));
+                    }
+                    {
+                        const float s_ = __fadd_rn(old.y, val.y);
+                        const float bv = __fsub_rn(s_, old.y);
+                        const float av = __fsub_rn(s_, bv);
+                        e.y = __fadd_rn(__fsub_rn(old.y, av), __fsub_rn(val.y, bv));
+                    }
+                    if (e.x != 0.f || e.y != 0.f) atomicAdd(a.grid_err + off, e);
+                } else {
+                    atomicAdd(gbase + off, val);
+                }
+            }
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        n_valid += __shfl_down_sync(0xffffffffu, n_valid, d);
+        n_taps += __shfl_down_sync(0xffffffffu, n_taps, d);
+    }
+    if (lane == 0 && n_valid) {
+        atomicAdd(work, n_valid);
+        atomicAdd(work + 1, n_taps);
+    }
+}
+
+template <int TK>
+void launch_direct_k(const GridArgs& a, const void* table, int64_t nvis,
+                     unsigned long long* work, cudaStream_t s) {
+    int64_t blocks = (nvis * 32 + 255) / 256;
+    if (blocks > current_sm_count() * 8) blocks = current_sm_count() * 8;
+    if (blocks < 1) blocks = 1;
+    switch (a.npol) {
+        case 1: k_grid_direct<1, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
+        case 2: k_grid_direct<2, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
+        case 3: k_grid_direct<3, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
+        default: k_grid_direct<4, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
+    }
+    note_launch();
+}
+
 }  // namespace
+
+void launch_grid_direct(const GridArgs& a, const void* table, int64_t nvis,
+                        unsigned long long* work, cudaStream_t s) {
+    if (nvis <= 0) return;
+    switch (a.table_kind) {
+        case GW_BF16X2: launch_direct_k<GW_BF16X2>(a, table, nvis, work, s); break;
+        case GW_F16X2: launch_direct_k<GW_F16X2>(a, table, nvis, work, s); break;
+        default: launch_direct_k<GW_C64>(a, table, nvis, work, s); break;
+    }
+}
 
 void launch_weight_vis(const void* vis, int kind, const float* w, int64_t n, float2* out,
                        cudaStream_t s) {

@@ -119,6 +119,9 @@ struct Scratch {
     unsigned long long* dropped = nullptr;  // [1]
     unsigned long long* work = nullptr;     // [2]: valid visibilities, sum of S_p^2
     float2* wvis = nullptr;                 // [chunk * npol] weighted visibilities (lazy)
+    uint32_t* scan_tmp = nullptr;           // [scan_tmp_words(scan_tmp_bins)] segment totals,
+                                            // or null (single-CTA scan)
+    int64_t scan_tmp_bins = 0;              // bins scan_tmp is sized for
     int64_t entries_cap = 0;
     int64_t items_cap = 0;
 };
@@ -167,6 +170,8 @@ struct BinGeom {
     int layer_tiles = 0;   // > 0: tile id += record.plane * layer_tiles (w-stacking layers)
     int nlayers = 1;       // layers binned when layer_tiles > 0 (ntu * ntv * nlayers tiles)
 };
+// Words of Scratch::scan_tmp for a multi-CTA scan over ntiles bins.
+int64_t scan_tmp_words(int64_t ntiles);
 // Also accumulates sc.work[0] += valid records, sc.work[1] += sum of S_p^2.
 // Work items are written only when sc.items is non-null.
 void launch_bin(const gw_index_rec* rec, int64_t nvis, const BinGeom& g, int P, int smin, int smax,
@@ -225,6 +230,15 @@ struct GridArgs {
     int64_t layer_stride = 0;
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
+// Direct gridding of nvis index records (no bins): `table` is the unpadded
+// table of kind a.table_kind; adds to work[0] (valid records) and work[1]
+// (sum of S_p^2).  For inputs small enough that launches dominate.
+void launch_grid_direct(const GridArgs& a, const void* table, int64_t nvis,
+                        unsigned long long* work, cudaStream_t s);
+// Direct gridding is chosen for at most this many visibilities per chunk and
+// this many tap updates (visibilities x S_max^2 x npol).
+constexpr int64_t kDirectMaxVis = 16384;
+constexpr int64_t kDirectMaxTaps = (int64_t)1 << 22;
 // One instantiation set per table kind (gw_grid_c64.cu, gw_grid_bf16.cu, gw_grid_f16.cu).
 void launch_grid_c64(const GridArgs& a, int num_sms, cudaStream_t s);
 void launch_grid_bf16(const GridArgs& a, int num_sms, cudaStream_t s);

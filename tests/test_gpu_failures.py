@@ -86,6 +86,7 @@ def test_lazy_scratch_fails_cleanly_and_the_plan_stays_usable():
         fresh.close()
         tol = 1e-6 * float(ref.abs().max())
 
+        plan.set_tuning(grid_kernel=1)      # binned: weighted scratch allocated on first use
         n, g = _sweep(P, lambda: plan.grid(uvw, freq, vis, weight=wt))
         assert n == 1 and float((g - ref_w).abs().max()) <= tol
         pin_uvw = torch.from_numpy(obs.uvw_m).pin_memory()

@@ -183,15 +183,46 @@ def test_bins(gw, case, mode):
         assert sorted(ent[offs[t]:offs[t + 1]].tolist()) == want[t]
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_bins_many_tiles(gw, mode):
+    """More bins than one CTA scans (65536): the multi-CTA scan path.
+    A 16384^2 grid has 512^2 = 262144 tiles of 32 x 32."""
+    # 2-D (no w-term): at this grid size a w-projection field of view of a
+    # small array would reach the horizon
+    obs = syn.small_case(n_ant=12, n_times=20, n_chan=4, npol=1, grid_n=16384, s_min=15,
+                         s_max=15, n_w=1, diameter_m=4000.0, seed=21)
+    prm = Params(**obs.plan_kwargs())
+    ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
+    S = plane_support(prm)
+    ntu = 16384 // 32
+    counts = np.zeros(ntu * ntu, dtype=np.int64)
+    for i in np.nonzero(ref["valid"])[0]:
+        h = int(S[ref["plane"][i]]) // 2
+        ku, kv = int(ref["ku"][i]), int(ref["kv"][i])
+        if mode == 1:
+            counts[(kv // 32) * ntu + ku // 32] += 1
+            continue
+        for tv in range((kv - h) // 32, (kv + h) // 32 + 1):
+            for tu in range((ku - h) // 32, (ku + h) // 32 + 1):
+                counts[tv * ntu + tu] += 1
+    with gw.Plan.from_observation(obs) as plan:
+        offs, ent = plan.debug_bins(dev(obs.uvw_m), dev(obs.freq_hz), mode=mode)
+    assert offs[0] == 0
+    assert np.array_equal(np.diff(offs), counts)
+    assert int(offs[-1]) == int(counts.sum()) == len(ent)
+
+
 # ---------------------------------------------------------------------------
 # gridding / degridding
 # ---------------------------------------------------------------------------
 
-def test_grid_matches_oracle(gw, case):
+@pytest.mark.parametrize("kernel", [1, 2], ids=["binned", "direct"])
+def test_grid_matches_oracle(gw, case, kernel):
     name, obs, prm = case
     orc = oracle_for(prm)
     ref = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis)
     with gw.Plan.from_observation(obs) as plan:
+        plan.set_tuning(grid_kernel=kernel)
         g, dropped = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis),
                                return_dropped=True)
     got = g.cpu().numpy().astype(np.complex128)
@@ -199,7 +230,8 @@ def test_grid_matches_oracle(gw, case):
     assert dropped == int((~orc.index(obs.uvw_m, obs.freq_hz)["valid"]).sum())
 
 
-def test_grid_weights_accumulate_and_chunks(gw):
+@pytest.mark.parametrize("kernel", [1, 2], ids=["binned", "direct"])
+def test_grid_weights_accumulate_and_chunks(gw, kernel):
     obs = CASES["small-w"]()
     prm = Params(**obs.plan_kwargs())
     orc = oracle_for(prm)
@@ -207,6 +239,7 @@ def test_grid_weights_accumulate_and_chunks(gw):
     ref = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis, weight=wt)
     # a small chunk size forces several internal chunks with a ragged last one
     with gw.Plan.from_observation(obs, max_vis_per_call=37 * obs.nchan + 1) as plan:
+        plan.set_tuning(grid_kernel=kernel)
         g = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis), weight=dev(wt))
         got = g.cpu().numpy().astype(np.complex128)
         assert rel_l2(got, ref) <= TOL_GRID
@@ -214,9 +247,11 @@ def test_grid_weights_accumulate_and_chunks(gw):
         assert rel_l2(g.cpu().numpy().astype(np.complex128), 2 * ref) <= TOL_GRID
 
 
-def test_grid_empty_and_all_dropped(gw):
+@pytest.mark.parametrize("kernel", [1, 2], ids=["binned", "direct"])
+def test_grid_empty_and_all_dropped(gw, kernel):
     obs = CASES["small-w"]()
     with gw.Plan.from_observation(obs) as plan:
+        plan.set_tuning(grid_kernel=kernel)
         e3 = torch.zeros((0, 3), dtype=torch.float64, device=DEV)
         f = dev(obs.freq_hz)
         v = torch.zeros((0, obs.nchan, obs.npol), dtype=torch.complex64, device=DEV)

@@ -126,14 +126,16 @@ def test_stored_tables_are_the_rounded_fp64_tables(gw, kind):
 COMBOS = [("bf16", "bf16"), ("f16", "f16"), ("bf16", "c64"), ("c64", "bf16"), ("f16", "c64")]
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["binned", "direct"])
 @pytest.mark.parametrize("table_kind,vis_kind", COMBOS)
-def test_grid_16bit_parity_and_storage_error(gw, table_kind, vis_kind):
+def test_grid_16bit_parity_and_storage_error(gw, table_kind, vis_kind, kernel):
     obs = small()
     prm = Params(**obs.plan_kwargs())
     vt, held = stored_vis(gw, obs.vis, vis_kind)
     ref_q = oracle(prm, table_kind).grid(obs.uvw_m, obs.freq_hz, held)
     exact = Oracle(prm, tables_for(prm)).grid(obs.uvw_m, obs.freq_hz, obs.vis)
     with gw.Plan.from_observation(obs, table_dtype=table_kind, vis_dtype=vis_kind) as plan:
+        plan.set_tuning(grid_kernel=kernel)
         g = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), vt)
     got = g.cpu().numpy().astype(np.complex128)
     parity = rel_l2(got, ref_q)
@@ -194,11 +196,13 @@ def test_16bit_vis_with_weights(gw):
 # compensated commits
 # ---------------------------------------------------------------------------
 
-def test_compensated_grid_matches_oracle(gw):
+@pytest.mark.parametrize("kernel", [1, 2], ids=["binned", "direct"])
+def test_compensated_grid_matches_oracle(gw, kernel):
     obs = small()
     prm = Params(**obs.plan_kwargs())
     exact = Oracle(prm, tables_for(prm)).grid(obs.uvw_m, obs.freq_hz, obs.vis)
     with gw.Plan.from_observation(obs, max_vis_per_call=29 * obs.nchan) as plan:
+        plan.set_tuning(grid_kernel=kernel)
         g = plan.new_grid()
         e = plan.new_grid()
         plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis), out=g, err=e)
@@ -224,6 +228,7 @@ def test_compensated_commits_recover_the_exact_sum(gw):
     vis = (rng.normal(size=(uu.size, 1, 1)) + 1j * rng.normal(size=(uu.size, 1, 1)))
     vis = vis.astype(np.complex64)
     with gw.Plan(**prm) as plan:
+        plan.set_tuning(grid_kernel=1)      # the binned kernel's per-item commits
         u, f, v = dev(uvw), dev(freq), dev(vis)
         one = plan.grid(u, f, v).cpu().numpy().astype(np.complex128)
         plain = plan.new_grid()
