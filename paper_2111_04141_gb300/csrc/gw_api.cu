@@ -457,7 +457,8 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 
     const int N = desc->grid_n, P = desc->n_wplanes, beta = desc->oversample;
     p->field = (double)N * desc->cell_rad;
-    p->geom_grid = BinGeom{0, 5, 5, (N + kGridTileU - 1) / kGridTileU, (N + kGridTileV - 1) / kGridTileV};
+    p->geom_grid = BinGeom{0, kGridTileShiftU, 5, (N + kGridTileU - 1) / kGridTileU,
+                           (N + kGridTileV - 1) / kGridTileV};
     p->geom_degrid = BinGeom{1, 5, 5, (N + kTile - 1) / kTile, (N + kTile - 1) / kTile};
     {
         const int st = degrid_staged_tile();

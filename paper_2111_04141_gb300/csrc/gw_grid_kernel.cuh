@@ -7,19 +7,20 @@
 //     G[pol][kv + tv][ku + tu] += K_p[ov][ou](tv, tu) * V[pol]   (conj K if w < 0)
 //
 // Design (GB300):
-// * A CTA (one per SM) owns one 32 x 32 tile of the grid for a work item (a
-//   run of that tile's bin) and keeps the tile's accumulators in registers,
-//   so each grid point is committed once per work item (vector atomics,
-//   red.global).
-// * Eight compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv) holds
-//   the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for every
-//   polarisation.  Four slots per warp amortise each record's staged
+// * A CTA (one per SM) owns one 64 (u) x 32 (v) tile of the grid for a work
+//   item (a run of that tile's bin) and keeps the tile's accumulators in
+//   registers, so each grid point is committed once per work item (vector
+//   atomics, red.global).
+// * Sixteen compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv)
+//   holds the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for
+//   every polarisation.  Four slots per warp amortise each record's staged
 //   visibility over up to 4 x 32 points.
 // * The work is bound by the gathers of kernel values from L2 (each a
-//   4-row x 64-byte window of a table slice per slot), so the design keeps
-//   many of them in flight: one CTA of 12 warps per SM leaves 168 registers
-//   per thread, and each compute warp keeps the kernel values of the next R
-//   list entries in a ring of registers.
+//   4-row x 64-byte window of a table slice per slot) and by the FP32 pipe,
+//   so the design keeps many gathers in flight and many warps issuing: 20
+//   warps per SM (4 compute warps and one producer warp per scheduler, 96
+//   registers per thread), each compute warp holding the kernel values of
+//   the next R = 3 list entries in a ring of registers.
 // * Four producer warps (one warpgroup) stage batches of 256 records into
 //   shared memory: the record ids and index records are loaded for all rows
 //   at once, the visibilities are copied straight into shared memory with
@@ -62,8 +63,12 @@ namespace gw {
 
 namespace {
 
-constexpr int kComputeWarps = 8;
-constexpr int kProducerWarps = 4;
+constexpr int kBlocksU = kGridTileU / 8;                 // 8 (u) x 16 (v) blocks per tile row
+constexpr int kComputeWarps = kBlocksU * (kGridTileV / 16);
+#ifndef GW_GRID_PRODUCER_WARPS
+#define GW_GRID_PRODUCER_WARPS 4
+#endif
+constexpr int kProducerWarps = GW_GRID_PRODUCER_WARPS;
 constexpr int kProducerThreads = kProducerWarps * 32;
 constexpr int kThreads = (kComputeWarps + kProducerWarps) * 32;
 constexpr int kBatch = 256;
@@ -278,6 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     __syncthreads();
 
     if (warp >= kComputeWarps) {
+#ifdef GW_GRID_SETMAXNREG
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 40;" ::: "memory");
+#endif
         // ----------------------------------------------------------- producers
         const int pt = threadIdx.x - kComputeWarps * 32;   // 0 .. kProducerThreads - 1
         const int pw = pt >> 5;
@@ -315,8 +323,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                 if (!done) {
                     // with w-layers (w-stacking) a tile id is layer * layer_tiles + tile
                     const int ltile = a.layer_tiles ? item.tile % a.layer_tiles : item.tile;
-                    const int tu0 = (ltile % side) * kTile;
-                    const int tv0 = (ltile / side) * kTile;
+                    const int tu0 = (ltile % side) * kGridTileU;
+                    const int tv0 = (ltile / side) * kGridTileV;
                     const int b0 = b * kBatch;
                     const int nb = min(kBatch, item.len - b0);
                     // all ids, then all index records of this thread's rows in flight
@@ -374,8 +382,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                         // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
                         const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
                         const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
-                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kTile - 1, uhi) >> 3;
-                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kTile - 1, vhi) >> 4;
+                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kGridTileU - 1, uhi) >> 3;
+                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kGridTileV - 1, vhi) >> 4;
                         for (int cv = cv0; cv <= cv1; ++cv) {
                             const int j0 = max(0, vlo - 16 * cv) >> 2;
                             const int j1 = min(15, vhi - 16 * cv) >> 2;
@@ -383,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                             const uint2 e = make_uint2((uint32_t)base,
                                                        (uint32_t)r | (mask << 20) | conj);
                             for (int cu = cu0; cu <= cu1; ++cu) {
-                                const int w = cv * 4 + cu;
+                                const int w = cv * kBlocksU + cu;
                                 const int pos = atomicAdd(&sm.cnt[buf][w], 1);
                                 sm.list[buf][w][pos] = e;
                             }
@@ -419,7 +427,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
     }
 
     // ---------------------------------------------------------------- consumers
-    const int bu = (warp & 3) * 8, bv = (warp >> 2) * 16;
+#ifdef GW_GRID_SETMAXNREG
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(GW_GRID_SETMAXNREG) : "memory");
+#endif
+    const int bu = (warp % kBlocksU) * 8, bv = (warp / kBlocksU) * 16;
     const int lu = lane & 7, lv = lane >> 3;
     const typename TE::T* __restrict__ tab =
         reinterpret_cast<const typename TE::T*>(a.ptable) + (bv + lv) * SP + bu + lu;
@@ -478,8 +489,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
             const int ltile = a.layer_tiles ? tile % a.layer_tiles : tile;
             float2* const gbase = a.grid + (a.layer_tiles ? (int64_t)(tile / a.layer_tiles) *
                                                                  a.layer_stride : 0);
-            const int u = (ltile % a.ntiles_u) * kTile + bu + lu;
-            const int v0 = (ltile / a.ntiles_u) * kTile + bv + lv;
+            const int u = (ltile % a.ntiles_u) * kGridTileU + bu + lu;
+            const int v0 = (ltile / a.ntiles_u) * kGridTileV + bv + lv;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int v = v0 + 4 * j;
@@ -516,9 +527,11 @@ void launch_v(const GridArgs& a, int num_sms, cudaStream_t s) {
 }
 
 // GW_GRID_BUFS staging buffers of 256 records and a ring of GW_GRID_RING
-// kernel-value register sets per compute warp.
+// kernel-value register sets per compute warp (measured on the 4-pol
+// w-projection batch: 16 compute warps with ring 3 beat 8 compute warps with
+// rings of 2-10 entries at 168 registers).
 #ifndef GW_GRID_RING
-#define GW_GRID_RING 8
+#define GW_GRID_RING 3
 #endif
 #ifndef GW_GRID_BUFS
 #define GW_GRID_BUFS 4

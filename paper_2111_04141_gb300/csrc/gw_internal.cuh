@@ -15,7 +15,11 @@ namespace gw {
 
 constexpr double kC0 = 299792458.0;   // speed of light, m/s
 constexpr int kTile = 32;             // grid tile side of the degridding binner
-constexpr int kGridTileU = 32;        // gridder tile: 32 (u) x 32 (v)
+#ifndef GW_GRID_TILE_SHIFT_U
+#define GW_GRID_TILE_SHIFT_U 6
+#endif
+constexpr int kGridTileShiftU = GW_GRID_TILE_SHIFT_U;
+constexpr int kGridTileU = 1 << kGridTileShiftU;   // gridder tile: kGridTileU (u) x 32 (v)
 constexpr int kGridTileV = 32;
 constexpr int kItemMax = 1024;        // default max bin entries per work item
 constexpr int kItemMin = 64;          // smallest work-item size a plan may be tuned to

@@ -359,7 +359,8 @@ class Server:
         the extra chunk length."""
         s = self.setups[setup]
         p = self.plans[setup]
-        mt = ((s.plan_kwargs["support_max"] - 1) // 32 + 2) ** 2
+        sm1 = s.plan_kwargs["support_max"] - 1
+        mt = (sm1 // p.info.grid_tile_u + 2) * (sm1 // p.info.grid_tile_v + 2)
         per_vis = 16 + 4 * mt + 16 * mt / 64.0
         return int(p.info.scratch_bytes + (self.max_vis - p.info.chunk_vis) * per_vis)
 

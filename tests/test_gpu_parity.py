@@ -161,7 +161,9 @@ def test_tables_match_oracle(gw, case):
 def test_bins(gw, case, mode):
     name, obs, prm = case
     ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
-    tu_, tv_ = (32, 32) if mode == 0 else (32, 32)
+    with gw.Plan.from_observation(obs) as plan:
+        info = plan.info
+    tu_, tv_ = (info.grid_tile_u, info.grid_tile_v) if mode == 0 else (info.degrid_tile,) * 2
     ntu = (prm.grid_n + tu_ - 1) // tu_
     ntv = (prm.grid_n + tv_ - 1) // tv_
     S = plane_support(prm)
@@ -186,7 +188,8 @@ def test_bins(gw, case, mode):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_bins_many_tiles(gw, mode):
     """More bins than one CTA scans (65536): the multi-CTA scan path.
-    A 16384^2 grid has 512^2 = 262144 tiles of 32 x 32."""
+    A 16384^2 grid has 131072 gridder tiles of 64 x 32 and 262144 degridder
+    tiles of 32 x 32."""
     # 2-D (no w-term): at this grid size a w-projection field of view of a
     # small array would reach the horizon
     obs = syn.small_case(n_ant=12, n_times=20, n_chan=4, npol=1, grid_n=16384, s_min=15,
@@ -194,16 +197,19 @@ def test_bins_many_tiles(gw, mode):
     prm = Params(**obs.plan_kwargs())
     ref = index_vis(obs.uvw_m, obs.freq_hz, prm)
     S = plane_support(prm)
-    ntu = 16384 // 32
-    counts = np.zeros(ntu * ntu, dtype=np.int64)
+    with gw.Plan.from_observation(obs) as plan:
+        info = plan.info
+    tu_, tv_ = (info.grid_tile_u, info.grid_tile_v) if mode == 0 else (info.degrid_tile,) * 2
+    ntu, ntv = 16384 // tu_, 16384 // tv_
+    counts = np.zeros(ntu * ntv, dtype=np.int64)
     for i in np.nonzero(ref["valid"])[0]:
         h = int(S[ref["plane"][i]]) // 2
         ku, kv = int(ref["ku"][i]), int(ref["kv"][i])
         if mode == 1:
-            counts[(kv // 32) * ntu + ku // 32] += 1
+            counts[(kv // tv_) * ntu + ku // tu_] += 1
             continue
-        for tv in range((kv - h) // 32, (kv + h) // 32 + 1):
-            for tu in range((ku - h) // 32, (ku + h) // 32 + 1):
+        for tv in range((kv - h) // tv_, (kv + h) // tv_ + 1):
+            for tu in range((ku - h) // tu_, (ku + h) // tu_ + 1):
                 counts[tv * ntu + tu] += 1
     with gw.Plan.from_observation(obs) as plan:
         offs, ent = plan.debug_bins(dev(obs.uvw_m), dev(obs.freq_hz), mode=mode)
