@@ -458,6 +458,14 @@ def measure_next(gw, plan, obs, uvw, freq, vis, dev, stream, steps):
                           "ratio": obs.nvis / max(ncomp, 1),
                           "ms_per_step": timed(lambda: plan.grid_compressed(uvw, freq, vis,
                                                                             out=g))}
+    # with the sampled decision (compress only when >= 5 % of a sample merges)
+    tun = plan.get_tuning()
+    plan.set_tuning(**dict(tun, compress_min_gain=50))
+    _, ncomp2, _ = plan.grid_compressed(uvw, freq, vis, out=g)
+    out["compression"]["auto_min_gain_5pct"] = {
+        "records_gridded": ncomp2, "compressed": ncomp2 == ncomp,
+        "ms_per_step": timed(lambda: plan.grid_compressed(uvw, freq, vis, out=g))}
+    plan.set_tuning(**tun)
     kw = dict(obs.plan_kwargs())
     kw.update(support_min=7, support_max=7, n_wplanes=1, w_max_lambda=0.0)
     sz = 15

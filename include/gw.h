@@ -136,6 +136,11 @@ typedef struct {
                                at most 16,384 visibilities and 2^22 tap updates, else
                                binned), 1 = binned register-tile gridder, 2 = direct
                                (one global atomic per tap and polarisation, no bins) */
+    int32_t compress_min_gain; /* gw_grid_vis_compressed: 0 = always compress; g in
+                               1..1000 = first compress a sample (the first rows, up to
+                               2^18 visibilities; the call synchronises the stream) and grid
+                               without compression when fewer than g per mille of its valid
+                               records merge (n_gridded then counts the valid records) */
 } gw_tuning;
 
 /* ------------------------------------------------------------------------

@@ -40,7 +40,8 @@ class PlanInfo(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("item_max", c_i32), ("degrid_kernel", c_i32), ("grid_kernel", c_i32)]
+    _fields_ = [("item_max", c_i32), ("degrid_kernel", c_i32), ("grid_kernel", c_i32),
+                ("compress_min_gain", c_i32)]
 
 
 class Timing(ctypes.Structure):

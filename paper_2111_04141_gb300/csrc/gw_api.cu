@@ -681,6 +681,8 @@ gw_status gw_plan_set_tuning(gw_plan p, const gw_tuning* t) {
         return fail(GW_EINVAL, "degrid_kernel must be 0 (auto), 1 (staged) or 2 (gather)");
     if (t->grid_kernel < 0 || t->grid_kernel > 2)
         return fail(GW_EINVAL, "grid_kernel must be 0 (auto), 1 (binned) or 2 (direct)");
+    if (t->compress_min_gain < 0 || t->compress_min_gain > 1000)
+        return fail(GW_EINVAL, "compress_min_gain must be in [0, 1000] (per mille)");
     p->tuning = *t;
     apply_tuning(p);
     return GW_OK;
@@ -996,9 +998,10 @@ static gw_status ensure_compress(gw_plan p, cudaStream_t s) {
     GW_CALLOC(cs.acc, (size_t)cap * npol);
     GW_CALLOC(cs.rec, (size_t)p->chunk);
     GW_CALLOC(cs.vis, (size_t)p->chunk * npol);
-    GW_CALLOC(cs.count, 2);
+    GW_CALLOC(cs.count, 3);
 #undef GW_CALLOC
     cs.total = cs.count + 1;
+    cs.n_in = cs.count + 2;
     cs.cap = cap;
     clear_compress_table(cs, npol, s);
     return GW_OK;
@@ -1019,11 +1022,37 @@ gw_status gw_grid_vis_compressed(gw_plan p, const double* uvw_m, const double* f
     cudaStream_t s = (cudaStream_t)cuda_stream;
     st = ensure_compress(p, s);
     if (st != GW_OK) return st;
-    cudaError_t e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->cs.total, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    cudaError_t e;
     const int npol = p->desc.npol;
     const int64_t rpc = rows_per_chunk(p, nchan);
+    if (p->tuning.compress_min_gain > 0 && nrow > 0 && nchan > 0) {
+        // compress a sample (the first rows, up to 2^18 visibilities) and
+        // grid without compression when too few of its records merge
+        const int64_t sr = std::min(rpc, std::max<int64_t>(1, ((int64_t)1 << 18) / nchan));
+        const int64_t nsr = std::min(sr, nrow);
+        e = cudaMemsetAsync(p->cs.count, 0, 3 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        launch_index(uvw_m, freq_hz, nsr, nchan, p->ip, p->sc.rec, p->sc.dropped, s);
+        launch_compress(p->sc.rec, nsr * nchan, vis, vk, weight, npol, p->desc.oversample, p->cs,
+                        s);
+        unsigned long long h[3] = {0, 0, 0};
+        e = cudaMemcpyAsync(h, p->cs.count, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the compression sample");
+        const double merged = h[2] ? 1.0 - (double)h[0] / (double)h[2] : 0.0;
+        if (merged * 1000.0 < (double)p->tuning.compress_min_gain) {
+            int64_t nd = 0;
+            st = grid_impl(p, uvw_m, freq_hz, nrow, nchan, vis, weight, grid, nullptr, &nd,
+                           cuda_stream);
+            if (st != GW_OK) return st;
+            if (n_dropped) *n_dropped = nd;
+            if (n_gridded) *n_gridded = nrow * (int64_t)nchan - nd;
+            return GW_OK;
+        }
+    }
+    e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->cs.total, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     for (int64_t r0 = 0; r0 < nrow && nchan > 0; r0 += rpc) {
         const int64_t nr = std::min(rpc, nrow - r0);
         const int64_t v0 = r0 * nchan;

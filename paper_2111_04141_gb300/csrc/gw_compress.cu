@@ -50,12 +50,14 @@ __global__ void k_hash_insert(const gw_index_rec* __restrict__ rec, int64_t nvis
                               const void* __restrict__ vis, int vis_kind,
                               const float* __restrict__ weight, int npol, int hb,
                               unsigned long long* __restrict__ keys, float2* __restrict__ acc,
-                              unsigned long long mask) {
+                              unsigned long long mask, unsigned long long* __restrict__ n_in) {
+    unsigned long long mine = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis;
          i += (int64_t)gridDim.x * blockDim.x) {
         int4 rv = __ldg(reinterpret_cast<const int4*>(rec) + i);
         const gw_index_rec r = *reinterpret_cast<gw_index_rec*>(&rv);
         if (!(r.flags & GW_FLAG_VALID)) continue;
+        ++mine;
         const unsigned long long key = make_key(r, hb);
         unsigned long long h = mix64(key) & mask;
         // at most half the table is occupied, so an empty slot is found in
@@ -75,6 +77,8 @@ __global__ void k_hash_insert(const gw_index_rec* __restrict__ rec, int64_t nvis
             atomicAdd(acc + h * npol + p, v);
         }
     }
+    for (int d = 16; d > 0; d >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, d);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(n_in, mine);
 }
 
 __global__ void k_compact(unsigned long long* __restrict__ keys, float2* __restrict__ acc,
@@ -112,7 +116,8 @@ void launch_compress(const gw_index_rec* rec, int64_t nvis, const void* vis, int
     if (nvis > 0) {
         k_hash_insert<<<blocks_for(nvis), 256, 0, s>>>(rec, nvis, vis, vis_kind, weight, npol,
                                                        beta / 2, cs.keys, cs.acc,
-                                                       (unsigned long long)(cs.cap - 1));
+                                                       (unsigned long long)(cs.cap - 1),
+                                                       cs.n_in);
         note_launch();
     }
     k_compact<<<blocks_for(cs.cap), 256, 0, s>>>(cs.keys, cs.acc, cs.cap, npol, beta / 2,

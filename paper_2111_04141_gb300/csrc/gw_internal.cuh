@@ -292,6 +292,7 @@ struct CompressScratch {
     float2* vis = nullptr;                // [chunk * npol] their visibilities
     unsigned long long* count = nullptr;  // [1] compressed records of the current chunk
     unsigned long long* total = nullptr;  // [1] compressed records of the call
+    unsigned long long* n_in = nullptr;   // [1] valid records inserted (accumulates)
     int64_t cap = 0;                      // power of two >= 2 * chunk
 };
 // Adds the weighted visibilities of valid records with equal (k, o, plane,

@@ -115,11 +115,12 @@ class Plan:
         t = _lib.Tuning()
         check(self._lib.gw_plan_get_tuning(self._h, ctypes.byref(t)), "gw_plan_get_tuning")
         return {"item_max": t.item_max, "degrid_kernel": t.degrid_kernel,
-                "grid_kernel": t.grid_kernel}
+                "grid_kernel": t.grid_kernel, "compress_min_gain": t.compress_min_gain}
 
-    def set_tuning(self, item_max: int = 0, degrid_kernel: int = 0, grid_kernel: int = 0):
+    def set_tuning(self, item_max: int = 0, degrid_kernel: int = 0, grid_kernel: int = 0,
+                   compress_min_gain: int = 0):
         t = _lib.Tuning(item_max=int(item_max), degrid_kernel=int(degrid_kernel),
-                        grid_kernel=int(grid_kernel))
+                        grid_kernel=int(grid_kernel), compress_min_gain=int(compress_min_gain))
         check(self._lib.gw_plan_set_tuning(self._h, ctypes.byref(t)), "gw_plan_set_tuning")
 
     @classmethod

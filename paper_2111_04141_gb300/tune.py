@@ -52,7 +52,8 @@ def tune_plan(plan, uvw, freq, vis, grid, reps: int = 3,
             ms = _time(step, stream, reps)
             timings[f"item_max={im},degrid_kernel={dk}"] = ms
             if ms < best_ms:
-                best, best_ms = {"item_max": im, "degrid_kernel": dk, "grid_kernel": 0}, ms
+                best, best_ms = {"item_max": im, "degrid_kernel": dk, "grid_kernel": 0,
+                                  "compress_min_gain": 0}, ms
     plan.set_tuning(**best)
     return {"tuning": best, "ms": best_ms, "timings": timings}
 

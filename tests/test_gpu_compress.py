@@ -90,3 +90,32 @@ def test_compression_within_chunks(gw):
     assert n_gridded == expect == n2
     assert rel_l2(g.cpu().numpy().astype(np.complex128), ref) <= 1e-5
     assert rel_l2(g2.cpu().numpy().astype(np.complex128), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("which", ["dense", "small-w"])
+def test_compression_decision_from_a_sample(gw, which):
+    """With compress_min_gain set, the call compresses a sample first (the
+    first rows, up to 2^18 visibilities) and compresses only when at least
+    that share of its records merges; either way the grid is the same."""
+    if which == "dense":
+        obs, uvw, vis = dense_case()         # every row three times: 2/3 merge
+    else:
+        obs = syn.small_case(n_ant=7, n_times=10, n_chan=3, npol=4, grid_n=128, s_min=7,
+                             s_max=21, n_w=5, diameter_m=1500.0)
+        uvw, vis = obs.uvw_m, obs.vis
+    prm = Params(**obs.plan_kwargs())
+    orc = Oracle(prm)
+    idx = orc.index(uvw, obs.freq_hz)
+    cidx, _ = full_compression(idx, vis)
+    valid = int(idx["valid"].sum())
+    merged = 1.0 - cidx["ku"].shape[0] / valid   # the sample is the whole (small) input
+    ref = orc.grid(uvw, obs.freq_hz, vis, idx=idx)
+    gain = 500
+    with gw.Plan.from_observation(obs) as plan:
+        plan.set_tuning(compress_min_gain=gain)
+        g, n_gridded, dropped = plan.grid_compressed(dev(uvw), dev(obs.freq_hz), dev(vis))
+    expect = cidx["ku"].shape[0] if merged * 1000 >= gain else valid
+    assert (which == "dense") == (merged * 1000 >= gain)
+    assert n_gridded == expect
+    assert dropped == int((~idx["valid"]).sum())
+    assert rel_l2(g.cpu().numpy().astype(np.complex128), ref) <= 1e-5
