@@ -510,16 +510,24 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 
 #define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { plan_free(p); \
         return fail(GW_ENOMEM, "device allocation of %s failed", #x); } } while (0)
-    GW_ALLOC(p->table, (size_t)p->plane_off[P]);
+    GW_ALLOC(p->table, (size_t)(p->plane_off[P] + kTableSlack));
     if (desc->table_dtype == GW_C64) {
         float2* pt = nullptr;
         GW_ALLOC(pt, (size_t)p->pplane_off[P]);
         p->ptable = pt;
     } else {
         uint32_t* pt = nullptr;
-        GW_ALLOC(p->table16, (size_t)p->plane_off[P]);
+        GW_ALLOC(p->table16, (size_t)(p->plane_off[P] + kTableSlack));
         GW_ALLOC(pt, (size_t)p->pplane_off[P]);
         p->ptable = pt;
+    }
+    // the slack after the last slice reads as zeros
+    e = cudaMemset(p->table + p->plane_off[P], 0, sizeof(float2) * kTableSlack);
+    if (e == cudaSuccess && p->table16)
+        e = cudaMemset(p->table16 + p->plane_off[P], 0, sizeof(uint32_t) * kTableSlack);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return cuda_fail(e, "cudaMemset");
     }
     GW_ALLOC(p->d_pplane_off, (size_t)P + 1);
     GW_ALLOC(p->d_plane_off, (size_t)P + 1);
@@ -591,9 +599,9 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     t->d_support = p->d_support;
     t->d_h = p->d_h;
     t->d_hf = p->d_hf;
-    t->bytes = (int64_t)sizeof(float2) * p->plane_off[P] +
+    t->bytes = (int64_t)sizeof(float2) * (p->plane_off[P] + kTableSlack) +
                (int64_t)dtype_bytes(desc->table_dtype) * p->pplane_off[P] +
-               (p->table16 ? (int64_t)sizeof(uint32_t) * p->plane_off[P] : 0) +
+               (p->table16 ? (int64_t)sizeof(uint32_t) * (p->plane_off[P] + kTableSlack) : 0) +
                (int64_t)(2 * sizeof(int64_t) + sizeof(int)) * (P + 1) +
                (int64_t)(sizeof(double) + sizeof(float)) * N;
     p->tabs = t;
@@ -1247,9 +1255,9 @@ gw_status gw_wstack_combine(gw_plan p, const void* layer_images, int32_t n_layer
 static gw_status hybrid_checks(gw_plan p, int32_t sz) {
     if (p->desc.n_wplanes != 1) return fail(GW_EINVAL, "hybrid gridding needs a 2-D plan");
     if (sz < 1 || !(sz & 1) || sz > 127) return fail(GW_EINVAL, "sz must be odd in [1, 127]");
-    if (p->desc.grid_n % 4 != 0) return fail(GW_EINVAL, "hybrid gridding needs grid_n % 4 == 0");
+    if (p->desc.grid_n % 4 != 0) return fail(GW_EINVAL, "hybrid gridding needs grid_n %% 4 == 0");
     if (p->desc.oversample % 4 != 0)
-        return fail(GW_EINVAL, "hybrid gridding needs oversample % 4 == 0");
+        return fail(GW_EINVAL, "hybrid gridding needs oversample %% 4 == 0");
     if ((int64_t)p->desc.oversample * p->desc.grid_n >= ((int64_t)1 << 31))
         return fail(GW_EINVAL, "oversample * grid_n too large");
     return GW_OK;

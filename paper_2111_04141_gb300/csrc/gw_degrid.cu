@@ -98,79 +98,201 @@ void launch_t(const DegridArgs& a, int64_t nvis, int num_sms, cudaStream_t s) {
     note_launch();
 }
 
-constexpr int kStagedThreads = 1024;
+#ifndef GW_DEGRID_THREADS
+#define GW_DEGRID_THREADS 768
+#endif
+constexpr int kStagedThreads = GW_DEGRID_THREADS;
 constexpr int kStagedTile = 16;
+constexpr int kStagedMeta = 1024;   // records whose metadata a CTA stages at once
+constexpr int kStagedPad = 4;       // zero elements after each staged plane
+#ifndef GW_DEGRID_DEPTH
+#define GW_DEGRID_DEPTH 4
+#endif
+constexpr int kStagedDepth = GW_DEGRID_DEPTH;   // steps of kernel values loaded ahead
+
+// Work of one CTA iteration: a chunk of at most kStagedMeta records of a work
+// item (items longer than that are served in several chunks from one staged
+// region).
+struct StagedChunk {
+    Item item;
+    int c0, nc;     // first record of the chunk in the item, records in it
+    int done;
+};
 
 template <int NPOL, int TK>
 __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, int hmax) {
     using TE = TabElem<TK>;
-    extern __shared__ __align__(16) float2 reg[];          // [NPOL][RS][RS]
-    __shared__ uint32_t s_item;
+    using T = typename TE::T;
+    constexpr int D = kStagedDepth;
+    // grid region as polarisation pairs [NPOL / 2][RS][RS] of (G_p, G_p+1),
+    // then [RS][RS] of the last polarisation if NPOL is odd, then the chunk's
+    // record metadata
+    constexpr int NPR = NPOL / 2;
+    extern __shared__ __align__(16) float4 reg[];
+    __shared__ StagedChunk s_ch;
+    __shared__ int s_next, s_front, s_back;
     const int RS = kStagedTile + 2 * hmax;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = kStagedThreads / 32;
+    // each plane holds RS x RS values and kStagedPad zeros (element RS * RS
+    // is read by lanes without a tap in a record's last step); RS is even, so
+    // every part stays 16-byte aligned
+    const int plane = RS * RS + kStagedPad;
+    const int zoff = RS * RS;
+    float2* single = reinterpret_cast<float2*>(reg + (size_t)NPR * plane);
+    uint4* meta = reinterpret_cast<uint4*>(single + (NPOL % 2 ? plane : 0));
+    if (threadIdx.x < kStagedPad) {
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) reg[(size_t)q * plane + zoff + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (NPOL % 2) single[zoff + threadIdx.x] = make_float2(0.f, 0.f);
+    }
+    const int lane = threadIdx.x & 31;
     const int N = a.N, hb = a.beta / 2;
     const uint32_t nitems = *a.item_count;
+    const T* __restrict__ tab = reinterpret_cast<const T*>(a.table);
+    // thread 0: the item being served and the next chunk's first record
+    Item cur{};
+    int next_c0 = 0;
     for (;;) {
-        __syncthreads();                       // previous item fully consumed
-        if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1u);
-        __syncthreads();
-        const uint32_t it = s_item;
-        if (it >= nitems) break;
-        const Item item = a.items[it];
-        const int rx0 = (item.tile % a.ntiles_u) * kStagedTile - hmax;
-        const int ry0 = (item.tile / a.ntiles_u) * kStagedTile - hmax;
-        // stage the region, polarisations interleaved
-        for (int e = threadIdx.x; e < RS * RS; e += kStagedThreads) {
-            const int y = e / RS, x = e - y * RS;
-            const int gy = ry0 + y, gx = rx0 + x;
-            const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p)
-                reg[(size_t)p * RS * RS + e] =
-                    in ? __ldg(a.grid + ((int64_t)p * N + gy) * N + gx) : make_float2(0.f, 0.f);
+        __syncthreads();                       // previous chunk fully consumed
+        if (threadIdx.x == 0) {
+            if (next_c0 == 0 || next_c0 >= cur.len) {
+                const uint32_t it = atomicAdd(a.queue, 1u);
+                s_ch.done = it >= nitems;
+                if (it < nitems) cur = a.items[it];
+                next_c0 = 0;
+            }
+            const int nc = min(kStagedMeta, cur.len - next_c0);
+            s_ch.item = cur;
+            s_ch.c0 = next_c0;
+            s_ch.nc = nc;
+            s_next = 0;
+            s_front = 0;
+            s_back = nc;
+            next_c0 += nc;
         }
         __syncthreads();
-        for (int r = warp; r < item.len; r += nwarps) {
-            const uint32_t id = __ldg(a.entries + item.start + r);
+        if (s_ch.done) break;
+        const Item item = s_ch.item;
+        const int c0 = s_ch.c0, nc = s_ch.nc;
+        const int rx0 = (item.tile % a.ntiles_u) * kStagedTile - hmax;
+        const int ry0 = (item.tile / a.ntiles_u) * kStagedTile - hmax;
+        if (c0 == 0) {
+            // stage the region
+            for (int e = threadIdx.x; e < zoff; e += kStagedThreads) {
+                const int y = e / RS, x = e - y * RS;
+                const int gy = ry0 + y, gx = rx0 + x;
+                const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+                float2 g[NPOL];
+#pragma unroll
+                for (int p = 0; p < NPOL; ++p)
+                    g[p] = in ? __ldg(a.grid + ((int64_t)p * N + gy) * N + gx) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < NPR; ++q)
+                    reg[(size_t)q * plane + e] = make_float4(g[2 * q].x, g[2 * q].y, g[2 * q + 1].x,
+                                                             g[2 * q + 1].y);
+                if (NPOL % 2) single[e] = g[NPOL - 1];
+            }
+        }
+        // record metadata (id, kernel slice offset, region index of tap (0, 0),
+        // support | conj << 16), records wider than h_max first: warps claim
+        // records in this order, so the long ones start early and the short
+        // ones even out the end of the chunk
+        for (int r = threadIdx.x; r < nc; r += kStagedThreads) {
+            const uint32_t id = __ldg(a.entries + item.start + c0 + r);
             int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
             const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
             const int S = __ldg(a.support + rc.plane), h = S >> 1;
-            const typename TE::T* K = reinterpret_cast<const typename TE::T*>(a.table) +
-                                      __ldg(a.plane_off + rc.plane) +
-                                      ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
-            const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
-            // region index of tap (0, 0)
+            const int64_t kofs = __ldg(a.plane_off + rc.plane) +
+                                 ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
             const int base = (rc.kv - h - ry0) * RS + (rc.ku - h - rx0);
-            float acc[NPOL][2];
-#pragma unroll
-            for (int p = 0; p < NPOL; ++p) acc[p][0] = acc[p][1] = 0.f;
+            const uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
+            const int pos = h > hmax / 2 ? atomicAdd(&s_front, 1) : atomicSub(&s_back, 1) - 1;
+            meta[pos] = make_uint4(id, (uint32_t)kofs, (uint32_t)base, w);
+        }
+        __syncthreads();
+        for (;;) {
+            int r = 0;
+            if (lane == 0) r = atomicAdd(&s_next, 1);
+            r = __shfl_sync(0xffffffffu, r, 0);
+            if (r >= nc) break;
+            const uint4 m = meta[r];
+            const uint32_t id = m.x;
+            const T* K = tab + m.y;
+            const int S = (int)(m.w & 0xffffu);
+            const float sg = (m.w >> 16) ? -1.f : 1.f;
             const int n = S * S;
-            // flattened taps t = lane + 32 i, (tv, tu) advanced incrementally;
-            // the kernel values of the next step load while this one's FMAs run
+            // flattened taps t = lane + 32 i; the region index advances by
+            // `step` per 32 taps, plus `wrap` when the tap column wraps
             const int dq = 32 / S, dr = 32 - dq * S;
-            int tv = lane / S, tu = lane - (lane / S) * S;
-            float2 k1 = lane < n ? TE::load(K + lane) : make_float2(0.f, 0.f);
-            for (int t = lane; t < n; t += 32) {
-                const float2 k = k1;
-                if (t + 32 < n) k1 = TE::load(K + t + 32);
-                const float ki = sg * k.y;
-                const int off = base + tv * RS + tu;
+            const int step = dq * RS + dr, wrap = RS - S;
+            int tu = lane % S;
+            int off = (int)m.z + (lane / S) * RS + tu;
+            // a1 = sum K.re G, a2 = sum K.im G (packed FP32x2 FMAs); the
+            // conjugation sign is applied once at the end
+            float2 a1[NPOL], a2[NPOL];
 #pragma unroll
-                for (int p = 0; p < NPOL; ++p) {
-                    const float2 gv = reg[(size_t)p * RS * RS + off];
-                    // conj(K_i) G with K_i = K (w >= 0) or conj K (w < 0)
-                    acc[p][0] = fmaf(k.x, gv.x, acc[p][0]);
-                    acc[p][0] = fmaf(ki, gv.y, acc[p][0]);
-                    acc[p][1] = fmaf(k.x, gv.y, acc[p][1]);
-                    acc[p][1] = fmaf(-ki, gv.x, acc[p][1]);
+            for (int p = 0; p < NPOL; ++p) a1[p] = a2[p] = make_float2(0.f, 0.f);
+            auto tap = [&](const float2 k, const int o) {
+                const float2 kxx = make_float2(k.x, k.x), kyy = make_float2(k.y, k.y);
+#pragma unroll
+                for (int q = 0; q < NPR; ++q) {
+                    const float4 g = reg[(size_t)q * plane + o];
+                    const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
+                    a1[2 * q] = __ffma2_rn(kxx, g0, a1[2 * q]);
+                    a2[2 * q] = __ffma2_rn(kyy, g0, a2[2 * q]);
+                    a1[2 * q + 1] = __ffma2_rn(kxx, g1, a1[2 * q + 1]);
+                    a2[2 * q + 1] = __ffma2_rn(kyy, g1, a2[2 * q + 1]);
                 }
+                if (NPOL % 2) {
+                    const float2 g = single[o];
+                    a1[NPOL - 1] = __ffma2_rn(kxx, g, a1[NPOL - 1]);
+                    a2[NPOL - 1] = __ffma2_rn(kyy, g, a2[NPOL - 1]);
+                }
+            };
+            auto advance = [&]() {
+                off += step;
                 tu += dr;
-                tv += dq;
                 if (tu >= S) {
                     tu -= S;
-                    ++tv;
+                    off += wrap;
                 }
+            };
+            // steps 0 .. nfull - 1 have a tap on every lane, step nfull on
+            // the lanes below n - 32 nfull.  Kernel values are loaded D steps
+            // ahead, unconditionally: past the slice they read the next
+            // slice or the table's zero slack, never used.
+            const int nfull = (n - 1) >> 5;
+            const T* kp = K + lane;
+            T kq[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) kq[d] = __ldg(kp + 32 * d);
+            kp += 32 * D;
+            int i = 0;
+            for (; i + D <= nfull; i += D) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float2 k = TE::cvt(kq[d]);
+                    kq[d] = __ldg(kp + 32 * d);
+                    tap(k, off);
+                    advance();
+                }
+                kp += 32 * D;
+            }
+            // the last (< D) full steps and the partial one, from the front
+            // of the ring
+            for (; i <= nfull; ++i) {
+                const bool live = i < nfull || lane + 32 * nfull < n;
+                tap(live ? TE::cvt(kq[0]) : make_float2(0.f, 0.f), live ? off : zoff);
+                advance();
+#pragma unroll
+                for (int d = 0; d + 1 < D; ++d) kq[d] = kq[d + 1];
+            }
+            // conj(K_i) G with K_i = K (w >= 0) or conj K (w < 0):
+            // re = sum K.re G.re + s K.im G.im, im = sum K.re G.im - s K.im G.re
+            float acc[NPOL][2];
+#pragma unroll
+            for (int p = 0; p < NPOL; ++p) {
+                acc[p][0] = fmaf(sg, a2[p].y, a1[p].x);
+                acc[p][1] = fmaf(-sg, a2[p].x, a1[p].y);
             }
             if constexpr (NPOL == 4) {
                 // reduce-scatter butterfly: lanes with bit 4 set keep pols 2, 3,
@@ -220,8 +342,9 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
 template <int NPOL, int TK>
 bool launch_staged_t(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s) {
     const int RS = kStagedTile + 2 * hmax;
-    const size_t smem = (size_t)RS * RS * NPOL * sizeof(float2);
-    if (smem > kStagedSmemMax) return false;
+    if ((size_t)RS * RS * NPOL * sizeof(float2) > kStagedSmemMax) return false;
+    const size_t smem = (size_t)(RS * RS + kStagedPad) * NPOL * sizeof(float2) +
+                        kStagedMeta * sizeof(uint4);
     cudaFuncSetAttribute(k_degrid_staged<NPOL, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int per_sm = 0;

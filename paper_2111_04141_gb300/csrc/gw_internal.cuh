@@ -279,6 +279,9 @@ struct DegridArgs {
 };
 void launch_degrid(const DegridArgs& a, int64_t nvis_upper, int num_sms, cudaStream_t s);
 constexpr size_t kStagedSmemMax = 200 * 1024;   // staged-degrid region budget (bytes)
+// Zeroed elements after the last kernel slice of the unpadded tables: the
+// staged degridder loads kernel values up to this many elements past a slice.
+constexpr int64_t kTableSlack = 256;
 int degrid_staged_tile();
 bool degrid_staged_fits(int hmax, int npol);
 // Returns false (nothing launched) if the region does not fit.
