@@ -125,24 +125,17 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
     using T = typename TE::T;
     constexpr int D = kStagedDepth;
     // grid region as polarisation pairs [NPOL / 2][RS][RS] of (G_p, G_p+1),
-    // then [RS][RS] of the last polarisation if NPOL is odd, then the chunk's
-    // record metadata
+    // then [RS][RS] of the last polarisation if NPOL is odd; the chunk's
+    // record metadata after the largest region (RS = 16 + 2 h_max)
     constexpr int NPR = NPOL / 2;
     extern __shared__ __align__(16) float4 reg[];
     __shared__ StagedChunk s_ch;
-    __shared__ int s_next, s_front, s_back;
-    const int RS = kStagedTile + 2 * hmax;
-    // each plane holds RS x RS values and kStagedPad zeros (element RS * RS
-    // is read by lanes without a tap in a record's last step); RS is even, so
-    // every part stays 16-byte aligned
-    const int plane = RS * RS + kStagedPad;
-    const int zoff = RS * RS;
-    float2* single = reinterpret_cast<float2*>(reg + (size_t)NPR * plane);
-    uint4* meta = reinterpret_cast<uint4*>(single + (NPOL % 2 ? plane : 0));
-    if (threadIdx.x < kStagedPad) {
-#pragma unroll
-        for (int q = 0; q < NPR; ++q) reg[(size_t)q * plane + zoff + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (NPOL % 2) single[zoff + threadIdx.x] = make_float2(0.f, 0.f);
+    __shared__ int s_next, s_front, s_back, s_h;
+    uint4* meta;
+    {
+        const int RSM = kStagedTile + 2 * hmax, pm = RSM * RSM + kStagedPad;
+        meta = reinterpret_cast<uint4*>(reinterpret_cast<float2*>(reg + (size_t)NPR * pm) +
+                                        (NPOL % 2 ? pm : 0));
     }
     const int lane = threadIdx.x & 31;
     const int N = a.N, hb = a.beta / 2;
@@ -167,16 +160,58 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             s_next = 0;
             s_front = 0;
             s_back = nc;
+            // an item served in several chunks keeps one region for all of
+            // them: the plan's largest half-support
+            s_h = cur.len > kStagedMeta ? hmax : 0;
             next_c0 += nc;
         }
         __syncthreads();
         if (s_ch.done) break;
         const Item item = s_ch.item;
         const int c0 = s_ch.c0, nc = s_ch.nc;
-        const int rx0 = (item.tile % a.ntiles_u) * kStagedTile - hmax;
-        const int ry0 = (item.tile / a.ntiles_u) * kStagedTile - hmax;
+        const int tx0 = (item.tile % a.ntiles_u) * kStagedTile;
+        const int ty0 = (item.tile / a.ntiles_u) * kStagedTile;
+        // record metadata (id, kernel slice offset, centre relative to the
+        // tile, support | conj << 16), records wider than h_max / 2 first:
+        // warps claim records in this order, so the long ones start early and
+        // the short ones even out the end of the chunk.  The largest
+        // half-support of the records sets the region.
+        {
+            int hw = 0;
+            for (int r = threadIdx.x; r < nc; r += kStagedThreads) {
+                const uint32_t id = __ldg(a.entries + item.start + c0 + r);
+                int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
+                const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
+                const int S = __ldg(a.support + rc.plane), h = S >> 1;
+                const int64_t kofs = __ldg(a.plane_off + rc.plane) +
+                                     ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+                const uint32_t rel = (uint32_t)(rc.ku - tx0) | (uint32_t)(rc.kv - ty0) << 8;
+                const uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
+                const int pos = h > hmax / 2 ? atomicAdd(&s_front, 1) : atomicSub(&s_back, 1) - 1;
+                meta[pos] = make_uint4(id, (uint32_t)kofs, rel, w);
+                hw = max(hw, h);
+            }
+            hw = (int)__reduce_max_sync(0xffffffffu, (unsigned)hw);
+            if (lane == 0 && hw > 0) atomicMax(&s_h, hw);
+        }
+        __syncthreads();
+        // the region: rows and columns [t0 - hi, t0 + 16 + hi) of the tile;
+        // each plane holds RS x RS values and kStagedPad zeros (element RS * RS
+        // is read by lanes without a tap in a record's last step); RS is even,
+        // so every part stays 16-byte aligned
+        const int hi = s_h;
+        const int RS = kStagedTile + 2 * hi;
+        const int plane = RS * RS + kStagedPad;
+        const int zoff = RS * RS;
+        float2* single = reinterpret_cast<float2*>(reg + (size_t)NPR * plane);
         if (c0 == 0) {
-            // stage the region
+            const int rx0 = tx0 - hi, ry0 = ty0 - hi;
+            if (threadIdx.x < kStagedPad) {
+#pragma unroll
+                for (int q = 0; q < NPR; ++q)
+                    reg[(size_t)q * plane + zoff + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (NPOL % 2) single[zoff + threadIdx.x] = make_float2(0.f, 0.f);
+            }
             for (int e = threadIdx.x; e < zoff; e += kStagedThreads) {
                 const int y = e / RS, x = e - y * RS;
                 const int gy = ry0 + y, gx = rx0 + x;
@@ -191,24 +226,8 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
                                                              g[2 * q + 1].y);
                 if (NPOL % 2) single[e] = g[NPOL - 1];
             }
+            __syncthreads();
         }
-        // record metadata (id, kernel slice offset, region index of tap (0, 0),
-        // support | conj << 16), records wider than h_max first: warps claim
-        // records in this order, so the long ones start early and the short
-        // ones even out the end of the chunk
-        for (int r = threadIdx.x; r < nc; r += kStagedThreads) {
-            const uint32_t id = __ldg(a.entries + item.start + c0 + r);
-            int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
-            const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
-            const int S = __ldg(a.support + rc.plane), h = S >> 1;
-            const int64_t kofs = __ldg(a.plane_off + rc.plane) +
-                                 ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
-            const int base = (rc.kv - h - ry0) * RS + (rc.ku - h - rx0);
-            const uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
-            const int pos = h > hmax / 2 ? atomicAdd(&s_front, 1) : atomicSub(&s_back, 1) - 1;
-            meta[pos] = make_uint4(id, (uint32_t)kofs, (uint32_t)base, w);
-        }
-        __syncthreads();
         for (;;) {
             int r = 0;
             if (lane == 0) r = atomicAdd(&s_next, 1);
@@ -225,7 +244,9 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             const int dq = 32 / S, dr = 32 - dq * S;
             const int step = dq * RS + dr, wrap = RS - S;
             int tu = lane % S;
-            int off = (int)m.z + (lane / S) * RS + tu;
+            // region index of tap (0, 0): centre - h + hi on both axes
+            const int base = ((int)(m.z >> 8) - (S >> 1) + hi) * RS + ((int)(m.z & 0xffu) - (S >> 1) + hi);
+            int off = base + (lane / S) * RS + tu;
             // a1 = sum K.re G, a2 = sum K.im G (packed FP32x2 FMAs); the
             // conjugation sign is applied once at the end
             float2 a1[NPOL], a2[NPOL];
