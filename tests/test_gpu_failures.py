@@ -108,3 +108,22 @@ def test_hook_is_off_after_firing_and_rejects_negative():
         gw.Plan.from_observation(obs).close()           # the hook fired once and is off
         with pytest.raises(gw.GwError):
             P.debug_fail_alloc(-1)
+
+
+def test_device_status_word_is_clear_after_gridding():
+    """The status word a bounded device wait sets when it gives up reads 0
+    (GW_OK) after gridding and degridding that completed, and reading it
+    leaves the plan usable."""
+    gw, P, obs = _setup()
+    with torch.cuda.device(DEV):
+        with gw.Plan.from_observation(obs) as plan:
+            uvw = torch.from_numpy(obs.uvw_m).to(DEV)
+            freq = torch.from_numpy(obs.freq_hz).to(DEV)
+            vis = torch.from_numpy(obs.vis).to(DEV)
+            for kernel in (1, 2):
+                plan.set_tuning(**dict(plan.get_tuning(), grid_kernel=kernel))
+                g = plan.grid(uvw, freq, vis)
+                plan.device_status()
+                out = plan.degrid(uvw, freq, g)
+                plan.device_status()
+                assert torch.isfinite(torch.view_as_real(out)).all()
