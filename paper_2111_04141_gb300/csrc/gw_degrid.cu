@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
     extern __shared__ __align__(16) float4 reg[];
     __shared__ StagedChunk s_ch;
     __shared__ int s_next, s_front, s_back, s_h;
+    __shared__ int s_taps[8];                  // taps of the chunk's records by S mod 8
     uint4* meta;
     {
         const int RSM = kStagedTile + 2 * hmax, pm = RSM * RSM + kStagedPad;
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             s_h = cur.len > kStagedMeta ? hmax : 0;
             next_c0 += nc;
         }
+        if (threadIdx.x < 8) s_taps[threadIdx.x] = 0;
         __syncthreads();
         if (s_ch.done) break;
         const Item item = s_ch.item;
@@ -190,19 +192,39 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
                 const int pos = h > hmax / 2 ? atomicAdd(&s_front, 1) : atomicSub(&s_back, 1) - 1;
                 meta[pos] = make_uint4(id, (uint32_t)kofs, rel, w);
                 hw = max(hw, h);
+                atomicAdd(&s_taps[S & 7], S * S);
             }
             hw = (int)__reduce_max_sync(0xffffffffu, (unsigned)hw);
             if (lane == 0 && hw > 0) atomicMax(&s_h, hw);
         }
         __syncthreads();
-        // the region: rows and columns [t0 - hi, t0 + 16 + hi) of the tile;
-        // each plane holds RS x RS values and kStagedPad zeros (element RS * RS
-        // is read by lanes without a tap in a record's last step); RS is even,
-        // so every part stays 16-byte aligned
+        // the region: rows and columns [t0 - hi, t0 + 16 + hi) of the tile,
+        // RS x RS values at row pitch RSP; each plane holds RS x RSP elements
+        // and kStagedPad zeros (element RS * RSP is read by lanes without a
+        // tap in a record's last step).  A quarter-warp's 8 flattened taps
+        // that cross a footprint row end jump by RSP - S elements: with RSP
+        // = S mod 8 its 16-byte loads stay free of bank conflicts, so the
+        // pitch is padded to the residue of the supports that carry most of
+        // the item's taps, where the shared memory allows (items served in
+        // several chunks keep RSP = RS).  RS is even, so every part stays
+        // 16-byte aligned.
         const int hi = s_h;
         const int RS = kStagedTile + 2 * hi;
-        const int plane = RS * RS + kStagedPad;
-        const int zoff = RS * RS;
+        int RSP = RS;
+        if (item.len <= kStagedMeta) {
+            int best = 0, bt = -1;
+#pragma unroll
+            for (int k = 1; k < 8; k += 2)     // supports are odd
+                if (s_taps[k] > bt) {
+                    bt = s_taps[k];
+                    best = k;
+                }
+            const int rsp = RS + ((best - RS) & 7);
+            const int RSM = kStagedTile + 2 * hmax;
+            if (RS * rsp <= RSM * RSM) RSP = rsp;
+        }
+        const int plane = RS * RSP + kStagedPad;
+        const int zoff = RS * RSP;
         float2* single = reinterpret_cast<float2*>(reg + (size_t)NPR * plane);
         if (c0 == 0) {
             const int rx0 = tx0 - hi, ry0 = ty0 - hi;
@@ -212,8 +234,9 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
                     reg[(size_t)q * plane + zoff + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (NPOL % 2) single[zoff + threadIdx.x] = make_float2(0.f, 0.f);
             }
-            for (int e = threadIdx.x; e < zoff; e += kStagedThreads) {
-                const int y = e / RS, x = e - y * RS;
+            for (int e0 = threadIdx.x; e0 < RS * RS; e0 += kStagedThreads) {
+                const int y = e0 / RS, x = e0 - y * RS;
+                const int e = y * RSP + x;
                 const int gy = ry0 + y, gx = rx0 + x;
                 const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
                 float2 g[NPOL];
@@ -242,11 +265,11 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             // flattened taps t = lane + 32 i; the region index advances by
             // `step` per 32 taps, plus `wrap` when the tap column wraps
             const int dq = 32 / S, dr = 32 - dq * S;
-            const int step = dq * RS + dr, wrap = RS - S;
+            const int step = dq * RSP + dr, wrap = RSP - S;
             int tu = lane % S;
             // region index of tap (0, 0): centre - h + hi on both axes
-            const int base = ((int)(m.z >> 8) - (S >> 1) + hi) * RS + ((int)(m.z & 0xffu) - (S >> 1) + hi);
-            int off = base + (lane / S) * RS + tu;
+            const int base = ((int)(m.z >> 8) - (S >> 1) + hi) * RSP + ((int)(m.z & 0xffu) - (S >> 1) + hi);
+            int off = base + (lane / S) * RSP + tu;
             // a1 = sum K.re G, a2 = sum K.im G (packed FP32x2 FMAs); the
             // conjugation sign is applied once at the end
             float2 a1[NPOL], a2[NPOL];
