@@ -110,14 +110,25 @@ constexpr int kStagedPad = 4;       // zero elements after each staged plane
 #endif
 constexpr int kStagedDepth = GW_DEGRID_DEPTH;   // steps of kernel values loaded ahead
 
-// Work of one CTA iteration: a chunk of at most kStagedMeta records of a work
-// item (items longer than that are served in several chunks from one staged
-// region).
+// A chunk: at most kStagedMeta records of a work item (items longer than
+// that are served in several chunks from one staged region), with its record
+// metadata in one of two shared buffers.
 struct StagedChunk {
     Item item;
     int c0, nc;     // first record of the chunk in the item, records in it
-    int done;
+    int done;       // no work left
+    int h;          // largest half-support of the chunk's records (the region's)
+    int front, back, next;   // metadata placement, record claims
+    int taps[8];    // taps of the chunk's records by S mod 8
 };
+
+constexpr int kLoaderThreads = 128;                       // warps 0-3
+constexpr int kMetaPerLoader = kStagedMeta / kLoaderThreads;
+constexpr int kLoaderBatch = 4;                           // records whose loads a loader issues together
+
+__device__ __forceinline__ void loader_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
+}
 
 template <int NPOL, int TK>
 __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, int hmax) {
@@ -125,18 +136,16 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
     using T = typename TE::T;
     constexpr int D = kStagedDepth;
     // grid region as polarisation pairs [NPOL / 2][RS][RS] of (G_p, G_p+1),
-    // then [RS][RS] of the last polarisation if NPOL is odd; the chunk's
+    // then [RS][RS] of the last polarisation if NPOL is odd; two chunks'
     // record metadata after the largest region (RS = 16 + 2 h_max)
     constexpr int NPR = NPOL / 2;
     extern __shared__ __align__(16) float4 reg[];
-    __shared__ StagedChunk s_ch;
-    __shared__ int s_next, s_front, s_back, s_h;
-    __shared__ int s_taps[8];                  // taps of the chunk's records by S mod 8
-    uint4* meta;
+    __shared__ StagedChunk s_ch[2];
+    uint4* meta0;
     {
         const int RSM = kStagedTile + 2 * hmax, pm = RSM * RSM + kStagedPad;
-        meta = reinterpret_cast<uint4*>(reinterpret_cast<float2*>(reg + (size_t)NPR * pm) +
-                                        (NPOL % 2 ? pm : 0));
+        meta0 = reinterpret_cast<uint4*>(reinterpret_cast<float2*>(reg + (size_t)NPR * pm) +
+                                         (NPOL % 2 ? pm : 0));
     }
     const int lane = threadIdx.x & 31;
     const int N = a.N, hb = a.beta / 2;
@@ -145,59 +154,94 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
     // thread 0: the item being served and the next chunk's first record
     Item cur{};
     int next_c0 = 0;
-    for (;;) {
-        __syncthreads();                       // previous chunk fully consumed
+
+    // The loader warps (0-3) pick the next chunk and load its records'
+    // metadata (id, kernel slice offset, centre relative to the tile,
+    // support | conj << 16) into buffer `buf`, records wider than h_max / 2
+    // first: warps claim records in this order, so the long ones start early
+    // and the short ones even out the end of the chunk.  Each loader thread
+    // issues the loads of its (up to 8) records together.
+    auto load_chunk = [&](const int buf) {
+        StagedChunk& c = s_ch[buf];
         if (threadIdx.x == 0) {
+            c.done = 0;
             if (next_c0 == 0 || next_c0 >= cur.len) {
                 const uint32_t it = atomicAdd(a.queue, 1u);
-                s_ch.done = it >= nitems;
+                c.done = it >= nitems;
                 if (it < nitems) cur = a.items[it];
                 next_c0 = 0;
             }
             const int nc = min(kStagedMeta, cur.len - next_c0);
-            s_ch.item = cur;
-            s_ch.c0 = next_c0;
-            s_ch.nc = nc;
-            s_next = 0;
-            s_front = 0;
-            s_back = nc;
+            c.item = cur;
+            c.c0 = next_c0;
+            c.nc = nc;
+            c.next = 0;
+            c.front = 0;
+            c.back = nc;
             // an item served in several chunks keeps one region for all of
             // them: the plan's largest half-support
-            s_h = cur.len > kStagedMeta ? hmax : 0;
+            c.h = cur.len > kStagedMeta ? hmax : 0;
+            for (int k = 0; k < 8; ++k) c.taps[k] = 0;
             next_c0 += nc;
         }
-        if (threadIdx.x < 8) s_taps[threadIdx.x] = 0;
-        __syncthreads();
-        if (s_ch.done) break;
-        const Item item = s_ch.item;
-        const int c0 = s_ch.c0, nc = s_ch.nc;
+        loader_sync();
+        if (c.done) return;
+        const Item item = c.item;
+        const int c0 = c.c0, nc = c.nc;
         const int tx0 = (item.tile % a.ntiles_u) * kStagedTile;
         const int ty0 = (item.tile / a.ntiles_u) * kStagedTile;
-        // record metadata (id, kernel slice offset, centre relative to the
-        // tile, support | conj << 16), records wider than h_max / 2 first:
-        // warps claim records in this order, so the long ones start early and
-        // the short ones even out the end of the chunk.  The largest
-        // half-support of the records sets the region.
-        {
-            int hw = 0;
-            for (int r = threadIdx.x; r < nc; r += kStagedThreads) {
-                const uint32_t id = __ldg(a.entries + item.start + c0 + r);
-                int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + id);
-                const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
-                const int S = __ldg(a.support + rc.plane), h = S >> 1;
-                const int64_t kofs = __ldg(a.plane_off + rc.plane) +
-                                     ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
-                const uint32_t rel = (uint32_t)(rc.ku - tx0) | (uint32_t)(rc.kv - ty0) << 8;
-                const uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
-                const int pos = h > hmax / 2 ? atomicAdd(&s_front, 1) : atomicSub(&s_back, 1) - 1;
-                meta[pos] = make_uint4(id, (uint32_t)kofs, rel, w);
-                hw = max(hw, h);
-                atomicAdd(&s_taps[S & 7], S * S);
+        uint4* meta = meta0 + buf * kStagedMeta;
+        int hw = 0;
+        for (int k0 = 0; k0 < kMetaPerLoader; k0 += kLoaderBatch) {
+            uint32_t ids[kLoaderBatch];
+            gw_index_rec rcs[kLoaderBatch];
+#pragma unroll
+            for (int k = 0; k < kLoaderBatch; ++k) {
+                const int r = (k0 + k) * kLoaderThreads + threadIdx.x;
+                ids[k] = r < nc ? __ldg(a.entries + item.start + c0 + r) : 0u;
             }
-            hw = (int)__reduce_max_sync(0xffffffffu, (unsigned)hw);
-            if (lane == 0 && hw > 0) atomicMax(&s_h, hw);
+#pragma unroll
+            for (int k = 0; k < kLoaderBatch; ++k) {
+                const int r = (k0 + k) * kLoaderThreads + threadIdx.x;
+                if (r < nc) {
+                    int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + ids[k]);
+                    rcs[k] = *reinterpret_cast<gw_index_rec*>(&rv);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kLoaderBatch; ++k) {
+                const int r = (k0 + k) * kLoaderThreads + threadIdx.x;
+                if (r < nc) {
+                    const gw_index_rec rc = rcs[k];
+                    const int S = __ldg(a.support + rc.plane), h = S >> 1;
+                    const int64_t kofs = __ldg(a.plane_off + rc.plane) +
+                                         ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+                    const uint32_t rel = (uint32_t)(rc.ku - tx0) | (uint32_t)(rc.kv - ty0) << 8;
+                    const uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
+                    const int pos =
+                        h > hmax / 2 ? atomicAdd(&c.front, 1) : atomicSub(&c.back, 1) - 1;
+                    meta[pos] = make_uint4(ids[k], (uint32_t)kofs, rel, w);
+                    hw = max(hw, h);
+                    atomicAdd(&c.taps[S & 7], S * S);
+                }
+            }
+            if ((k0 + kLoaderBatch) * kLoaderThreads >= nc) break;
         }
-        __syncthreads();
+        hw = (int)__reduce_max_sync(0xffffffffu, (unsigned)hw);
+        if (lane == 0 && hw > 0) atomicMax(&c.h, hw);
+    };
+
+    if (threadIdx.x < kLoaderThreads) load_chunk(0);
+    __syncthreads();
+    for (int kc = 0;; ++kc) {
+        const int buf = kc & 1;
+        const StagedChunk& c = s_ch[buf];
+        if (c.done) break;
+        const Item item = c.item;
+        const int c0 = c.c0, nc = c.nc;
+        const int tx0 = (item.tile % a.ntiles_u) * kStagedTile;
+        const int ty0 = (item.tile / a.ntiles_u) * kStagedTile;
+        const uint4* meta = meta0 + buf * kStagedMeta;
         // the region: rows and columns [t0 - hi, t0 + 16 + hi) of the tile,
         // RS x RS values at row pitch RSP; each plane holds RS x RSP elements
         // and kStagedPad zeros (element RS * RSP is read by lanes without a
@@ -208,15 +252,15 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
         // the item's taps, where the shared memory allows (items served in
         // several chunks keep RSP = RS).  RS is even, so every part stays
         // 16-byte aligned.
-        const int hi = s_h;
+        const int hi = c.h;
         const int RS = kStagedTile + 2 * hi;
         int RSP = RS;
         if (item.len <= kStagedMeta) {
             int best = 0, bt = -1;
 #pragma unroll
             for (int k = 1; k < 8; k += 2)     // supports are odd
-                if (s_taps[k] > bt) {
-                    bt = s_taps[k];
+                if (c.taps[k] > bt) {
+                    bt = c.taps[k];
                     best = k;
                 }
             const int rsp = RS + ((best - RS) & 7);
@@ -251,9 +295,11 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
             }
             __syncthreads();
         }
+        // the loaders prepare the next chunk, then join the record claims
+        if (threadIdx.x < kLoaderThreads) load_chunk(buf ^ 1);
         for (;;) {
             int r = 0;
-            if (lane == 0) r = atomicAdd(&s_next, 1);
+            if (lane == 0) r = atomicAdd(&s_ch[buf].next, 1);
             r = __shfl_sync(0xffffffffu, r, 0);
             if (r >= nc) break;
             const uint4 m = meta[r];
@@ -380,6 +426,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
                 }
             }
         }
+        __syncthreads();   // chunk consumed, the next chunk's metadata in place
     }
 }
 
@@ -388,7 +435,7 @@ bool launch_staged_t(const DegridArgs& a, int hmax, int num_sms, cudaStream_t s)
     const int RS = kStagedTile + 2 * hmax;
     if ((size_t)RS * RS * NPOL * sizeof(float2) > kStagedSmemMax) return false;
     const size_t smem = (size_t)(RS * RS + kStagedPad) * NPOL * sizeof(float2) +
-                        kStagedMeta * sizeof(uint4);
+                        2 * kStagedMeta * sizeof(uint4);
     cudaFuncSetAttribute(k_degrid_staged<NPOL, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int per_sm = 0;

@@ -278,7 +278,9 @@ struct DegridArgs {
     int ntiles_u = 0;
 };
 void launch_degrid(const DegridArgs& a, int64_t nvis_upper, int num_sms, cudaStream_t s);
-constexpr size_t kStagedSmemMax = 200 * 1024;   // staged-degrid region budget (bytes)
+// Staged-degrid region budget (bytes): the 227 KB a CTA may hold, less two
+// buffers of 1,024 records' metadata and the static shared memory.
+constexpr size_t kStagedSmemMax = 232448 - 2 * 1024 * 16 - 512;
 // Zeroed elements after the last kernel slice of the unpadded tables: the
 // staged degridder loads kernel values up to this many elements past a slice.
 constexpr int64_t kTableSlack = 256;

@@ -284,6 +284,34 @@ def test_degrid_matches_oracle(gw, case):
     assert rel_l2(got, ref) <= TOL_GRID, name
 
 
+def test_degrid_long_items_in_chunks(gw):
+    """Tiles holding more records than the staged degridder's metadata buffer
+    (1,024) are served in several chunks from one region: with one work item
+    per tile the result matches the oracle and the default item size."""
+    obs = syn.small_case(n_ant=12, n_times=64, n_chan=4, npol=4, grid_n=64, s_min=7, s_max=15,
+                         n_w=4, diameter_m=400.0, seed=11)
+    prm = Params(**obs.plan_kwargs())
+    rng = np.random.default_rng(22)
+    N = prm.grid_n
+    grid = (rng.normal(size=(prm.npol, N, N)) + 1j * rng.normal(size=(prm.npol, N, N)))
+    grid = grid.astype(np.complex64)
+    ref = oracle_for(prm).degrid(obs.uvw_m, obs.freq_hz, grid.astype(np.complex128))
+    with gw.Plan.from_observation(obs) as plan:
+        idx, _ = _gpu_index(gw, plan, obs.uvw_m, obs.freq_hz)
+        plan.set_tuning(**dict(plan.get_tuning(), item_max=1 << 20, degrid_kernel=1))
+        v_long = plan.degrid(dev(obs.uvw_m), dev(obs.freq_hz), dev(grid)).cpu().numpy()
+        plan.set_tuning(**dict(plan.get_tuning(), item_max=1024))
+        v_def = plan.degrid(dev(obs.uvw_m), dev(obs.freq_hz), dev(grid)).cpu().numpy()
+    got = v_long.reshape(ref.shape).astype(np.complex128)
+    assert obs.nvis > 4 * 1024
+    assert rel_l2(got, ref) <= TOL_GRID
+    assert rel_l2(v_def.reshape(ref.shape).astype(np.complex128), ref) <= TOL_GRID
+    # records per 16 x 16 centre tile: some tiles need more than one chunk
+    ok = (idx["flags"] & 1) != 0
+    tiles = (idx["kv"][ok] // 16) * (N // 16) + idx["ku"][ok] // 16
+    assert np.bincount(tiles).max() > 1024
+
+
 def test_adjoint_dot_gpu(gw):
     obs = CASES["small-w"]()
     rng = np.random.default_rng(3)
