@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 5
+#define GW_API_VERSION 6
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -383,6 +383,28 @@ gw_status gw_grid_vis_devcount(gw_plan plan, const double* uvw_m, const double* 
 gw_status gw_degrid_vis_devcount(gw_plan plan, const double* uvw_m, const double* freq_hz,
                                  const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
                                  const void* grid, void* vis_out, void* cuda_stream);
+
+/* gw_grid_vis_devcount with the grid read back to the host while it is
+ * still being computed.  No thesis counterpart (serving: a job's latency
+ * includes bringing its grid to the host).  The gridder runs once per band
+ * of grid-tile rows (n_bands bands of about equal height, at most the number
+ * of tile rows, in [1, 64]); a band's tiles receive updates only from its own
+ * work items, so when its launch ends its grid rows are final and are
+ * copied to host_grid ([npol][N][N] complex64, page-locked host memory,
+ * 8-byte aligned; rows of every polarisation plane) on a copy stream of the
+ * plan while the next band grids.  Work issued later on cuda_stream waits
+ * for the last copy, so a stream synchronise (or an event) covers the
+ * result in host memory.  `grid` (device) accumulates as in
+ * gw_grid_vis_devcount (zero it first for a fresh grid) and holds the same
+ * values.  No allocation and no synchronisation after the plan's first call
+ * (which creates the copy stream and its events): the call can be captured
+ * into a CUDA graph.  GW_EINVAL for n_bands out of range, a null or
+ * misaligned host_grid, or the gw_grid_vis_devcount conditions. */
+gw_status gw_grid_vis_devcount_readback(gw_plan plan, const double* uvw_m,
+                                        const double* freq_hz, const int64_t* d_nrow,
+                                        int64_t max_nrow, int32_t nchan, const void* vis,
+                                        void* grid, void* host_grid, int32_t n_bands,
+                                        void* cuda_stream);
 
 /* Grid correction (Correction Step, Section 2.3 / 3.3.8), in place on
  * image (device, [npol][N][N] c64):

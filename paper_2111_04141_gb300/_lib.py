@@ -79,6 +79,8 @@ _SIGS = {
     "gw_grid_vis_compressed": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp,
                                        ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_vp]),
     "gw_grid_vis_devcount": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
+    "gw_grid_vis_devcount_readback": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
+                                              c_vp, c_i32, c_vp]),
     "gw_degrid_vis_devcount": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "gw_degrid_vis": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp,
                               ctypes.POINTER(c_i64), c_vp]),

@@ -151,6 +151,10 @@ struct gw_plan_s {
     double c1_norm = 1.0;
     // host-input pipeline (gw_grid_vis_host): a copy stream, two staging sets
     cudaStream_t h_copy = nullptr;
+    // banded read-back (gw_grid_vis_devcount_readback): copy stream and
+    // per-band events, created on first use
+    cudaStream_t rb_stream = nullptr;
+    std::vector<cudaEvent_t> rb_ev;
     cudaEvent_t h_ready[2] = {nullptr, nullptr}, h_free[2] = {nullptr, nullptr};
     double* h_uvw[2] = {nullptr, nullptr};
     void* h_vis[2] = {nullptr, nullptr};
@@ -224,6 +228,8 @@ void plan_free(gw_plan p) {
     }
     dev_free(p->h_freq);
     if (p->h_copy) cudaStreamDestroy(p->h_copy);
+    for (auto ev : p->rb_ev) cudaEventDestroy(ev);
+    if (p->rb_stream) cudaStreamDestroy(p->rb_stream);
     dev_free(p->d_c1);
     dev_free(p->d_z);
     dev_free(p->d_hpr);
@@ -1505,6 +1511,103 @@ gw_status gw_grid_vis_devcount(gw_plan p, const double* uvw_m, const double* fre
     launch_grid(a, p->num_sms, s);
     e = cudaGetLastError();
     return e == cudaSuccess ? GW_OK : cuda_fail(e, "grid launch");
+}
+
+gw_status gw_grid_vis_devcount_readback(gw_plan p, const double* uvw_m, const double* freq_hz,
+                                        const int64_t* d_nrow, int64_t max_nrow, int32_t nchan,
+                                        const void* vis, void* grid, void* host_grid,
+                                        int32_t n_bands, void* cuda_stream) {
+    gw_status st = devcount_checks(p, uvw_m, freq_hz, d_nrow, max_nrow, nchan, vis, grid);
+    if (st != GW_OK) return st;
+    if (!host_grid) return fail(GW_EINVAL, "null host_grid");
+    if (n_bands < 1 || n_bands > kReadbackBandsMax)
+        return fail(GW_EINVAL, "n_bands must be in [1, %d]", kReadbackBandsMax);
+    const int vk = p->desc.vis_dtype;
+    if ((reinterpret_cast<uintptr_t>(grid) % 8 != 0) ||
+        (reinterpret_cast<uintptr_t>(host_grid) % 8 != 0) ||
+        (reinterpret_cast<uintptr_t>(vis) % dtype_bytes(vk) != 0))
+        return fail(GW_EINVAL, "grid and host_grid must be 8-byte aligned and vis aligned to its "
+                    "element size");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSuccess;
+    // copy stream and events (outside any capture: the first call creates them)
+    if (!p->rb_stream) {
+        e = cudaStreamCreateWithFlags(&p->rb_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            p->rb_stream = nullptr;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+    }
+    while ((int)p->rb_ev.size() < n_bands + 1) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        p->rb_ev.push_back(ev);
+    }
+    const int N = p->desc.grid_n, npol = p->desc.npol;
+    const int ntu = p->geom_grid.ntu, ntv = p->geom_grid.ntv;
+    const int nb = std::min(n_bands, ntv);
+    float2* g = reinterpret_cast<float2*>(grid);
+    float2* h = reinterpret_cast<float2*>(host_grid);
+    auto copy_rows = [&](int r0, int r1) -> cudaError_t {
+        cudaError_t ce = cudaSuccess;
+        for (int q = 0; q < npol && ce == cudaSuccess && r1 > r0; ++q) {
+            const size_t off = ((size_t)q * N + r0) * N;
+            ce = cudaMemcpyAsync(h + off, g + off, sizeof(float2) * (size_t)(r1 - r0) * N,
+                                 cudaMemcpyDeviceToHost, p->rb_stream);
+        }
+        return ce;
+    };
+    if (max_nrow > 0 && nchan > 0) {
+        e = cudaMemsetAsync(p->sc.dropped, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        const DevCount dc{d_nrow, nchan};
+        launch_index(uvw_m, freq_hz, max_nrow, nchan, p->ip, p->sc.rec, p->sc.dropped, s, d_nrow);
+        launch_bin(p->sc.rec, max_nrow * (int64_t)nchan, p->geom_grid, p->desc.n_wplanes,
+                   p->desc.support_min, p->desc.support_max, p->sc, s, dc);
+    }
+    GridArgs a;
+    a.rec = p->sc.rec;
+    a.ptable = p->ptable;
+    a.pplane_off = p->d_pplane_off;
+    a.vis = vis;
+    a.vis_kind = vk;
+    a.weight = nullptr;
+    a.table_kind = p->desc.table_dtype;
+    a.table_inv = p->table_inv;
+    a.plane_off = p->d_plane_off;
+    a.support = p->d_support;
+    a.entries = p->sc.entries;
+    a.items = p->sc.items;
+    a.queue = p->sc.counters;
+    a.grid = g;
+    a.grid_err = nullptr;
+    a.N = N;
+    a.npol = npol;
+    a.beta = p->desc.oversample;
+    a.ntiles_u = ntu;
+    a.pad_stride = p->pad_stride;
+    // band b: tile rows [b ntv / nb, (b + 1) ntv / nb), its work items the
+    // contiguous run item_off[first tile] .. item_off[first tile of the next
+    // band]; its grid rows are final once its launch ends (no other band's
+    // items touch its tiles), so they are copied while the next band grids
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        const int tv0 = (int)((int64_t)b * ntv / nb), tv1 = (int)((int64_t)(b + 1) * ntv / nb);
+        if (max_nrow > 0 && nchan > 0) {
+            a.item_first = p->sc.item_off + tv0 * ntu;
+            a.item_count = p->sc.item_off + tv1 * ntu;
+            launch_grid(a, p->num_sms, s);
+        }
+        e = cudaEventRecord(p->rb_ev[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->rb_stream, p->rb_ev[b], 0);
+        if (e == cudaSuccess)
+            e = copy_rows(tv0 * kGridTileV, std::min(tv1 * kGridTileV, N));
+    }
+    // the caller's stream continues after the last copy
+    if (e == cudaSuccess) e = cudaEventRecord(p->rb_ev[nb], p->rb_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->rb_ev[nb], 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : cuda_fail(e, "banded gridding and read-back");
 }
 
 gw_status gw_degrid_vis_devcount(gw_plan p, const double* uvw_m, const double* freq_hz,

@@ -289,7 +289,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
         // ----------------------------------------------------------- producers
         const int pt = threadIdx.x - kComputeWarps * 32;   // 0 .. kProducerThreads - 1
         const int pw = pt >> 5;
-        const uint32_t nitems = *a.item_count;
+        // items [i0, *item_count): a band of tile rows, or all of them
+        const uint32_t i0 = a.item_first ? *a.item_first : 0u;
+        const uint32_t nitems = *a.item_count - i0;
         // visibilities copied as they are: FP32 pairs without weights, with
         // the 16-byte alignment the 16-byte copies need (pairs of polarisations)
         const bool copy_vis = a.vis_kind == GW_C64 && a.weight == nullptr &&
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                     if (b == 0 && lane == 0) {
                         const uint32_t it = atomicAdd(a.queue, 1u);
                         sm.done = it >= nitems;
-                        if (it < nitems) sm.item = a.items[it];
+                        if (it < nitems) sm.item = a.items[i0 + it];
                     }
                     if (lane < kComputeWarps) sm.cnt[buf][lane] = 0;
                 }

@@ -219,7 +219,8 @@ struct GridArgs {
     const int* support;        // device [P]
     const uint32_t* entries;
     const Item* items;
-    const uint32_t* item_count;  // device scalar: item_off[ntiles]
+    const uint32_t* item_count;  // device scalar: item_off[ntiles] (one past the last item)
+    const uint32_t* item_first = nullptr;  // device scalar: first item (null: 0)
     uint32_t* queue;             // device words: [0] work queue head (zeroed before launch),
                                  // [1] status (bit 0 set when a bounded device wait gave up)
     float2* grid;                // [npol][N][N]
@@ -242,6 +243,8 @@ void launch_grid_direct(const GridArgs& a, const void* table, int64_t nvis,
 // Direct gridding is chosen for at most this many visibilities per chunk and
 // this many tap updates (visibilities x S_max^2 x npol).
 constexpr int64_t kDirectMaxVis = 16384;
+// Bands of tile rows a banded read-back may use (gw_grid_vis_devcount_readback).
+constexpr int kReadbackBandsMax = 64;
 constexpr int64_t kDirectMaxTaps = (int64_t)1 << 22;
 // One instantiation set per table kind (gw_grid_c64.cu, gw_grid_bf16.cu, gw_grid_f16.cu).
 void launch_grid_c64(const GridArgs& a, int num_sms, cudaStream_t s);

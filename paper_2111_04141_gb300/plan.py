@@ -219,6 +219,30 @@ class Plan:
               "gw_grid_vis_devcount")
         return out
 
+    def grid_devcount_readback(self, uvw, freq, d_nrow, vis, out, host_out, n_bands=8,
+                               stream=None):
+        """gw_grid_vis_devcount_readback: as grid_devcount, and the grid is
+        copied band by band to ``host_out`` (a page-locked host tensor of the
+        grid's shape) while later bands grid; work issued later on the stream
+        waits for the copies.  Capturable in a CUDA graph after the plan's
+        first call."""
+        max_nrow, nchan = self._coords(uvw, freq)
+        vis = self._vis_arg(vis, "vis", max_nrow, nchan)
+        _need(d_nrow, "d_nrow", torch.int64, self.device, (1,))
+        gshape = (self.npol, self.grid_n, self.grid_n)
+        _need(out, "grid", torch.complex64, self.device, gshape)
+        if (not isinstance(host_out, torch.Tensor) or host_out.device.type != "cpu"
+                or host_out.dtype != torch.complex64 or tuple(host_out.shape) != gshape
+                or not host_out.is_contiguous()):
+            raise TypeError(f"host_out must be a contiguous host complex64 tensor of shape {gshape}")
+        if not host_out.is_pinned():
+            raise ValueError("host_out must be page-locked (pin_memory())")
+        check(self._lib.gw_grid_vis_devcount_readback(
+            self._h, _ptr(uvw), _ptr(freq), _ptr(d_nrow), max_nrow, nchan, _ptr(vis), _ptr(out),
+            _ptr(host_out), int(n_bands), _stream_ptr(stream, self.device)),
+            "gw_grid_vis_devcount_readback")
+        return out
+
     def degrid_devcount(self, uvw, freq, d_nrow, grid, out, stream=None):
         """gw_degrid_vis_devcount: rows [0, d_nrow[0]) of ``out`` from ``grid``."""
         max_nrow, nchan = self._coords(uvw, freq)

@@ -134,8 +134,9 @@ def test_autotuner_picks_a_candidate(gw):
     assert c.get("x") == res["tuning"]
 
 
-@pytest.mark.parametrize("use_graphs", [True, False])
-def test_server_results_same_alone_and_in_the_mix(gw, use_graphs):
+@pytest.mark.parametrize("use_graphs,bands", [(True, 0), (True, 4), (False, 0)],
+                         ids=["graphs", "graphs-readback", "plain"])
+def test_server_results_same_alone_and_in_the_mix(gw, use_graphs, bands):
     from paper_2111_04141_gb300.serve import Server, build_stream, run_sequential
     max_vis = 60_000
     specs = syn.serving_setups(n_setups=4, max_vis=max_vis, grid_sizes=(256, 512))
@@ -148,7 +149,7 @@ def test_server_results_same_alone_and_in_the_mix(gw, use_graphs):
               for s in setups}
     mixed = {}
     srv = Server(setups, DEV, budget=8 << 30, n_slots=3, max_vis=max_vis, use_graphs=use_graphs,
-                 on_result=lambda j, t: mixed.__setitem__(j.id, t.clone()))
+                 readback_bands=bands, on_result=lambda j, t: mixed.__setitem__(j.id, t.clone()))
     srv.warm(models)
     done = srv.run(jobs)
     assert len(done) == len(jobs) and len(mixed) == len(jobs)
@@ -164,3 +165,49 @@ def test_server_results_same_alone_and_in_the_mix(gw, use_graphs):
     for j in jobs:
         assert rel(mixed[j.id], alone[j.id]) <= TOL, (j.id, j.kind, j.setup)
     srv.close()
+
+
+@pytest.mark.parametrize("n_bands", [1, 3, 8, 64])
+def test_grid_readback_matches_devcount(gw, n_bands):
+    """Banded gridding with read-back (gw_grid_vis_devcount_readback): the
+    host copy equals the device grid it leaves behind, both match plain
+    device-count gridding, for band counts from 1 to more than the tile rows;
+    and the call replays from a CUDA graph with another row count."""
+    obs = syn.small_case(n_ant=10, n_times=24, n_chan=3, npol=4, grid_n=160, s_min=7,
+                         s_max=31, n_w=6, diameter_m=1500.0, seed=4)
+    uvw, freq, vis = dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)
+    with gw.Plan.from_observation(obs) as plan:
+        d_nrow = torch.tensor([obs.nrow], dtype=torch.int64, device=DEV)
+        ref = plan.grid_devcount(uvw, freq, d_nrow, vis, plan.new_grid())
+        g = plan.new_grid()
+        host = torch.empty(g.shape, dtype=torch.complex64).pin_memory()
+        plan.grid_devcount_readback(uvw, freq, d_nrow, vis, g, host, n_bands=n_bands)
+        torch.cuda.synchronize()
+        assert torch.equal(host, g.cpu())
+        assert rel(g, ref) <= TOL
+        # captured once, replayed for a different row count
+        s = torch.cuda.Stream()
+        g2 = plan.new_grid()
+        host2 = torch.empty(g.shape, dtype=torch.complex64).pin_memory()
+
+        def body():
+            g2.zero_()
+            plan.grid_devcount_readback(uvw, freq, d_nrow, vis, g2, host2, n_bands=n_bands)
+
+        with torch.cuda.stream(s):
+            body()
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            body()
+        half = obs.nrow // 2
+        d_nrow.fill_(half)
+        ref_half = plan.grid_devcount(uvw, freq, d_nrow, vis, plan.new_grid())
+        host2.zero_()
+        with torch.cuda.stream(s):
+            graph.replay()
+        s.synchronize()
+        assert torch.equal(host2, g2.cpu())
+        assert rel(host2.to(DEV), ref_half) <= TOL
+        with pytest.raises(gw.GwError):
+            plan.grid_devcount_readback(uvw, freq, d_nrow, vis, g, host, n_bands=0)
