@@ -6,22 +6,23 @@ namespace gw {
 
 namespace {
 
-// Zero-padded copy of the tables: slice (p, o) becomes (S + 6) rows x SP
-// columns with the S x S values at row 3, column 7.
+// Zero-padded copy of the tables: slice (p, o) becomes (S + 2 kGridPadR)
+// rows x SP columns with the S x S values at row kGridPadR, column kGridPadC
+// (3 and 7 for the 8 x 4 lane layout).
 template <class T>
 __global__ void k_pad_tables(const T* __restrict__ tab, const int64_t* __restrict__ plane_off,
                              const int64_t* __restrict__ pplane_off, const int* __restrict__ support,
                              int P, int beta, int SP, T* __restrict__ ptab) {
     const int p = blockIdx.y;
     if (p >= P) return;
-    const int S = support[p], SR = S + 6;
+    const int S = support[p], SR = S + 2 * kGridPadR;
     const int64_t per = (int64_t)SR * SP;
     const int64_t n = (int64_t)beta * beta * per;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = e / per;
         const int rem = (int)(e - o * per);
-        const int row = rem / SP - 3, col = rem % SP - 7;
+        const int row = rem / SP - kGridPadR, col = rem % SP - kGridPadC;
         T v{};
         if (row >= 0 && row < S && col >= 0 && col < S)
             v = tab[plane_off[p] + o * S * S + (int64_t)row * S + col];
@@ -159,12 +160,19 @@ void launch_weight_vis(const void* vis, int kind, const float* w, int64_t n, flo
 }
 
 int padded_stride(int smax) {
-    const int need = smax + 14;
+    const int need = smax + 2 * kGridPadC;
+#if GW_GRID_LANES_U == 16
+    for (int sp : {32, 48, 64, 96, 160}) if (need <= sp) return sp;
+    return 288;
+#else
     for (int sp : {24, 32, 48, 80, 144}) if (need <= sp) return sp;
     return 272;
+#endif
 }
 
-int64_t padded_table_elems(int S, int beta, int SP) { return (int64_t)beta * beta * (S + 6) * SP; }
+int64_t padded_table_elems(int S, int beta, int SP) {
+    return (int64_t)beta * beta * (S + 2 * kGridPadR) * SP;
+}
 
 void launch_pad_tables(const void* tab, int kind, const int64_t* plane_off,
                        const int64_t* pplane_off, const int* support, int P, int beta, int SP,

@@ -63,8 +63,10 @@ namespace gw {
 
 namespace {
 
-constexpr int kBlocksU = kGridTileU / 8;                 // 8 (u) x 16 (v) blocks per tile row
-constexpr int kComputeWarps = kBlocksU * (kGridTileV / 16);
+constexpr int kBlockU = kGridLanesU;                      // warp block: kBlockU (u) x kBlockV (v)
+constexpr int kBlockV = 4 * kGridLanesV;
+constexpr int kBlocksU = kGridTileU / kBlockU;            // blocks per tile row
+constexpr int kComputeWarps = kBlocksU * (kGridTileV / kBlockV);
 #ifndef GW_GRID_PRODUCER_WARPS
 #define GW_GRID_PRODUCER_WARPS 4
 #endif
@@ -225,9 +227,9 @@ __device__ __forceinline__ void load_masked(const typename TE::T* __restrict__ t
     const T* p_ = tab + (int)en.x;
     const T z{};
     Kd[0] = (m & 1u) ? __ldg(p_) : z;
-    Kd[1] = (m & 2u) ? __ldg(p_ + 4 * SP) : z;
-    Kd[2] = (m & 4u) ? __ldg(p_ + 8 * SP) : z;
-    Kd[3] = (m & 8u) ? __ldg(p_ + 12 * SP) : z;
+    Kd[1] = (m & 2u) ? __ldg(p_ + kGridLanesV * SP) : z;
+    Kd[2] = (m & 4u) ? __ldg(p_ + 2 * kGridLanesV * SP) : z;
+    Kd[3] = (m & 8u) ? __ldg(p_ + 3 * kGridLanesV * SP) : z;
 }
 
 // Fills the ring with the first R entries of a list.
@@ -377,18 +379,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                         const int S = __ldg(a.support + plane), h = S >> 1;
                         const int64_t slice = __ldg(a.pplane_off + plane) +
                                               ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *
-                                                  (int64_t)(S + 6) * SP;
+                                                  (int64_t)(S + 2 * kGridPadR) * SP;
                         // padded index of the tile origin relative to this record
-                        const int base = (int)slice + (tv0 - rc.kv + h + 3) * SP + (tu0 - rc.ku + h + 7);
+                        const int base = (int)slice + (tv0 - rc.kv + h + kGridPadR) * SP +
+                                         (tu0 - rc.ku + h + kGridPadC);
                         const uint32_t conj = (rc.flags & GW_FLAG_CONJ) ? kConjBit : 0u;
                         // footprint relative to the tile: [ulo, uhi] x [vlo, vhi]
                         const int ulo = rc.ku - h - tu0, uhi = rc.ku + h - tu0;
                         const int vlo = rc.kv - h - tv0, vhi = rc.kv + h - tv0;
-                        const int cu0 = max(0, ulo) >> 3, cu1 = min(kGridTileU - 1, uhi) >> 3;
-                        const int cv0 = max(0, vlo) >> 4, cv1 = min(kGridTileV - 1, vhi) >> 4;
+                        const int cu0 = max(0, ulo) / kBlockU, cu1 = min(kGridTileU - 1, uhi) / kBlockU;
+                        const int cv0 = max(0, vlo) / kBlockV, cv1 = min(kGridTileV - 1, vhi) / kBlockV;
                         for (int cv = cv0; cv <= cv1; ++cv) {
-                            const int j0 = max(0, vlo - 16 * cv) >> 2;
-                            const int j1 = min(15, vhi - 16 * cv) >> 2;
+                            const int j0 = max(0, vlo - kBlockV * cv) / kGridLanesV;
+                            const int j1 = min(kBlockV - 1, vhi - kBlockV * cv) / kGridLanesV;
                             const uint32_t mask = ((2u << j1) - 1u) & ~((1u << j0) - 1u);
                             const uint2 e = make_uint2((uint32_t)base,
                                                        (uint32_t)r | (mask << 20) | conj);
@@ -432,8 +435,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
 #ifdef GW_GRID_SETMAXNREG
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(GW_GRID_SETMAXNREG) : "memory");
 #endif
-    const int bu = (warp % kBlocksU) * 8, bv = (warp / kBlocksU) * 16;
-    const int lu = lane & 7, lv = lane >> 3;
+    const int bu = (warp % kBlocksU) * kBlockU, bv = (warp / kBlocksU) * kBlockV;
+    const int lu = lane % kGridLanesU, lv = lane / kGridLanesU;
     const typename TE::T* __restrict__ tab =
         reinterpret_cast<const typename TE::T*>(a.ptable) + (bv + lv) * SP + bu + lu;
     const int N = a.N;
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
             const int v0 = (ltile / a.ntiles_u) * kGridTileV + bv + lv;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int v = v0 + 4 * j;
+                const int v = v0 + kGridLanesV * j;
 #pragma unroll
                 for (int p = 0; p < NPOL; ++p) {
                     if (u < N && v < N && (acc[j][p].x != 0.f || acc[j][p].y != 0.f)) {
@@ -546,12 +549,21 @@ void launch_sp(const GridArgs& a, int num_sms, cudaStream_t s) {
 template <int NPOL, int TK>
 void launch_t(const GridArgs& a, int num_sms, cudaStream_t s) {
     switch (a.pad_stride) {
+#if GW_GRID_LANES_U == 16
+        case 32: launch_sp<NPOL, 32, TK>(a, num_sms, s); break;
+        case 48: launch_sp<NPOL, 48, TK>(a, num_sms, s); break;
+        case 64: launch_sp<NPOL, 64, TK>(a, num_sms, s); break;
+        case 96: launch_sp<NPOL, 96, TK>(a, num_sms, s); break;
+        case 160: launch_sp<NPOL, 160, TK>(a, num_sms, s); break;
+        default: launch_sp<NPOL, 288, TK>(a, num_sms, s); break;
+#else
         case 24: launch_sp<NPOL, 24, TK>(a, num_sms, s); break;
         case 32: launch_sp<NPOL, 32, TK>(a, num_sms, s); break;
         case 48: launch_sp<NPOL, 48, TK>(a, num_sms, s); break;
         case 80: launch_sp<NPOL, 80, TK>(a, num_sms, s); break;
         case 144: launch_sp<NPOL, 144, TK>(a, num_sms, s); break;
         default: launch_sp<NPOL, 272, TK>(a, num_sms, s); break;
+#endif
     }
 }
 

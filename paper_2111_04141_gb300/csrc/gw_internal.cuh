@@ -21,6 +21,19 @@ constexpr int kTile = 32;             // grid tile side of the degridding binner
 constexpr int kGridTileShiftU = GW_GRID_TILE_SHIFT_U;
 constexpr int kGridTileU = 1 << kGridTileShiftU;   // gridder tile: kGridTileU (u) x 32 (v)
 constexpr int kGridTileV = 32;
+// Gridder lane layout: a compute warp's 32 lanes are kGridLanesU (u) x
+// kGridLanesV (v) grid points, and each lane holds 4 of them kGridLanesV
+// rows apart, so a warp owns a kGridLanesU x 4 kGridLanesV block.  The padded
+// tables carry kGridLanesV - 1 zero rows above and below each slice and at
+// least kGridLanesU - 1 zero columns on each side (the lanes of a loaded slot
+// reach that far past the footprint).
+#ifndef GW_GRID_LANES_U
+#define GW_GRID_LANES_U 8
+#endif
+constexpr int kGridLanesU = GW_GRID_LANES_U;
+constexpr int kGridLanesV = 32 / kGridLanesU;
+constexpr int kGridPadR = kGridLanesV - 1;
+constexpr int kGridPadC = kGridLanesU - 1;
 constexpr int kItemMax = 1024;        // default max bin entries per work item
 constexpr int kItemMin = 64;          // smallest work-item size a plan may be tuned to
 constexpr double kQLimit = 1073741824.0;  // 2^30: |q| bound for a representable record
