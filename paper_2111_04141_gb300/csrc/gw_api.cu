@@ -930,6 +930,11 @@ static gw_status ensure_host_pipe(gw_plan p, int64_t rows, int nchan) {
     return GW_OK;
 }
 
+#ifndef GW_HOST_FIRST_DIV
+#define GW_HOST_FIRST_DIV 8
+#endif
+static constexpr int64_t kHostFirstDiv = GW_HOST_FIRST_DIV;
+
 gw_status gw_grid_vis_host(gw_plan p, const double* uvw_h, const double* freq_h, int64_t nrow,
                            int32_t nchan, const void* vis_h, const float* weight_h, void* grid,
                            int64_t* n_dropped, void* cuda_stream) {
@@ -943,13 +948,17 @@ gw_status gw_grid_vis_host(gw_plan p, const double* uvw_h, const double* freq_h,
     if (nrow == 0 || nchan == 0) return finish_dropped(p, n_dropped, s);
     const int npol = p->desc.npol;
     const size_t vb = dtype_bytes(p->desc.vis_dtype);
-    // pipeline step: half of the rows or the plan's chunk, whichever is
-    // smaller.  k steps leave 1/k of the copy time exposed and add k - 1
-    // gridding passes (commits, launch tails); two measured best on the
-    // 8.26M-visibility batch (13.34 ms vs 13.54 / 13.57 / 13.67 for 3 / 4 / 1)
-    int64_t rows = std::min(rows_per_chunk(p, nchan), (nrow + 1) / 2);
-    rows = std::max<int64_t>(rows, 1);
-    st = ensure_host_pipe(p, rows, nchan);
+    // pipeline steps: a short first step (1/kHostFirstDiv of the rows), whose
+    // copy is the only one left exposed, then steps of the rest up to the
+    // plan's chunk; the second step's copy overlaps the first step's
+    // gridding.  Each step beyond one adds a gridding pass (commits, launch
+    // tails).  On the 8.26M-visibility batch, with the grid's read-back
+    // overlapping the next call: first step 1/2 / 1/4 / 1/8 / 1/16 of the rows
+    // 10.2-10.3 / 9.7 / 9.6 / 10.0 ms per call.
+    const int64_t rpc = rows_per_chunk(p, nchan);
+    const int64_t first = std::max<int64_t>(1, std::min(rpc, (nrow + kHostFirstDiv - 1) / kHostFirstDiv));
+    const int64_t rows = std::max<int64_t>(1, std::min(rpc, nrow - first));
+    st = ensure_host_pipe(p, std::max(first, rows), nchan);
     if (st != GW_OK) return st;
     e = cudaMemcpyAsync(p->h_freq, freq_h, sizeof(double) * nchan, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "copying frequencies");
@@ -958,8 +967,8 @@ gw_status gw_grid_vis_host(gw_plan p, const double* uvw_h, const double* freq_h,
     if (e == cudaSuccess) e = cudaEventRecord(p->h_free[1], s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     int b = 0;
-    for (int64_t r0 = 0; r0 < nrow; r0 += rows, b ^= 1) {
-        const int64_t nr = std::min(rows, nrow - r0);
+    for (int64_t r0 = 0; r0 < nrow; r0 += (r0 == 0 ? first : rows), b ^= 1) {
+        const int64_t nr = std::min(r0 == 0 ? first : rows, nrow - r0);
         const int64_t nv = nr * nchan;
         // copy stream: wait until set b is free, then copy the step's inputs
         e = cudaStreamWaitEvent(p->h_copy, p->h_free[b], 0);
