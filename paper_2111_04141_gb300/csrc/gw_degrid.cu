@@ -6,18 +6,20 @@
 // and the result is written in the plan's visibility kind.
 //
 // Two kernels:
-// * k_degrid_staged (used by gw_degrid_vis): a CTA takes a work item of one
-//   16 x 16 centre tile, copies the tile's grid region (the tile plus the
-//   plan's largest half-support on every side, one plane per polarisation) into
-//   shared memory once, and serves all records of the item from it, so the
-//   grid is read from L2/HBM about once per tile instead of once per tap.
-//   One warp per record: lanes take consecutive taps of the S x S footprint
-//   (flattened, so every lane is busy), multiply-accumulate all polarisations
-//   against the kernel slice (read coalesced from the table, one step ahead)
-//   and reduce with warp shuffles.  The region fills most of an SM's shared
-//   memory, so a CTA is 32 warps: the table loads from L2 are the latency to
-//   hide, and planes per polarisation keep each lane's grid reads
-//   conflict-light (8-byte stride).
+// * k_degrid_staged (used by gw_degrid_vis): one CTA of 24 warps per SM
+//   serves chunks of work items (at most 1,024 records centred in one 16 x 16
+//   tile).  Warps 0-3 load the records' metadata (id, kernel slice, centre,
+//   support) into one of two shared buffers, the next chunk's while all
+//   warps compute the current one.  The CTA stages the tile's grid region
+//   (the tile plus the chunk's largest half-support on every side) in
+//   shared memory once, as polarisation pairs, at a row pitch padded to the
+//   support residue (mod 8) that carries most of the item's taps, and serves
+//   all of the item's records from it, so the grid is read from L2/HBM
+//   about once per tile instead of once per tap.  Warps claim records one at
+//   a time, wide supports first.  One warp per record: lanes take
+//   consecutive taps of the S x S footprint (flattened, so every lane is
+//   busy), with kernel values loaded four steps ahead, packed FP32x2 FMAs
+//   into K.re G and K.im G sums, and a reduce-scatter over the lanes.
 // * k_degrid (the fallback when the region does not fit in shared memory,
 //   and the allocation-free entry point): the same per-record warp, reading
 //   the grid through L1/L2, records visited in 32 x 32 centre-tile order.

@@ -14,7 +14,9 @@
 // * Sixteen compute warps each own an 8 (u) x 16 (v) block; lane (lu, lv)
 //   holds the points (lu, lv + 4 j), j = 0..3 ("slots" of 8 x 4 points), for
 //   every polarisation.  Four slots per warp amortise each record's staged
-//   visibility over up to 4 x 32 points.
+//   visibility over up to 4 x 32 points.  (The lane layout is a compile-time
+//   choice, kGridLanesU x kGridLanesV = 8 x 4 or 16 x 2; the text describes
+//   the default.)
 // * The work is bound by the gathers of kernel values from L2 (each a
 //   4-row x 64-byte window of a table slice per slot) and by the FP32 pipe,
 //   so the design keeps many gathers in flight and many warps issuing: 20
@@ -30,19 +32,21 @@
 //   tile and the slots its rows meet (one 64-bit entry).  Compute warps
 //   therefore only see records that touch them.
 // * Hand-over through mbarriers: a compute warp waits only for the batch it
-//   needs and releases it when done, so the eight compute warps run
-//   independently; the producers wait until all eight have released a
+//   needs and releases it when done, so the sixteen compute warps run
+//   independently; the producers wait until all of them have released a
 //   buffer before refilling it.  Every wait is bounded: a wait that gives up
 //   sets the plan's device status word and the kernel returns.
 // * The producers pad every warp's list to a multiple of R and append R more
 //   null entries (no loads, the all-zero visibility row), so the compute loop
 //   has no tail tests: the kernel values of entry i + R are loaded into the
 //   registers entry i has just used, and the last pass over a batch loads the
-//   first entries of the next batch (the ring never drains between batches).  An entry loads the slots its record
+//   first entries of the next batch (the ring never drains between batches).
+//   An entry loads the slots its record
 //   meets and zeros for the others, and always updates all four slots (one
 //   loop body, no per-entry jump: the code stays small at ring depth R).
-// * Kernel values come from zero-padded slices (7 zero columns and 3 zero
-//   rows around each S x S slice, one compile-time row stride per plan), so
+// * Kernel values come from zero-padded slices (kGridPadC = 7 zero columns
+//   and kGridPadR = 3 zero rows around each S x S slice, one compile-time
+//   row stride per plan), so
 //   lanes outside the footprint read zeros and slot addresses are immediate
 //   offsets.
 // * Per tap and polarisation the update is two packed FP32x2 FMAs (Blackwell
