@@ -40,8 +40,8 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
-GRID_TRAFFIC = {"sha256": "908fb0560eaeb99e03c3c6ad51084a14c99c2020dc8e675b12f2cba95953ae68",
-                "bytes_per_launch": 0.963030e9 + 0.264580e9,
+GRID_TRAFFIC = {"sha256": "12be6ee91f495fc0707e4b27b4e542edd48511d3602e2ad03820cb8c80701828",
+                "bytes_per_launch": 0.963445e9 + 0.264317e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
 
 
