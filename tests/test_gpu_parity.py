@@ -284,12 +284,15 @@ def test_degrid_matches_oracle(gw, case):
     assert rel_l2(got, ref) <= TOL_GRID, name
 
 
-def test_degrid_long_items_in_chunks(gw):
+@pytest.mark.parametrize("npol", [1, 3, 4])
+def test_degrid_long_items_in_chunks(gw, npol):
     """Tiles holding more records than the staged degridder's metadata buffer
     (1,024) are served in several chunks from one region: with one work item
-    per tile the result matches the oracle and the default item size."""
-    obs = syn.small_case(n_ant=12, n_times=64, n_chan=4, npol=4, grid_n=64, s_min=7, s_max=15,
-                         n_w=4, diameter_m=400.0, seed=11)
+    per tile the result matches the oracle and the default item size, for
+    region layouts of pairs only, pairs and a single plane, and a single
+    plane."""
+    obs = syn.small_case(n_ant=12, n_times=64, n_chan=4, npol=npol, grid_n=64, s_min=7,
+                         s_max=15, n_w=4, diameter_m=400.0, seed=11)
     prm = Params(**obs.plan_kwargs())
     rng = np.random.default_rng(22)
     N = prm.grid_n
