@@ -795,14 +795,10 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
         const int64_t nr = std::min(rpc, nrow - r0);
         const int64_t v0 = r0 * nchan;
         if (use_direct(p, nr * nchan)) {
-            // small input: index, then direct gridding (weights applied in the kernel)
-            {
-                StageTimer t(p, kStIndex, s);
-                launch_index(uvw_m + 3 * r0, freq_hz, nr, nchan, p->ip, p->sc.rec, p->sc.dropped,
-                             s);
-            }
+            // small input: one launch that indexes and grids (weights applied
+            // in the kernel)
             GridArgs a;
-            a.rec = p->sc.rec;
+            a.rec = nullptr;
             a.vis = static_cast<const char*>(vis) + (size_t)v0 * npol * vb;
             a.vis_kind = vk;
             a.weight = weight ? weight + v0 * npol : nullptr;
@@ -817,8 +813,9 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
             a.beta = p->desc.oversample;
             {
                 StageTimer t(p, kStGrid, s);
+                const DirectIndex di{uvw_m + 3 * r0, freq_hz, nr, nchan, p->ip, p->sc.dropped};
                 launch_grid_direct(a, p->table16 ? (const void*)p->table16 : (const void*)p->table,
-                                   nr * nchan, p->sc.work, s);
+                                   di, p->sc.work, s);
             }
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(e, "grid launch");

@@ -40,26 +40,57 @@ __global__ void k_weight_vis(const void* __restrict__ vis, int kind, const float
     }
 }
 
-// Direct gridding for small inputs: no binning, one warp per record, lanes
-// over the flattened S x S taps of its (unpadded) kernel slice, one global
-// vector atomic per tap and polarisation.  Two launches per call (index and
-// this) instead of the binned path's six, which is what small jobs pay for.
-// Also accumulates the work counters the binner would (valid records, sum
-// of S^2).
+// Direct gridding for small inputs: no binning, one warp per visibility,
+// whose lane 0 computes the visibility's index record (the same bit-exact
+// FP64 sequence as the index stage) and broadcasts it, then spreads it over
+// the flattened S x S taps of its (unpadded) kernel slice with one global
+// vector atomic per tap and polarisation.  One launch per call instead of
+// the binned path's seven, which is what small jobs pay for.  Counts the
+// dropped visibilities and accumulates the work counters the binner would
+// (valid records, sum of S^2).
+constexpr int kDirectChanCache = 256;   // channel factors kept in shared memory
+
 template <int NPOL, int TK>
 __global__ void __launch_bounds__(256) k_grid_direct(GridArgs a, const void* __restrict__ table,
-                                                     int64_t nvis,
+                                                     DirectIndex di,
                                                      unsigned long long* __restrict__ work) {
     using TE = TabElem<TK>;
+    // [P - 1] w-plane thresholds as int64 bit patterns and [nc] channel
+    // factors f / c0, as the index stage builds them
+    extern __shared__ long long sh_idx[];
+    const int nthr = di.p.P > 1 ? di.p.P - 1 : 0;
+    const int nc = min(di.nchan, kDirectChanCache);
+    long long* thr = sh_idx;
+    double* fc = reinterpret_cast<double*>(sh_idx + nthr);
+    for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr[j] = wplane_threshold(j, di.p);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) fc[c] = __ddiv_rn(__ldg(di.freq + c), kC0);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int hb = a.beta / 2, N = a.N;
-    unsigned long long n_valid = 0, n_taps = 0;
+    const int64_t nvis = di.nrow * (int64_t)di.nchan;
+    unsigned long long n_valid = 0, n_taps = 0, n_drop = 0;
     for (int64_t i = warp0; i < nvis; i += nwarps) {
-        int4 rv = __ldg(reinterpret_cast<const int4*>(a.rec) + i);
-        const gw_index_rec rc = *reinterpret_cast<gw_index_rec*>(&rv);
-        if (!(rc.flags & GW_FLAG_VALID)) continue;
+        int4 rv = make_int4(0, 0, 0, 0);
+        if (lane == 0) {
+            const int64_t row = i / di.nchan;
+            const int chan = (int)(i - row * di.nchan);
+            const double f_c = chan < nc ? fc[chan] : __ddiv_rn(__ldg(di.freq + chan), kC0);
+            gw_index_rec r;
+            index_record(__ldg(di.uvw + 3 * row + 0), __ldg(di.uvw + 3 * row + 1),
+                         __ldg(di.uvw + 3 * row + 2), f_c, di.p, thr, r);
+            rv = *reinterpret_cast<const int4*>(&r);
+        }
+        rv.x = __shfl_sync(0xffffffffu, rv.x, 0);
+        rv.y = __shfl_sync(0xffffffffu, rv.y, 0);
+        rv.z = __shfl_sync(0xffffffffu, rv.z, 0);
+        rv.w = __shfl_sync(0xffffffffu, rv.w, 0);
+        const gw_index_rec rc = *reinterpret_cast<const gw_index_rec*>(&rv);
+        if (!(rc.flags & GW_FLAG_VALID)) {
+            if (lane == 0) ++n_drop;
+            continue;
+        }
         const int plane = a.layer_tiles ? 0 : rc.plane;
         const int S = __ldg(a.support + plane), h = S >> 1;
         if (lane == 0) {
@@ -113,40 +144,43 @@ __global__ void __launch_bounds__(256) k_grid_direct(GridArgs a, const void* __r
             }
         }
     }
-    for (int d = 16; d > 0; d >>= 1) {
-        n_valid += __shfl_down_sync(0xffffffffu, n_valid, d);
-        n_taps += __shfl_down_sync(0xffffffffu, n_taps, d);
-    }
-    if (lane == 0 && n_valid) {
-        atomicAdd(work, n_valid);
-        atomicAdd(work + 1, n_taps);
+    // counts are held by lane 0 of each warp
+    if (lane == 0) {
+        if (n_valid) {
+            atomicAdd(work, n_valid);
+            atomicAdd(work + 1, n_taps);
+        }
+        if (n_drop) atomicAdd(di.dropped, n_drop);
     }
 }
 
 template <int TK>
-void launch_direct_k(const GridArgs& a, const void* table, int64_t nvis,
+void launch_direct_k(const GridArgs& a, const void* table, const DirectIndex& di,
                      unsigned long long* work, cudaStream_t s) {
+    const int64_t nvis = di.nrow * (int64_t)di.nchan;
     int64_t blocks = (nvis * 32 + 255) / 256;
     if (blocks > current_sm_count() * 8) blocks = current_sm_count() * 8;
     if (blocks < 1) blocks = 1;
+    const size_t smem = sizeof(long long) * (size_t)(di.p.P > 1 ? di.p.P - 1 : 0) +
+                        sizeof(double) * (size_t)std::min(di.nchan, kDirectChanCache);
     switch (a.npol) {
-        case 1: k_grid_direct<1, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
-        case 2: k_grid_direct<2, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
-        case 3: k_grid_direct<3, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
-        default: k_grid_direct<4, TK><<<(unsigned)blocks, 256, 0, s>>>(a, table, nvis, work); break;
+        case 1: k_grid_direct<1, TK><<<(unsigned)blocks, 256, smem, s>>>(a, table, di, work); break;
+        case 2: k_grid_direct<2, TK><<<(unsigned)blocks, 256, smem, s>>>(a, table, di, work); break;
+        case 3: k_grid_direct<3, TK><<<(unsigned)blocks, 256, smem, s>>>(a, table, di, work); break;
+        default: k_grid_direct<4, TK><<<(unsigned)blocks, 256, smem, s>>>(a, table, di, work); break;
     }
     note_launch();
 }
 
 }  // namespace
 
-void launch_grid_direct(const GridArgs& a, const void* table, int64_t nvis,
+void launch_grid_direct(const GridArgs& a, const void* table, const DirectIndex& di,
                         unsigned long long* work, cudaStream_t s) {
-    if (nvis <= 0) return;
+    if (di.nrow <= 0 || di.nchan <= 0) return;
     switch (a.table_kind) {
-        case GW_BF16X2: launch_direct_k<GW_BF16X2>(a, table, nvis, work, s); break;
-        case GW_F16X2: launch_direct_k<GW_F16X2>(a, table, nvis, work, s); break;
-        default: launch_direct_k<GW_C64>(a, table, nvis, work, s); break;
+        case GW_BF16X2: launch_direct_k<GW_BF16X2>(a, table, di, work, s); break;
+        case GW_F16X2: launch_direct_k<GW_F16X2>(a, table, di, work, s); break;
+        default: launch_direct_k<GW_C64>(a, table, di, work, s); break;
     }
 }
 

@@ -19,25 +19,7 @@ namespace gw {
 
 namespace {
 
-struct AxisIdx {
-    long long k, o;
-    bool ok;
-};
-
 constexpr int kChanCache = 1024;   // channel factors kept in shared memory
-
-__device__ __forceinline__ AxisIdx axis_index(double coord_m, double sc, const IndexParams& p) {
-    // u_lambda = u * (f / c0) ; x = u_lambda * L + N/2 ; q = floor(beta * x + 0.5)
-    const double lam = __dmul_rn(coord_m, sc);
-    const double x = __dadd_rn(__dmul_rn(lam, p.L), p.halfN);
-    const double q = floor(__dadd_rn(__dmul_rn(p.beta_d, x), 0.5));
-    AxisIdx r;
-    r.ok = isfinite(q) && fabs(q) < kQLimit;
-    const long long qi = r.ok ? (long long)q : 0LL;
-    r.k = floor_div(qi + p.beta / 2, p.beta);
-    r.o = qi - r.k * p.beta;
-    return r;
-}
 
 __global__ void k_index(const double* __restrict__ uvw, const double* __restrict__ freq,
                         int64_t nrow, const int64_t* __restrict__ d_nrow, int nchan,
@@ -52,10 +34,7 @@ __global__ void k_index(const double* __restrict__ uvw, const double* __restrict
     double* sc = sh;
     long long* thr = reinterpret_cast<long long*>(sh + nc);
     for (int c = threadIdx.x; c < nc; c += blockDim.x) sc[c] = __ddiv_rn(__ldg(freq + c), kC0);
-    for (int j = threadIdx.x; j < nthr; j += blockDim.x) {
-        const double t = __ddiv_rn((double)j + 0.5, p.Pm1_d);      // (j + 1) - 1/2, exact
-        thr[j] = __double_as_longlong(__dmul_rn(__dmul_rn(t, t), p.wmax));
-    }
+    for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr[j] = wplane_threshold(j, p);
     __syncthreads();
     if (d_nrow) nrow = min(nrow, *d_nrow);     // row count read on the device
     const int64_t nvis = nrow * (int64_t)nchan;
@@ -69,52 +48,10 @@ __global__ void k_index(const double* __restrict__ uvw, const double* __restrict
     const int schan = (int)(stride - srow * nchan);
     for (; i < nvis; i += stride) {
         const double f_c = chan < nc ? sc[chan] : __ddiv_rn(__ldg(freq + chan), kC0);
-        const double u = __ldg(uvw + 3 * row + 0);
-        const double v = __ldg(uvw + 3 * row + 1);
-        const AxisIdx au = axis_index(u, f_c, p);
-        const AxisIdx av = axis_index(v, f_c, p);
-        int plane = 0;
-        bool conj = false, okw = true;
-        if (p.P > 1) {
-            const double wl = __dmul_rn(__ldg(uvw + 3 * row + 2), f_c);
-            okw = isfinite(wl);
-            if (okw) {
-                // number of thresholds <= |w| (first index with thr > |w|)
-                const long long a = __double_as_longlong(fabs(wl));
-                int lo = 0, hi = nthr;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (thr[mid] <= a) lo = mid + 1; else hi = mid;
-                }
-                plane = lo;
-            }
-            conj = wl < 0.0;
-        } else if (p.nlayers > 0) {
-            // w-stacking layer: nearest of w_l = wmin + l dw, clamped to the layers
-            const double wl = __dmul_rn(__ldg(uvw + 3 * row + 2), f_c);
-            const double t = floor(__dadd_rn(__ddiv_rn(__dsub_rn(wl, p.wmin), p.dw), 0.5));
-            okw = isfinite(t);
-            plane = okw ? (int)fmin(fmax(t, 0.0), (double)(p.nlayers - 1)) : 0;
-        }
-        const int h = plane_support(plane, p.P, p.smin, p.smax) / 2;
-        const bool inside = (au.k - h >= 0) && (au.k + h <= p.N - 1) &&
-                            (av.k - h >= 0) && (av.k + h <= p.N - 1);
-        const bool valid = au.ok && av.ok && okw && inside;
         gw_index_rec r;
-        if (valid) {
-            r.ku = (int32_t)au.k;
-            r.kv = (int32_t)av.k;
-            r.ou = (int16_t)au.o;
-            r.ov = (int16_t)av.o;
-            r.plane = (int16_t)plane;
-            r.flags = (uint16_t)(GW_FLAG_VALID | (conj ? GW_FLAG_CONJ : 0u));
-        } else {
-            r.ku = r.kv = 0;
-            r.ou = r.ov = 0;
-            r.plane = 0;
-            r.flags = 0;
+        if (!index_record(__ldg(uvw + 3 * row + 0), __ldg(uvw + 3 * row + 1),
+                          __ldg(uvw + 3 * row + 2), f_c, p, thr, r))
             ++my_drops;
-        }
         reinterpret_cast<int4*>(out)[i] = *reinterpret_cast<const int4*>(&r);
         row += srow;
         chan += schan;

@@ -116,6 +116,83 @@ struct IndexParams {
     double wmin = 0.0, dw = 1.0;
 };
 
+// The index record of one visibility (Section 3.3.5 pre-processing, Section
+// 2.3.6 NN lookup, Section 2.3.1 bounded records): every floating-point step
+// an explicitly rounded FP64 intrinsic, so the result is bit-exact with any
+// IEEE-754 implementation of the same sequence.  f_c = f / c0 of the
+// visibility's channel; thr[0 .. P - 2] are the w-plane thresholds
+// ((j + 1/2) / (P - 1))^2 w_max as int64 bit patterns (non-negative finite
+// doubles order like their bits).  Returns false (and an all-zero record)
+// for a dropped visibility.
+struct IndexAxis {
+    long long k, o;
+    bool ok;
+};
+__device__ __forceinline__ IndexAxis index_axis(double coord_m, double f_c, const IndexParams& p) {
+    // u_lambda = u * (f / c0) ; x = u_lambda * L + N/2 ; q = floor(beta * x + 0.5)
+    const double lam = __dmul_rn(coord_m, f_c);
+    const double x = __dadd_rn(__dmul_rn(lam, p.L), p.halfN);
+    const double q = floor(__dadd_rn(__dmul_rn(p.beta_d, x), 0.5));
+    IndexAxis r;
+    r.ok = isfinite(q) && fabs(q) < kQLimit;
+    const long long qi = r.ok ? (long long)q : 0LL;
+    r.k = floor_div(qi + p.beta / 2, p.beta);
+    r.o = qi - r.k * p.beta;
+    return r;
+}
+__device__ __forceinline__ bool index_record(double u, double v, double w, double f_c,
+                                             const IndexParams& p, const long long* thr,
+                                             gw_index_rec& r) {
+    const IndexAxis au = index_axis(u, f_c, p);
+    const IndexAxis av = index_axis(v, f_c, p);
+    int plane = 0;
+    bool conj = false, okw = true;
+    if (p.P > 1) {
+        const double wl = __dmul_rn(w, f_c);
+        okw = isfinite(wl);
+        if (okw) {
+            // number of thresholds <= |w| (first index with thr > |w|)
+            const long long a = __double_as_longlong(fabs(wl));
+            int lo = 0, hi = p.P - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (thr[mid] <= a) lo = mid + 1; else hi = mid;
+            }
+            plane = lo;
+        }
+        conj = wl < 0.0;
+    } else if (p.nlayers > 0) {
+        // w-stacking layer: nearest of w_l = wmin + l dw, clamped to the layers
+        const double wl = __dmul_rn(w, f_c);
+        const double t = floor(__dadd_rn(__ddiv_rn(__dsub_rn(wl, p.wmin), p.dw), 0.5));
+        okw = isfinite(t);
+        plane = okw ? (int)fmin(fmax(t, 0.0), (double)(p.nlayers - 1)) : 0;
+    }
+    const int h = plane_support(plane, p.P, p.smin, p.smax) / 2;
+    const bool inside = (au.k - h >= 0) && (au.k + h <= p.N - 1) &&
+                        (av.k - h >= 0) && (av.k + h <= p.N - 1);
+    const bool valid = au.ok && av.ok && okw && inside;
+    if (valid) {
+        r.ku = (int32_t)au.k;
+        r.kv = (int32_t)av.k;
+        r.ou = (int16_t)au.o;
+        r.ov = (int16_t)av.o;
+        r.plane = (int16_t)plane;
+        r.flags = (uint16_t)(GW_FLAG_VALID | (conj ? GW_FLAG_CONJ : 0u));
+    } else {
+        r.ku = r.kv = 0;
+        r.ou = r.ov = 0;
+        r.plane = 0;
+        r.flags = 0;
+    }
+    return valid;
+}
+// Threshold j of the w-plane search (as its int64 bit pattern).
+__device__ __forceinline__ long long wplane_threshold(int j, const IndexParams& p) {
+    const double t = __ddiv_rn((double)j + 0.5, p.Pm1_d);      // (j + 1) - 1/2, exact
+    return __double_as_longlong(__dmul_rn(__dmul_rn(t, t), p.wmax));
+}
+
 // Work item of the gridder: a contiguous run of one tile's bin.
 struct Item {
     int32_t tile;
@@ -248,10 +325,20 @@ struct GridArgs {
     int64_t layer_stride = 0;
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
-// Direct gridding of nvis index records (no bins): `table` is the unpadded
-// table of kind a.table_kind; adds to work[0] (valid records) and work[1]
-// (sum of S_p^2).  For inputs small enough that launches dominate.
-void launch_grid_direct(const GridArgs& a, const void* table, int64_t nvis,
+// Direct gridding (no bins) of nrow x nchan visibilities, each warp
+// computing its visibility's index record: `table` is the unpadded table of
+// kind a.table_kind; adds the dropped visibilities to *dropped, and to
+// work[0] (valid records) and work[1] (sum of S_p^2).  For inputs small
+// enough that launches dominate.
+struct DirectIndex {
+    const double* uvw;       // [nrow][3] metres (device)
+    const double* freq;      // [nchan] Hz (device)
+    int64_t nrow;
+    int nchan;
+    IndexParams p;
+    unsigned long long* dropped;
+};
+void launch_grid_direct(const GridArgs& a, const void* table, const DirectIndex& di,
                         unsigned long long* work, cudaStream_t s);
 // Direct gridding is chosen for at most this many visibilities per chunk and
 // this many tap updates (visibilities x S_max^2 x npol).
