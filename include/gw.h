@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 6
+#define GW_API_VERSION 7
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -54,7 +54,8 @@ typedef enum {
     GW_ECUDA = -3,         /* a CUDA runtime call failed (see gw_last_error) */
     GW_ETIMEDOUT = -4,     /* a bounded device-side wait gave up */
     GW_EUNSUPPORTED = -5,  /* valid request this build does not implement */
-    GW_EDEVICE = -6        /* called with a different current device than the plan's */
+    GW_EDEVICE = -6,       /* called with a different current device than the plan's */
+    GW_EBOUNDS = -7        /* a device-side bounds check of the debug build failed */
 } gw_status;
 
 /* Storage type of visibilities and of the kernel tables.  The 16-bit kinds
@@ -189,9 +190,12 @@ int64_t gw_debug_live_bytes(void);
  * thesis counterpart): GW_ETIMEDOUT if, since the last check, a bounded
  * device-side wait of the gridding kernel gave up (its producer / consumer
  * hand-over waits at most about two seconds; the kernel then returns and
- * that call's grid is incomplete), else GW_OK.  The word is cleared when
- * read.  Calls that return n_dropped check it the same way.
- * Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA, GW_ETIMEDOUT. */
+ * that call's grid is incomplete); GW_EBOUNDS if a kernel of the debug build
+ * (libgw_debug.so, compiled with GW_DEBUG_BOUNDS) found an index outside
+ * its buffer (the access is skipped, so that call's result is wrong but
+ * nothing faults); else GW_OK.  The word is cleared when read.  Calls that
+ * return n_dropped check it the same way.
+ * Errors: GW_EINVAL, GW_EDEVICE, GW_ECUDA, GW_ETIMEDOUT, GW_EBOUNDS. */
 gw_status gw_plan_device_status(gw_plan plan, void* cuda_stream);
 
 /* Free all device memory of the plan.  NULL is accepted.  The caller must

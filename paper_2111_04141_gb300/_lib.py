@@ -9,7 +9,10 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgw.so")
+# GW_DEBUG_BOUNDS=1 selects the build with device-side bounds checks
+# (build(debug=True)); the default is the release library
+LIB_PATH = os.path.join(_HERE, "libgw_debug.so" if os.environ.get("GW_DEBUG_BOUNDS") == "1"
+                        else "libgw.so")
 
 GW_C64, GW_BF16X2, GW_F16X2 = 0, 1, 2
 GW_FLAG_VALID, GW_FLAG_CONJ = 1, 2

@@ -399,6 +399,9 @@ gw_status read_device_status(gw_plan p) {
     if (st == 0) return GW_OK;
     e = cudaMemset(p->sc.counters + 1, 0, sizeof st);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");
+    if (st & kStatusBounds)
+        return fail(GW_EBOUNDS, "a device bounds check failed (status 0x%x); the results of the "
+                    "calls since the last check are wrong", st);
     return fail(GW_ETIMEDOUT, "a bounded device wait gave up (status 0x%x); the results of the "
                 "calls since the last check are incomplete", st);
 }
@@ -441,6 +444,7 @@ const char* gw_strerror(gw_status s) {
         case GW_ETIMEDOUT: return "device wait timed out";
         case GW_EUNSUPPORTED: return "unsupported";
         case GW_EDEVICE: return "wrong current device";
+        case GW_EBOUNDS: return "device bounds check failed";
     }
     return "unknown status";
 }
@@ -813,6 +817,8 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
             a.beta = p->desc.oversample;
             {
                 StageTimer t(p, kStGrid, s);
+                a.queue = p->sc.counters;
+                a.table_elems = p->plane_off.back();
                 const DirectIndex di{uvw_m + 3 * r0, freq_hz, nr, nchan, p->ip, p->sc.dropped};
                 launch_grid_direct(a, p->table16 ? (const void*)p->table16 : (const void*)p->table,
                                    di, p->sc.work, s);
@@ -858,6 +864,7 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
         a.beta = p->desc.oversample;
         a.ntiles_u = p->geom_grid.ntu;
         a.pad_stride = p->pad_stride;
+        a.ptable_elems = p->pplane_off.back();
         {
             StageTimer t(p, kStGrid, s);
             launch_grid(a, p->num_sms, s);
@@ -1112,6 +1119,7 @@ gw_status gw_grid_vis_compressed(gw_plan p, const double* uvw_m, const double* f
         a.beta = p->desc.oversample;
         a.ntiles_u = p->geom_grid.ntu;
         a.pad_stride = p->pad_stride;
+        a.ptable_elems = p->pplane_off.back();
         {
             StageTimer t(p, kStGrid, s);
             launch_grid(a, p->num_sms, s);
@@ -1236,6 +1244,7 @@ gw_status gw_grid_vis_wstack(gw_plan p, const double* uvw_m, const double* freq_
         a.beta = p->desc.oversample;
         a.ntiles_u = g.ntu;
         a.pad_stride = p->pad_stride;
+        a.ptable_elems = p->pplane_off.back();
         a.layer_tiles = g.layer_tiles;
         a.layer_stride = (int64_t)npol * p->desc.grid_n * p->desc.grid_n;
         {
@@ -1438,11 +1447,13 @@ gw_status gw_degrid_vis(gw_plan p, const double* uvw_m, const double* freq_hz, i
         a.table_kind = p->desc.table_dtype;
         a.vis_kind = p->desc.vis_dtype;
         a.table_inv = p->table_inv;
+        a.table_elems = p->plane_off.back() + kTableSlack;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = p->sc.entries;
         a.n_entries = p->sc.offsets + geom.ntu * geom.ntv;
         a.vis_out = out;
+        a.vis_count = nr * (int64_t)nchan;
         a.N = p->desc.grid_n;
         a.npol = npol;
         a.beta = p->desc.oversample;
@@ -1514,6 +1525,7 @@ gw_status gw_grid_vis_devcount(gw_plan p, const double* uvw_m, const double* fre
     a.beta = p->desc.oversample;
     a.ntiles_u = p->geom_grid.ntu;
     a.pad_stride = p->pad_stride;
+    a.ptable_elems = p->pplane_off.back();
     launch_grid(a, p->num_sms, s);
     e = cudaGetLastError();
     return e == cudaSuccess ? GW_OK : cuda_fail(e, "grid launch");
@@ -1593,6 +1605,7 @@ gw_status gw_grid_vis_devcount_readback(gw_plan p, const double* uvw_m, const do
     a.beta = p->desc.oversample;
     a.ntiles_u = ntu;
     a.pad_stride = p->pad_stride;
+    a.ptable_elems = p->pplane_off.back();
     // band b: tile rows [b ntv / nb, (b + 1) ntv / nb), its work items the
     // contiguous run item_off[first tile] .. item_off[first tile of the next
     // band]; its grid rows are final once its launch ends (no other band's
@@ -1643,11 +1656,13 @@ gw_status gw_degrid_vis_devcount(gw_plan p, const double* uvw_m, const double* f
     a.table_kind = p->desc.table_dtype;
     a.vis_kind = vk;
     a.table_inv = p->table_inv;
+    a.table_elems = p->plane_off.back() + kTableSlack;
     a.plane_off = p->d_plane_off;
     a.support = p->d_support;
     a.entries = p->sc.entries;
     a.n_entries = p->sc.offsets + geom.ntu * geom.ntv;
     a.vis_out = vis_out;
+    a.vis_count = max_nrow * (int64_t)nchan;
     a.N = p->desc.grid_n;
     a.npol = npol;
     a.beta = p->desc.oversample;
@@ -1700,11 +1715,13 @@ gw_status gw_degrid_vis_static(gw_plan p, const double* uvw_m, const double* fre
         a.table_kind = p->desc.table_dtype;
         a.vis_kind = p->desc.vis_dtype;
         a.table_inv = p->table_inv;
+        a.table_elems = p->plane_off.back() + kTableSlack;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
         a.entries = sc.entries;
         a.n_entries = sc.offsets + g.ntu * g.ntv;
         a.vis_out = vis_out;
+        a.vis_count = nrow * (int64_t)nchan;
         a.N = p->desc.grid_n;
         a.npol = p->desc.npol;
         a.beta = p->desc.oversample;

@@ -218,10 +218,31 @@ __global__ void __launch_bounds__(kStagedThreads) k_degrid_staged(DegridArgs a, 
                     const int S = __ldg(a.support + rc.plane), h = S >> 1;
                     const int64_t kofs = __ldg(a.plane_off + rc.plane) +
                                          ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
-                    const uint32_t rel = (uint32_t)(rc.ku - tx0) | (uint32_t)(rc.kv - ty0) << 8;
-                    const uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
+                    uint32_t rel = (uint32_t)(rc.ku - tx0) | (uint32_t)(rc.kv - ty0) << 8;
+                    uint32_t w = (uint32_t)S | ((rc.flags & GW_FLAG_CONJ) ? 1u << 16 : 0u);
+#ifdef GW_DEBUG_BOUNDS
+                    // the record's slice, centre tile, region and output row: a
+                    // record that fails is replaced by a 1 x 1 one at the
+                    // table's start, centred in the tile
+                    const bool ok =
+                        (a.table_elems == 0 || (kofs >= 0 && kofs + (int64_t)S * S <= a.table_elems)) &&
+                        rc.ku - tx0 >= 0 && rc.ku - tx0 < kStagedTile && rc.kv - ty0 >= 0 &&
+                        rc.kv - ty0 < kStagedTile && h <= hmax &&
+                        (a.vis_count == 0 || ids[k] < (uint64_t)a.vis_count);
+                    if (!gw_in_bounds(ok, a.queue + 1)) {
+                        rel = 8u | 8u << 8;
+                        w = 1u;
+                    }
+#endif
                     const int pos =
                         h > hmax / 2 ? atomicAdd(&c.front, 1) : atomicSub(&c.back, 1) - 1;
+#ifdef GW_DEBUG_BOUNDS
+                    if (!gw_in_bounds(pos >= 0 && pos < nc, a.queue + 1)) continue;
+                    if ((w & 0xffffu) == 1u && S != 1) {
+                        meta[pos] = make_uint4(0u, 0u, rel, w);
+                        continue;
+                    }
+#endif
                     meta[pos] = make_uint4(ids[k], (uint32_t)kofs, rel, w);
                     hw = max(hw, h);
                     atomicAdd(&c.taps[S & 7], S * S);

@@ -97,9 +97,16 @@ __global__ void __launch_bounds__(256) k_grid_direct(GridArgs a, const void* __r
             ++n_valid;
             n_taps += (unsigned long long)(S * S);
         }
-        const typename TE::T* K = reinterpret_cast<const typename TE::T*>(table) +
-                                  __ldg(a.plane_off + plane) +
-                                  ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+        const int64_t kofs = __ldg(a.plane_off + plane) +
+                             ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) * S * S;
+#ifdef GW_DEBUG_BOUNDS
+        // the slice and the footprint's pixels
+        if (!gw_in_bounds((a.table_elems == 0 || (kofs >= 0 && kofs + (int64_t)S * S <= a.table_elems)) &&
+                              rc.ku - h >= 0 && rc.ku + h < N && rc.kv - h >= 0 && rc.kv + h < N,
+                          a.queue ? a.queue + 1 : nullptr))
+            continue;
+#endif
+        const typename TE::T* K = reinterpret_cast<const typename TE::T*>(table) + kofs;
         const float sg = (rc.flags & GW_FLAG_CONJ) ? -1.f : 1.f;
         float2 V[NPOL];
 #pragma unroll

@@ -401,8 +401,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                                                        (uint32_t)r | (mask << 20) | conj);
                             for (int cu = cu0; cu <= cu1; ++cu) {
                                 const int w = cv * kBlocksU + cu;
+#ifdef GW_DEBUG_BOUNDS
+                                // the entry's loads: slots j0..j1 of the warp's block
+                                const int64_t lo = (int64_t)base + (int64_t)(kBlockV * cv + kGridLanesV * j0) * SP +
+                                                   kBlockU * cu;
+                                const int64_t hi = (int64_t)base +
+                                                   (int64_t)(kBlockV * cv + kGridLanesV * j1 + kGridLanesV - 1) * SP +
+                                                   kBlockU * cu + kBlockU - 1;
+                                if (!gw_in_bounds(a.ptable_elems == 0 || (lo >= 0 && hi < a.ptable_elems),
+                                                  a.queue + 1))
+                                    continue;
+#endif
                                 const int pos = atomicAdd(&sm.cnt[buf][w], 1);
-                                sm.list[buf][w][pos] = e;
+                                if (gw_in_bounds(pos < kBatch, a.queue + 1)) sm.list[buf][w][pos] = e;
                             }
                         }
                     }

@@ -311,6 +311,8 @@ struct GridArgs {
     const Item* items;
     const uint32_t* item_count;  // device scalar: item_off[ntiles] (one past the last item)
     const uint32_t* item_first = nullptr;  // device scalar: first item (null: 0)
+    int64_t ptable_elems = 0;    // elements of ptable (debug bounds checks)
+    int64_t table_elems = 0;     // elements of the unpadded table (direct path; checks)
     uint32_t* queue;             // device words: [0] work queue head (zeroed before launch),
                                  // [1] status (bit 0 set when a bounded device wait gave up)
     float2* grid;                // [npol][N][N]
@@ -379,11 +381,30 @@ struct DegridArgs {
     const uint32_t* item_count = nullptr;
     uint32_t* queue = nullptr;
     int ntiles_u = 0;
+    // debug bounds checks (0: unknown, not checked)
+    int64_t table_elems = 0;    // elements of `table`, slack included
+    int64_t vis_count = 0;      // visibilities of vis_out
 };
 void launch_degrid(const DegridArgs& a, int64_t nvis_upper, int num_sms, cudaStream_t s);
 // Staged-degrid region budget (bytes): the 227 KB a CTA may hold, less two
 // buffers of 1,024 records' metadata and the static shared memory.
 constexpr size_t kStagedSmemMax = 232448 - 2 * 1024 * 16 - 512;
+// Device status word bits (the word after the work-queue head): a bounded
+// wait gave up; a bounds check of the debug build failed.
+constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusBounds = 2u;
+// Bounds checks of the debug build (GW_DEBUG_BOUNDS): a failed check sets
+// kStatusBounds in the status word and the caller skips the access.  In
+// the release build the checks compile to `true`.
+#ifdef GW_DEBUG_BOUNDS
+__device__ __forceinline__ bool gw_in_bounds(bool ok, uint32_t* status) {
+    if (!ok && status) atomicOr(status, kStatusBounds);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool gw_in_bounds(bool, uint32_t*) { return true; }
+#endif
+
 // Zeroed elements after the last kernel slice of the unpadded tables: the
 // staged degridder loads kernel values up to this many elements past a slice.
 constexpr int64_t kTableSlack = 256;

@@ -448,6 +448,15 @@ class Server:
 
     # ---- job execution ------------------------------------------------------
     def _launch(self, job: Job, slot: int):
+        # an NVTX range per launch and per completion: profiler timelines show
+        # which job each slot's stream work belongs to
+        self.torch.cuda.nvtx.range_push(f"gw launch job {job.id} {job.kind} {job.setup} slot {slot}")
+        try:
+            self._launch_job(job, slot)
+        finally:
+            self.torch.cuda.nvtx.range_pop()
+
+    def _launch_job(self, job: Job, slot: int):
         torch = self.torch
         s = self.setups[job.setup]
         b = self.slots[slot]
@@ -484,6 +493,13 @@ class Server:
             b["event"].record(stream)
 
     def _finish(self, slot: int, now: float):
+        self.torch.cuda.nvtx.range_push(f"gw finish slot {slot}")
+        try:
+            return self._finish_job(slot, now)
+        finally:
+            self.torch.cuda.nvtx.range_pop()
+
+    def _finish_job(self, slot: int, now: float):
         job = self.sched.complete(slot)
         job.t_done = now
         if self.on_result is not None:
