@@ -40,8 +40,8 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
-GRID_TRAFFIC = {"sha256": "12be6ee91f495fc0707e4b27b4e542edd48511d3602e2ad03820cb8c80701828",
-                "bytes_per_launch": 0.963445e9 + 0.264317e9,
+GRID_TRAFFIC = {"sha256": "252e5c795457bda1dd660d13b6e992a3820f516fa4fe21adb78f33d105c0cdc0",
+                "bytes_per_launch": 0.962913e9 + 0.264283e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
 
 
