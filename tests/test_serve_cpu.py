@@ -213,3 +213,28 @@ def test_without_work_cap_only_slots_and_memory_limit_admission():
         j.work = 1e15
         s.arrive(j)
     assert [j.id for j, *_ in s.admit(lambda slot, setup: 0)] == [0, 1, 2]
+
+
+def test_slow_job_holds_one_slot_while_the_others_keep_serving():
+    """A job that does not finish (a fake slow job: its slot is never
+    completed) keeps only its own slot; every later job is served by the
+    other slots in arrival order."""
+    s = Scheduler(n_slots=3, budget=10**12)
+    for i in range(12):
+        s.arrive(job(i))
+    first = s.admit(lambda slot, setup: 0)
+    slow_slot = first[0][1]                               # job 0 never completes
+    served = [j.id for j, *_ in first]
+    running = {slot: j for j, slot, *_ in first}
+    while s.pending:
+        for slot in [sl for sl in list(running) if sl != slow_slot]:
+            s.complete(slot)
+            del running[slot]
+        got = s.admit(lambda slot, setup: 0)
+        assert got, "the other slots must keep admitting"
+        assert all(slot != slow_slot for _, slot, *_ in got)
+        for j, slot, *_ in got:
+            running[slot] = j
+            served.append(j.id)
+    assert served == list(range(12))
+    assert s.busy[slow_slot].id == 0
