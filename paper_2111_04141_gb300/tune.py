@@ -4,8 +4,9 @@ timing candidates on a sample job (CUDA events on the launching stream).
 The candidates are the plan tunables (gw_tuning): records per work item,
 which trades SM load balance on small or sparse jobs against commit
 traffic, and the degridding kernel (shared-memory staged tiles or global
-gather).  The best configuration of each setup is kept in a dict (and,
-optionally, a JSON file) keyed by the setup's name.
+gather).  The best configuration is kept in a dict (and, optionally, a JSON
+file) keyed by the setup's name or by ``plan_key(plan)``: the plan
+parameters the timings depend on and the device's SM count.
 """
 from __future__ import annotations
 
@@ -56,6 +57,19 @@ def tune_plan(plan, uvw, freq, vis, grid, reps: int = 3,
                                   "compress_min_gain": 0}, ms
     plan.set_tuning(**best)
     return {"tuning": best, "ms": best_ms, "timings": timings}
+
+
+def plan_key(plan, num_sms: Optional[int] = None) -> str:
+    """Cache key of a plan's tuning: grid size, support range, oversampling,
+    w-planes, polarisations, storage kinds and the SM count of its device
+    (a tuning found on another GPU or for other plan parameters is not
+    reused)."""
+    d = plan.desc
+    if num_sms is None:
+        import torch
+        num_sms = torch.cuda.get_device_properties(plan.device).multi_processor_count
+    return (f"N{d.grid_n}-S{d.support_min}-{d.support_max}-b{d.oversample}-P{d.n_wplanes}"
+            f"-pol{d.npol}-vis{d.vis_dtype}-tab{d.table_dtype}-sm{int(num_sms)}")
 
 
 class TuningCache:

@@ -238,3 +238,23 @@ def test_slow_job_holds_one_slot_while_the_others_keep_serving():
             served.append(j.id)
     assert served == list(range(12))
     assert s.busy[slow_slot].id == 0
+
+
+def test_tuning_cache_keys_by_plan_parameters_and_persists(tmp_path):
+    """The autotuner cache key names the plan parameters the timings depend
+    on and the SM count; the cache survives a reload from its JSON file."""
+    from types import SimpleNamespace
+    from paper_2111_04141_gb300.tune import TuningCache, plan_key
+    desc = SimpleNamespace(grid_n=4096, support_min=7, support_max=63, oversample=8,
+                           n_wplanes=32, npol=4, vis_dtype=0, table_dtype=1)
+    plan = SimpleNamespace(desc=desc, device=None)
+    k = plan_key(plan, num_sms=152)
+    assert k == "N4096-S7-63-b8-P32-pol4-vis0-tab1-sm152"
+    assert plan_key(plan, num_sms=148) != k
+    desc.table_dtype = 0
+    assert plan_key(plan, num_sms=152) != k
+    path = str(tmp_path / "tune.json")
+    c = TuningCache(path)
+    c.put(k, {"item_max": 2048, "degrid_kernel": 1, "grid_kernel": 0, "compress_min_gain": 0})
+    assert TuningCache(path).get(k)["item_max"] == 2048
+    assert TuningCache(path).get("other") is None
