@@ -40,8 +40,8 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
-GRID_TRAFFIC = {"sha256": "252e5c795457bda1dd660d13b6e992a3820f516fa4fe21adb78f33d105c0cdc0",
-                "bytes_per_launch": 0.962913e9 + 0.264283e9,
+GRID_TRAFFIC = {"sha256": "143ed5e434f929e3248e0370557c3e0a5ad9ae36c845cf2d804a10612c9f912f",
+                "bytes_per_launch": 0.962756e9 + 0.263721e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
 
 
@@ -395,6 +395,7 @@ def measure_c5(gw, dev, stream, steps, peak):
                          "stage_ms_per_step": {k: tm[f"{k}_ms"] / steps
                                                for k in ("index", "bin", "grid")},
                          "table_bytes": int(info.table_bytes),
+                         "plane_groups": int(info.plane_groups),
                          "mean_S2": tm["taps"] / max(1, tm["valid_vis"])}
             del g
             if kind != "c64":

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define GW_API_VERSION 7
+#define GW_API_VERSION 8
 
 typedef struct gw_plan_s* gw_plan;
 
@@ -119,7 +119,8 @@ typedef struct {
     int32_t table_exp2;       /* 16-bit tables store round(K * 2^table_exp2); 0 for
                                  GW_C64 and GW_BF16X2; for GW_F16X2 chosen so the largest
                                  entry (w = 0, o = 0 centre tap) lies in [2^14, 2^15) */
-    int32_t reserved;
+    int32_t plane_groups;     /* plane groups the binned gridder uses under the current
+                                 tuning (gw_tuning.plane_groups; 1 = tiles only) */
     int64_t table_bytes;      /* device bytes of the kernel tables (shared with clones) */
     int64_t scratch_bytes;    /* device bytes of this plan's own scratch */
 } gw_plan_info;
@@ -142,6 +143,13 @@ typedef struct {
                                2^18 visibilities; the call synchronises the stream) and grid
                                without compression when fewer than g per mille of its valid
                                records merge (n_gridded then counts the valid records) */
+    int32_t plane_groups;   /* binned gridding in gw_grid_vis / _host / _compressed: bins
+                               keyed by (w-plane group, tile) and served group by group, so
+                               one group's kernel tables stay in L2 (Section 3.3.5 "SS"
+                               ordering): 0 = automatic (FP32 tables above 128 MB: one
+                               group per 64 MB of padded tables; otherwise 1),
+                               1 = tiles only, n in 2..16 (at most the w-planes) = n
+                               groups of consecutive planes */
 } gw_tuning;
 
 /* ------------------------------------------------------------------------

@@ -39,12 +39,12 @@ class PlanInfo(ctypes.Structure):
                 ("device", c_i32), ("table_elems", c_i64), ("chunk_vis", c_i64),
                 ("field", c_f64), ("taper_c", c_f64), ("table_scale", c_f64),
                 ("vis_dtype", c_i32), ("table_dtype", c_i32), ("table_exp2", c_i32),
-                ("reserved", c_i32), ("table_bytes", c_i64), ("scratch_bytes", c_i64)]
+                ("plane_groups", c_i32), ("table_bytes", c_i64), ("scratch_bytes", c_i64)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("item_max", c_i32), ("degrid_kernel", c_i32), ("grid_kernel", c_i32),
-                ("compress_min_gain", c_i32)]
+                ("compress_min_gain", c_i32), ("plane_groups", c_i32)]
 
 
 class Timing(ctypes.Structure):

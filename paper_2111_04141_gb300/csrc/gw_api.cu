@@ -128,7 +128,9 @@ struct gw_plan_s {
     int num_sms = 0;
     BinGeom geom_grid{}, geom_degrid{}, geom_staged{};
     int hmax = 0;        // largest half-support over the planes
-    int ntiles = 0;      // bins allocated (max over both geometries)
+    int ntiles = 0;      // bins allocated (max over the geometries and plane groups)
+    int max_groups = 1;  // plane groups the bins are allocated for (gw_tuning.plane_groups)
+    int auto_groups = 1; // plane groups chosen when plane_groups = 0
     int pad_stride = 0;
     double field = 0, table_scale = 0;
     std::vector<int> support;
@@ -500,6 +502,18 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
         plan_free(p);
         return fail(GW_EINVAL, "kernel tables exceed 2^31 elements");
     }
+    // plane groups: bins keyed by (group of consecutive w-planes, tile) keep
+    // one group's padded tables in L2 while its items are gridded; chosen
+    // automatically for FP32 tables above kGroupTableBytes (16-bit tables
+    // did not grid faster in groups, and grouped binning costs more)
+    p->max_groups = P > 1 ? std::min(P, kMaxPlaneGroups) : 1;
+    {
+        const int64_t tb = p->pplane_off[P] * (int64_t)dtype_bytes(desc->table_dtype);
+        const int64_t g = desc->table_dtype == GW_C64 && tb > kGroupTableBytes
+                              ? (tb + kGroupTargetBytes - 1) / kGroupTargetBytes : 1;
+        p->auto_groups = (int)std::min<int64_t>(g, p->max_groups);
+    }
+    p->ntiles = std::max(p->ntiles, p->geom_grid.ntu * p->geom_grid.ntv * p->max_groups);
     p->max_tiles_per_vis = std::max(((smax_real - 1) / kGridTileU + 2) * ((smax_real - 1) / kGridTileV + 2), 1);
     p->chunk = desc->max_vis_per_call > 0 ? desc->max_vis_per_call : ((int64_t)1 << 23);
     if (p->chunk * p->max_tiles_per_vis >= ((int64_t)1 << 32)) {
@@ -644,6 +658,8 @@ gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream
     p->geom_staged = src->geom_staged;
     p->hmax = src->hmax;
     p->ntiles = src->ntiles;
+    p->max_groups = src->max_groups;
+    p->auto_groups = src->auto_groups;
     p->pad_stride = src->pad_stride;
     p->field = src->field;
     p->table_scale = src->table_scale;
@@ -701,6 +717,8 @@ gw_status gw_plan_set_tuning(gw_plan p, const gw_tuning* t) {
         return fail(GW_EINVAL, "grid_kernel must be 0 (auto), 1 (binned) or 2 (direct)");
     if (t->compress_min_gain < 0 || t->compress_min_gain > 1000)
         return fail(GW_EINVAL, "compress_min_gain must be in [0, 1000] (per mille)");
+    if (t->plane_groups < 0 || t->plane_groups > p->max_groups)
+        return fail(GW_EINVAL, "plane_groups must be in [0, %d] for this plan", p->max_groups);
     p->tuning = *t;
     apply_tuning(p);
     return GW_OK;
@@ -740,6 +758,22 @@ int64_t gw_debug_live_bytes(void) {
     return g_live_bytes;
 }
 
+// Plane groups of the binned gridder (gw_tuning.plane_groups, 0 = the plan's
+// automatic choice), and the bin geometry for them.
+static int grid_groups(gw_plan p) {
+    const int g = p->tuning.plane_groups > 0 ? p->tuning.plane_groups : p->auto_groups;
+    return std::max(1, std::min(g, p->max_groups));
+}
+static BinGeom grid_geom(gw_plan p, int groups) {
+    BinGeom g = p->geom_grid;
+    if (groups > 1) {
+        g.layer_tiles = g.ntu * g.ntv;
+        g.nlayers = groups;
+        g.group_planes = (p->desc.n_wplanes + groups - 1) / groups;
+    }
+    return g;
+}
+
 gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
     if (!p || !out) return fail(GW_EINVAL, "null argument");
     out->grid_n = p->desc.grid_n;
@@ -758,7 +792,7 @@ gw_status gw_plan_info_get(gw_plan p, gw_plan_info* out) {
     out->vis_dtype = p->desc.vis_dtype;
     out->table_dtype = p->desc.table_dtype;
     out->table_exp2 = p->table_exp2;
-    out->reserved = 0;
+    out->plane_groups = grid_groups(p);
     out->table_bytes = p->tabs ? p->tabs->bytes : 0;
     out->scratch_bytes = p->scratch_bytes;
     return GW_OK;
@@ -827,7 +861,9 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
             if (e != cudaSuccess) return cuda_fail(e, "grid launch");
             continue;
         }
-        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, p->geom_grid, s);
+        const int groups = grid_groups(p);
+        const BinGeom geom = grid_geom(p, groups);
+        st = index_and_bin(p, uvw_m + 3 * r0, freq_hz, nr, nchan, geom, s);
         if (st != GW_OK) return st;
         GridArgs a;
         a.rec = p->sc.rec;
@@ -855,7 +891,12 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
         a.support = p->d_support;
         a.entries = p->sc.entries;
         a.items = p->sc.items;
-        a.item_count = p->sc.item_off + p->geom_grid.ntu * p->geom_grid.ntv;
+        a.item_count = p->sc.item_off + p->geom_grid.ntu * p->geom_grid.ntv * groups;
+        if (groups > 1) {
+            a.layer_tiles = p->geom_grid.ntu * p->geom_grid.ntv;
+            a.layer_stride = 0;
+            a.plane_groups = 1;
+        }
         a.queue = p->sc.counters;
         a.grid = reinterpret_cast<float2*>(grid);
         a.grid_err = reinterpret_cast<float2*>(grid_err);

@@ -55,7 +55,7 @@ __global__ void k_count(const gw_index_rec* __restrict__ rec, int64_t nvis, DevC
         ++n_valid;
         n_taps += (unsigned long long)(S * S);
         const TileRange t = tile_range(r, g, P, smin, smax);
-        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        const int lbase = g.layer_tiles ? (r.plane / g.group_planes) * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu)
                 atomicAdd(count + lbase + tv * g.ntu + tu, 1u);
@@ -228,7 +228,7 @@ __global__ void k_scatter(const gw_index_rec* __restrict__ rec, int64_t nvis, De
         const gw_index_rec r = load_rec(rec, i);
         if (!(r.flags & GW_FLAG_VALID)) continue;
         const TileRange t = tile_range(r, g, P, smin, smax);
-        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        const int lbase = g.layer_tiles ? (r.plane / g.group_planes) * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu) {
                 const int tile = lbase + tv * g.ntu + tu;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kBinSmThreads) k_count_sm(
         ++n_valid;
         n_taps += (unsigned long long)(S * S);
         const TileRange t = tile_range(r, g, P, smin, smax);
-        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        const int lbase = g.layer_tiles ? (r.plane / g.group_planes) * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(hist + lbase + tv * g.ntu + tu, 1u);
     }
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kBinSmThreads) k_scatter_sm(
         const gw_index_rec r = load_rec(rec, i);
         if (!(r.flags & GW_FLAG_VALID)) continue;
         const TileRange t = tile_range(r, g, P, smin, smax);
-        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        const int lbase = g.layer_tiles ? (r.plane / g.group_planes) * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu) atomicAdd(hist + lbase + tv * g.ntu + tu, 1u);
     }
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kBinSmThreads) k_scatter_sm(
         const gw_index_rec r = load_rec(rec, i);
         if (!(r.flags & GW_FLAG_VALID)) continue;
         const TileRange t = tile_range(r, g, P, smin, smax);
-        const int lbase = g.layer_tiles ? r.plane * g.layer_tiles : 0;
+        const int lbase = g.layer_tiles ? (r.plane / g.group_planes) * g.layer_tiles : 0;
         for (int tv = t.tv0; tv <= t.tv1; ++tv)
             for (int tu = t.tu0; tu <= t.tu1; ++tu) {
                 const uint32_t pos = atomicAdd(hist + lbase + tv * g.ntu + tu, 1u);

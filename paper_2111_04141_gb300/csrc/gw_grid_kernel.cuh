@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid(GridArgs a) {
                         }
                         // w-stacking records carry their layer in `plane`; the
                         // kernel is the plan's single (w = 0) plane
-                        const int plane = a.layer_tiles ? 0 : rc.plane;
+                        const int plane = (a.layer_tiles && !a.plane_groups) ? 0 : rc.plane;
                         const int S = __ldg(a.support + plane), h = S >> 1;
                         const int64_t slice = __ldg(a.pplane_off + plane) +
                                               ((int64_t)(rc.ov + hb) * a.beta + (rc.ou + hb)) *

@@ -261,8 +261,9 @@ void launch_index(const double* uvw, const double* freq, int64_t nrow, int nchan
 struct BinGeom {
     int mode, su, sv, ntu, ntv;
     int item_max = kItemMax;
-    int layer_tiles = 0;   // > 0: tile id += record.plane * layer_tiles (w-stacking layers)
+    int layer_tiles = 0;   // > 0: tile id += (record.plane / group_planes) * layer_tiles
     int nlayers = 1;       // layers binned when layer_tiles > 0 (ntu * ntv * nlayers tiles)
+    int group_planes = 1;  // planes per layer: 1 for w-stacking layers, more for plane groups
 };
 // Words of Scratch::scan_tmp for a multi-CTA scan over ntiles bins.
 int64_t scan_tmp_words(int64_t ntiles);
@@ -325,6 +326,10 @@ struct GridArgs {
     // layer in `plane`, layer grids are layer_stride elements apart (0 = off)
     int layer_tiles = 0;
     int64_t layer_stride = 0;
+    // plane groups: tile ids are group * layer_tiles + tile as above, but the
+    // records keep their own w-plane and every group adds into `grid`
+    // (layer_stride 0)
+    int plane_groups = 0;
 };
 void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s);
 // Direct gridding (no bins) of nrow x nchan visibilities, each warp
@@ -345,6 +350,12 @@ void launch_grid_direct(const GridArgs& a, const void* table, const DirectIndex&
 // Direct gridding is chosen for at most this many visibilities per chunk and
 // this many tap updates (visibilities x S_max^2 x npol).
 constexpr int64_t kDirectMaxVis = 16384;
+// Plane groups of the binned gridder: at most this many, chosen
+// automatically when FP32 padded tables exceed kGroupTableBytes (about the
+// L2), with about kGroupTargetBytes of tables per group.
+constexpr int kMaxPlaneGroups = 16;
+constexpr int64_t kGroupTableBytes = 128ll << 20;
+constexpr int64_t kGroupTargetBytes = 64ll << 20;
 // Bands of tile rows a banded read-back may use (gw_grid_vis_devcount_readback).
 constexpr int kReadbackBandsMax = 64;
 constexpr int64_t kDirectMaxTaps = (int64_t)1 << 22;

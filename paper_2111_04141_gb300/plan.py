@@ -115,13 +115,18 @@ class Plan:
         t = _lib.Tuning()
         check(self._lib.gw_plan_get_tuning(self._h, ctypes.byref(t)), "gw_plan_get_tuning")
         return {"item_max": t.item_max, "degrid_kernel": t.degrid_kernel,
-                "grid_kernel": t.grid_kernel, "compress_min_gain": t.compress_min_gain}
+                "grid_kernel": t.grid_kernel, "compress_min_gain": t.compress_min_gain,
+                "plane_groups": t.plane_groups}
 
     def set_tuning(self, item_max: int = 0, degrid_kernel: int = 0, grid_kernel: int = 0,
-                   compress_min_gain: int = 0):
+                   compress_min_gain: int = 0, plane_groups: int = 0):
         t = _lib.Tuning(item_max=int(item_max), degrid_kernel=int(degrid_kernel),
-                        grid_kernel=int(grid_kernel), compress_min_gain=int(compress_min_gain))
+                        grid_kernel=int(grid_kernel), compress_min_gain=int(compress_min_gain),
+                        plane_groups=int(plane_groups))
         check(self._lib.gw_plan_set_tuning(self._h, ctypes.byref(t)), "gw_plan_set_tuning")
+        info = PlanInfo()   # plane_groups follows the tuning
+        check(self._lib.gw_plan_info_get(self._h, ctypes.byref(info)), "gw_plan_info_get")
+        self.info = info
 
     @classmethod
     def from_observation(cls, obs, **kw):

@@ -54,7 +54,7 @@ def tune_plan(plan, uvw, freq, vis, grid, reps: int = 3,
             timings[f"item_max={im},degrid_kernel={dk}"] = ms
             if ms < best_ms:
                 best, best_ms = {"item_max": im, "degrid_kernel": dk, "grid_kernel": 0,
-                                  "compress_min_gain": 0}, ms
+                                  "compress_min_gain": 0, "plane_groups": 0}, ms
     plan.set_tuning(**best)
     return {"tuning": best, "ms": best_ms, "timings": timings}
 

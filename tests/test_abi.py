@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
     for name in declared_functions():
         assert hasattr(lib, name), name
         assert name in L.EXPORTED, name
-    assert lib.gw_api_version() == 7
+    assert lib.gw_api_version() == 8
     assert lib.gw_strerror(-1) == b"invalid argument"
 
 

@@ -236,6 +236,24 @@ def test_grid_matches_oracle(gw, case, kernel):
     assert dropped == int((~orc.index(obs.uvw_m, obs.freq_hz)["valid"]).sum())
 
 
+@pytest.mark.parametrize("groups", [2, 0], ids=["two", "one-per-plane"])
+def test_grid_plane_groups_match_oracle(gw, case, groups):
+    """Bins keyed by (w-plane group, tile), served group by group, give the
+    oracle's grid; 0 here asks for the most groups the plan allows (up to one
+    per plane)."""
+    name, obs, prm = case
+    if prm.n_wplanes < 2:
+        pytest.skip("one w-plane: nothing to group")
+    orc = oracle_for(prm)
+    ref = orc.grid(obs.uvw_m, obs.freq_hz, obs.vis)
+    with gw.Plan.from_observation(obs, max_vis_per_call=max(obs.nchan, obs.nvis // 3)) as plan:
+        n = groups or min(prm.n_wplanes, 16)
+        plan.set_tuning(grid_kernel=1, plane_groups=n)
+        assert plan.info.plane_groups == n
+        g = plan.grid(dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)).cpu().numpy()
+    assert rel_l2(g.astype(np.complex128), ref) <= TOL_GRID, (name, n)
+
+
 @pytest.mark.parametrize("kernel", [1, 2], ids=["binned", "direct"])
 def test_grid_weights_accumulate_and_chunks(gw, kernel):
     obs = CASES["small-w"]()

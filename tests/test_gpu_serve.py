@@ -101,23 +101,28 @@ def test_clone_shares_tables_and_outlives_master(gw):
     clone.close()
 
 
-@pytest.mark.parametrize("item_max,degrid_kernel,grid_kernel",
-                         [(64, 2, 1), (256, 1, 2), (4096, 0, 0)])
-def test_tuning_changes_nothing_but_speed(gw, item_max, degrid_kernel, grid_kernel):
+@pytest.mark.parametrize("item_max,degrid_kernel,grid_kernel,plane_groups",
+                         [(64, 2, 1, 2), (256, 1, 2, 1), (4096, 0, 0, 0), (1024, 0, 1, 3)])
+def test_tuning_changes_nothing_but_speed(gw, item_max, degrid_kernel, grid_kernel, plane_groups):
     obs = small()
     u, f, v = dev(obs.uvw_m), dev(obs.freq_hz), dev(obs.vis)
     with gw.Plan.from_observation(obs) as plan:
         g0 = plan.grid(u, f, v)
         d0 = plan.degrid(u, f, g0)
-        plan.set_tuning(item_max=item_max, degrid_kernel=degrid_kernel, grid_kernel=grid_kernel)
+        plan.set_tuning(item_max=item_max, degrid_kernel=degrid_kernel, grid_kernel=grid_kernel,
+                        plane_groups=plane_groups)
         assert plan.get_tuning() == {"item_max": item_max, "degrid_kernel": degrid_kernel,
-                                     "grid_kernel": grid_kernel, "compress_min_gain": 0}
+                                     "grid_kernel": grid_kernel, "compress_min_gain": 0,
+                                     "plane_groups": plane_groups}
+        assert plan.info.plane_groups == max(1, plane_groups)   # small FP32 tables: auto = 1
         assert rel(plan.grid(u, f, v), g0) <= TOL
         assert rel(plan.degrid(u, f, g0), d0) <= TOL
         with pytest.raises(gw.GwError):
             plan.set_tuning(item_max=3)
         with pytest.raises(gw.GwError):
             plan.set_tuning(grid_kernel=3)
+        with pytest.raises(gw.GwError):
+            plan.set_tuning(plane_groups=17)
 
 
 def test_autotuner_picks_a_candidate(gw):
