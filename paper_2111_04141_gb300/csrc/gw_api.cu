@@ -173,7 +173,8 @@ struct gw_plan_s {
     // device state
     float2* table = nullptr;      // FP32 tables (always built)
     uint32_t* table16 = nullptr;  // 16-bit-pair tables (table_dtype != GW_C64)
-    void* ptable = nullptr;       // zero-padded gridder tables of kind table_dtype
+    void* ptable = nullptr;       // zero-padded gridder tables of kind grid_tk
+    int grid_tk = GW_C64;         // their kind: table_dtype, or kTabRealF32 (w = 0 kernel)
     int table_exp2 = 0;           // 16-bit tables hold K * 2^table_exp2
     float table_inv = 1.f;        // 2^-table_exp2
     std::vector<int64_t> pplane_off;
@@ -535,7 +536,14 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
 #define GW_ALLOC(x, n) do { e = dmalloc(&(x), (n)); if (e != cudaSuccess) { plan_free(p); \
         return fail(GW_ENOMEM, "device allocation of %s failed", #x); } } while (0)
     GW_ALLOC(p->table, (size_t)(p->plane_off[P] + kTableSlack));
-    if (desc->table_dtype == GW_C64) {
+    // 2-D plans (P = 1) grid with the real w = 0 kernel: its imaginary parts
+    // are exactly zero, so the gridder's padded table keeps the real parts
+    p->grid_tk = desc->table_dtype == GW_C64 && P == 1 ? kTabRealF32 : desc->table_dtype;
+    if (p->grid_tk == kTabRealF32) {
+        float* pt = nullptr;
+        GW_ALLOC(pt, (size_t)p->pplane_off[P]);
+        p->ptable = pt;
+    } else if (desc->table_dtype == GW_C64) {
         float2* pt = nullptr;
         GW_ALLOC(pt, (size_t)p->pplane_off[P]);
         p->ptable = pt;
@@ -605,7 +613,7 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     }
     p->table_inv = std::ldexp(1.0f, -p->table_exp2);
     if (desc->table_dtype == GW_C64)
-        launch_pad_tables(p->table, GW_C64, p->d_plane_off, p->d_pplane_off, p->d_support, P,
+        launch_pad_tables(p->table, p->grid_tk, p->d_plane_off, p->d_pplane_off, p->d_support, P,
                           beta, p->pad_stride, p->ptable, s);
     else
         launch_pad_tables(p->table16, desc->table_dtype, p->d_plane_off, p->d_pplane_off,
@@ -624,7 +632,8 @@ gw_status gw_plan_create(const gw_plan_desc* desc, void* cuda_stream, gw_plan* o
     t->d_h = p->d_h;
     t->d_hf = p->d_hf;
     t->bytes = (int64_t)sizeof(float2) * (p->plane_off[P] + kTableSlack) +
-               (int64_t)dtype_bytes(desc->table_dtype) * p->pplane_off[P] +
+               (int64_t)(p->grid_tk == kTabRealF32 ? sizeof(float) : dtype_bytes(desc->table_dtype)) *
+                   p->pplane_off[P] +
                (p->table16 ? (int64_t)sizeof(uint32_t) * (p->plane_off[P] + kTableSlack) : 0) +
                (int64_t)(2 * sizeof(int64_t) + sizeof(int)) * (P + 1) +
                (int64_t)(sizeof(double) + sizeof(float)) * N;
@@ -681,6 +690,7 @@ gw_status gw_plan_clone(gw_plan src, int64_t max_vis_per_call, void* cuda_stream
     p->table = src->table;
     p->table16 = src->table16;
     p->ptable = src->ptable;
+    p->grid_tk = src->grid_tk;
     p->table_exp2 = src->table_exp2;
     p->table_inv = src->table_inv;
     p->d_pplane_off = src->d_pplane_off;
@@ -885,7 +895,7 @@ static gw_status grid_impl(gw_plan p, const double* uvw_m, const double* freq_hz
             a.vis = p->sc.wvis;
             a.vis_kind = GW_C64;
         }
-        a.table_kind = p->desc.table_dtype;
+        a.table_kind = p->grid_tk;
         a.table_inv = p->table_inv;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
@@ -1145,7 +1155,7 @@ gw_status gw_grid_vis_compressed(gw_plan p, const double* uvw_m, const double* f
         a.vis = p->cs.vis;
         a.vis_kind = GW_C64;
         a.weight = nullptr;
-        a.table_kind = p->desc.table_dtype;
+        a.table_kind = p->grid_tk;
         a.table_inv = p->table_inv;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
@@ -1270,7 +1280,7 @@ gw_status gw_grid_vis_wstack(gw_plan p, const double* uvw_m, const double* freq_
         a.vis = static_cast<const char*>(vis) + (size_t)v0 * npol * vb;
         a.vis_kind = vk;
         a.weight = weight ? weight + v0 * npol : nullptr;
-        a.table_kind = p->desc.table_dtype;
+        a.table_kind = p->grid_tk;
         a.table_inv = p->table_inv;
         a.plane_off = p->d_plane_off;
         a.support = p->d_support;
@@ -1551,7 +1561,7 @@ gw_status gw_grid_vis_devcount(gw_plan p, const double* uvw_m, const double* fre
     a.vis = vis;
     a.vis_kind = vk;
     a.weight = nullptr;
-    a.table_kind = p->desc.table_dtype;
+    a.table_kind = p->grid_tk;
     a.table_inv = p->table_inv;
     a.plane_off = p->d_plane_off;
     a.support = p->d_support;
@@ -1632,7 +1642,7 @@ gw_status gw_grid_vis_devcount_readback(gw_plan p, const double* uvw_m, const do
     a.vis = vis;
     a.vis_kind = vk;
     a.weight = nullptr;
-    a.table_kind = p->desc.table_dtype;
+    a.table_kind = p->grid_tk;
     a.table_inv = p->table_inv;
     a.plane_off = p->d_plane_off;
     a.support = p->d_support;

@@ -30,6 +30,28 @@ __global__ void k_pad_tables(const T* __restrict__ tab, const int64_t* __restric
     }
 }
 
+// The same padding for a real kernel: the real parts of an FP32 table.
+__global__ void k_pad_tables_real(const float2* __restrict__ tab, const int64_t* __restrict__ plane_off,
+                                  const int64_t* __restrict__ pplane_off,
+                                  const int* __restrict__ support, int P, int beta, int SP,
+                                  float* __restrict__ ptab) {
+    const int p = blockIdx.y;
+    if (p >= P) return;
+    const int S = support[p], SR = S + 2 * kGridPadR;
+    const int64_t per = (int64_t)SR * SP;
+    const int64_t n = (int64_t)beta * beta * per;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = e / per;
+        const int rem = (int)(e - o * per);
+        const int row = rem / SP - kGridPadR, col = rem % SP - kGridPadC;
+        float v = 0.f;
+        if (row >= 0 && row < S && col >= 0 && col < S)
+            v = tab[plane_off[p] + o * S * S + (int64_t)row * S + col].x;
+        ptab[pplane_off[p] + e] = v;
+    }
+}
+
 __global__ void k_weight_vis(const void* __restrict__ vis, int kind, const float* __restrict__ w,
                              int64_t n, float2* __restrict__ out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -218,7 +240,11 @@ int64_t padded_table_elems(int S, int beta, int SP) {
 void launch_pad_tables(const void* tab, int kind, const int64_t* plane_off,
                        const int64_t* pplane_off, const int* support, int P, int beta, int SP,
                        void* ptab, cudaStream_t s) {
-    if (kind == GW_C64)
+    if (kind == kTabRealF32)
+        k_pad_tables_real<<<dim3(256, P), 256, 0, s>>>(
+            static_cast<const float2*>(tab), plane_off, pplane_off, support, P, beta, SP,
+            static_cast<float*>(ptab));
+    else if (kind == GW_C64)
         k_pad_tables<float2><<<dim3(256, P), 256, 0, s>>>(
             static_cast<const float2*>(tab), plane_off, pplane_off, support, P, beta, SP,
             static_cast<float2*>(ptab));
@@ -234,6 +260,7 @@ void launch_grid(const GridArgs& a, int num_sms, cudaStream_t s) {
     switch (a.table_kind) {
         case GW_BF16X2: launch_grid_bf16(a, num_sms, s); break;
         case GW_F16X2: launch_grid_f16(a, num_sms, s); break;
+        case kTabRealF32: launch_grid_r32(a, num_sms, s); break;
         default: launch_grid_c64(a, num_sms, s); break;
     }
 }

@@ -184,7 +184,7 @@ struct Smem {
 };
 
 // Packed FMAs of one entry into slots J0..J1 (compile-time range); A = V,
-// Bv = s (-V.im, V.re).
+// Bv = s (-V.im, V.re) (unused for a real kernel).
 template <int NPOL, int J0, int J1, class TE>
 __device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const typename TE::T (&Kr)[4],
                                          const float2 (&A)[NPOL], const float2 (&Bv)[NPOL]) {
@@ -195,13 +195,16 @@ __device__ __forceinline__ void slot_fma(float2 (&acc)[4][NPOL], const typename 
         const float2 kyy = make_float2(kc.y, kc.y);
 #pragma unroll
         for (int p = 0; p < NPOL; ++p) acc[j][p] = __ffma2_rn(kxx, A[p], acc[j][p]);
+        if constexpr (!TE::kReal) {
 #pragma unroll
-        for (int p = 0; p < NPOL; ++p) acc[j][p] = __ffma2_rn(kyy, Bv[p], acc[j][p]);
+            for (int p = 0; p < NPOL; ++p) acc[j][p] = __ffma2_rn(kyy, Bv[p], acc[j][p]);
+        }
     }
 }
 
-// Staged visibility of an entry and the second FMA operand s (-V.im, V.re).
-template <int NPOL>
+// Staged visibility of an entry and the second FMA operand s (-V.im, V.re)
+// (not formed for a real kernel).
+template <int NPOL, bool REAL>
 __device__ __forceinline__ void load_v(float2 (&A)[NPOL], float2 (&Bv)[NPOL],
                                        const float2 (*vs)[NPOL], uint32_t ey) {
     const float2* row = vs[ey & 0x1ff];
@@ -216,9 +219,11 @@ __device__ __forceinline__ void load_v(float2 (&A)[NPOL], float2 (&Bv)[NPOL],
 #pragma unroll
         for (int p = 0; p < NPOL; ++p) A[p] = row[p];
     }
-    const float s = (ey & kConjBit) ? -1.f : 1.f;
+    if constexpr (!REAL) {
+        const float s = (ey & kConjBit) ? -1.f : 1.f;
 #pragma unroll
-    for (int p = 0; p < NPOL; ++p) Bv[p] = make_float2(-s * A[p].y, s * A[p].x);
+        for (int p = 0; p < NPOL; ++p) Bv[p] = make_float2(-s * A[p].y, s * A[p].x);
+    }
 }
 
 // Kernel values of one list entry, as stored: the slots in its mask, zero
@@ -260,7 +265,7 @@ __device__ __forceinline__ void ring_pass(const uint2* next, const float2 (*vs)[
 #pragma unroll
     for (int d = 0; d < R; ++d) {
         float2 A[NPOL], Bv[NPOL];
-        load_v<NPOL>(A, Bv, vs, ey[d]);
+        load_v<NPOL, TE::kReal>(A, Bv, vs, ey[d]);
         slot_fma<NPOL, 0, 3, TE>(acc, K[d], A, Bv);
         const uint2 en = next[d];
         ey[d] = en.y;

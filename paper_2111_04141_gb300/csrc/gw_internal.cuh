@@ -67,22 +67,37 @@ __device__ __forceinline__ float2 unpack_f16x2(uint32_t u) {
     return __half22float2(h);
 }
 
-// Table element of kind TK and its load (read-only path).
+// Gridder table kind of the real w = 0 kernel (2-D plans with FP32 tables):
+// the padded gridder table holds the real parts only, the imaginary parts of
+// that kernel being exactly zero (no w-screen phase, cosine transform).
+constexpr int kTabRealF32 = 3;
+
+// Table element of kind TK and its load (read-only path); kReal: the
+// imaginary part is zero and its FMAs are left out.
 template <int TK> struct TabElem;
 template <> struct TabElem<GW_C64> {
+    static constexpr bool kReal = false;
     using T = float2;
     static __device__ __forceinline__ float2 cvt(T v) { return v; }
     static __device__ __forceinline__ float2 load(const T* p) { return __ldg(p); }
 };
 template <> struct TabElem<GW_BF16X2> {
+    static constexpr bool kReal = false;
     using T = uint32_t;
     static __device__ __forceinline__ float2 cvt(T v) { return unpack_bf16x2(v); }
     static __device__ __forceinline__ float2 load(const T* p) { return unpack_bf16x2(__ldg(p)); }
 };
 template <> struct TabElem<GW_F16X2> {
+    static constexpr bool kReal = false;
     using T = uint32_t;
     static __device__ __forceinline__ float2 cvt(T v) { return unpack_f16x2(v); }
     static __device__ __forceinline__ float2 load(const T* p) { return unpack_f16x2(__ldg(p)); }
+};
+template <> struct TabElem<kTabRealF32> {
+    static constexpr bool kReal = true;
+    using T = float;
+    static __device__ __forceinline__ float2 cvt(T v) { return make_float2(v, 0.f); }
+    static __device__ __forceinline__ float2 load(const T* p) { return make_float2(__ldg(p), 0.f); }
 };
 
 // Visibility i of a buffer of kind `kind` (uniform runtime branch).
@@ -359,8 +374,10 @@ constexpr int64_t kGroupTargetBytes = 64ll << 20;
 // Bands of tile rows a banded read-back may use (gw_grid_vis_devcount_readback).
 constexpr int kReadbackBandsMax = 64;
 constexpr int64_t kDirectMaxTaps = (int64_t)1 << 22;
-// One instantiation set per table kind (gw_grid_c64.cu, gw_grid_bf16.cu, gw_grid_f16.cu).
+// One instantiation set per table kind (gw_grid_c64.cu, gw_grid_bf16.cu, gw_grid_f16.cu,
+// gw_grid_r32.cu).
 void launch_grid_c64(const GridArgs& a, int num_sms, cudaStream_t s);
+void launch_grid_r32(const GridArgs& a, int num_sms, cudaStream_t s);
 void launch_grid_bf16(const GridArgs& a, int num_sms, cudaStream_t s);
 void launch_grid_f16(const GridArgs& a, int num_sms, cudaStream_t s);
 // out[e] = vis[e] * w[e] in FP32 (weights applied before gridding); vis of kind `kind`.
