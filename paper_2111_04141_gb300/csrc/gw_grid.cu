@@ -80,12 +80,14 @@ __global__ void __launch_bounds__(256) k_grid_direct(GridArgs a, const void* __r
     // [P - 1] w-plane thresholds as int64 bit patterns and [nc] channel
     // factors f / c0, as the index stage builds them
     extern __shared__ long long sh_idx[];
+    __shared__ unsigned long long s_cnt[3];   // the block's valid, taps, dropped
     const int nthr = di.p.P > 1 ? di.p.P - 1 : 0;
     const int nc = min(di.nchan, kDirectChanCache);
     long long* thr = sh_idx;
     double* fc = reinterpret_cast<double*>(sh_idx + nthr);
     for (int j = threadIdx.x; j < nthr; j += blockDim.x) thr[j] = wplane_threshold(j, di.p);
     for (int c = threadIdx.x; c < nc; c += blockDim.x) fc[c] = __ddiv_rn(__ldg(di.freq + c), kC0);
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -173,13 +175,22 @@ __global__ void __launch_bounds__(256) k_grid_direct(GridArgs a, const void* __r
             }
         }
     }
-    // counts are held by lane 0 of each warp
+    // counts are held by lane 0 of each warp: summed per block first, so
+    // the global counters take one atomic per block
     if (lane == 0) {
         if (n_valid) {
-            atomicAdd(work, n_valid);
-            atomicAdd(work + 1, n_taps);
+            atomicAdd(&s_cnt[0], n_valid);
+            atomicAdd(&s_cnt[1], n_taps);
         }
-        if (n_drop) atomicAdd(di.dropped, n_drop);
+        if (n_drop) atomicAdd(&s_cnt[2], n_drop);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) {
+            atomicAdd(work, s_cnt[0]);
+            atomicAdd(work + 1, s_cnt[1]);
+        }
+        if (s_cnt[2]) atomicAdd(di.dropped, s_cnt[2]);
     }
 }
 
