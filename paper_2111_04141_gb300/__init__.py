@@ -6,5 +6,6 @@ device memory and streams only.
 """
 from ._lib import GwError, LIB_PATH, load as load_library  # noqa: F401
 from .plan import Plan, ffma_peak, launch_count  # noqa: F401
+from . import hostmem  # noqa: F401
 
 __all__ = ["Plan", "GwError", "ffma_peak", "launch_count", "load_library", "LIB_PATH"]

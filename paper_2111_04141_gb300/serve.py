@@ -260,12 +260,16 @@ class Server:
                 host memory (the tensor is a slot staging buffer: copy it to keep it);
                 a job that was rejected or cancelled without running gets
                 host_tensor None and its reason in job.error
+    host_staging  optional list of n_slots pinned complex64 host tensors used as
+                the slots' result staging instead of allocating new ones (for
+                servers that never run at the same time, or buffers on huge
+                pages from ``hostmem.pinned_empty``)
     """
 
     def __init__(self, setups: List[Setup], device, budget: int, n_slots: int = 4,
                  max_vis: int = 10_000_000, use_graphs: bool = True, tuning: Optional[dict] = None,
                  on_result: Optional[Callable] = None, work_cap: Optional[float] = None,
-                 readback_bands: int = 0):
+                 readback_bands: int = 0, host_staging: Optional[list] = None):
         import torch
         from .plan import Plan
         self.torch = torch
@@ -280,6 +284,7 @@ class Server:
         self.budget = int(budget)
         self.work_cap = work_cap
         self.readback_bands = int(readback_bands)
+        self.host_staging = host_staging
         self.plans: Dict[str, object] = {}
         self.models: Dict[str, object] = {}
         self.freqs: Dict[str, object] = {}
@@ -321,15 +326,22 @@ class Server:
             max_rows = max(max_rows, rows)
             max_grid = max(max_grid, s.grid_bytes())
             max_vis_el = max(max_vis_el, rows * s.nchan * s.npol)
-        for _ in range(self.n_slots):
+        n_host = max(max_grid // 8, max_vis_el)
+        if self.host_staging is not None:
+            if len(self.host_staging) < self.n_slots or any(
+                    h.numel() < n_host or not h.is_pinned() or h.dtype != torch.complex64
+                    for h in self.host_staging[:self.n_slots]):
+                raise ValueError(f"host_staging needs {self.n_slots} pinned complex64 tensors "
+                                 f"of at least {n_host} elements")
+        for k in range(self.n_slots):
             st = torch.cuda.Stream(self.device)
             slot = {
                 "stream": st,
                 "uvw": torch.empty((max_rows, 3), dtype=torch.float64, device=self.device),
                 "vis": torch.empty(max_vis_el, dtype=torch.complex64, device=self.device),
                 "grid": torch.empty(max_grid // 8, dtype=torch.complex64, device=self.device),
-                "host": torch.empty(max(max_grid // 8, max_vis_el), dtype=torch.complex64,
-                                    pin_memory=True),
+                "host": (self.host_staging[k] if self.host_staging is not None else
+                         torch.empty(n_host, dtype=torch.complex64, pin_memory=True)),
                 "event": torch.cuda.Event(),
             }
             resident += (max_rows * 24 + max_vis_el * 8 + max_grid)
@@ -593,10 +605,12 @@ def _mean_s2(s: Setup) -> float:
 # --------------------------------------------------------------------------
 
 def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, jobs: List[Job],
-                   device, on_result: Optional[Callable] = None, clock=time.perf_counter):
+                   device, on_result: Optional[Callable] = None, clock=time.perf_counter,
+                   host_buf=None):
     """Jobs in arrival order on one stream: wait for arrival, copy in, grid or
     degrid with the setup's plan (default tuning, no graphs), copy out into a
-    preallocated pinned buffer (as the server's slots do), synchronise."""
+    preallocated pinned buffer (as the server's slots do; ``host_buf`` if
+    given and large enough), synchronise."""
     import torch
     setups = {s.name: s for s in setups}
     jobs = sorted(jobs, key=lambda j: j.arrival)
@@ -604,7 +618,8 @@ def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, 
     n_host = max(max(setups[j.setup].npol * setups[j.setup].grid_n ** 2,
                      j.nrow * setups[j.setup].nchan * setups[j.setup].npol) for j in jobs) \
         if jobs else 1
-    host_buf = torch.empty(n_host, dtype=torch.complex64, pin_memory=True)
+    if host_buf is None or host_buf.numel() < n_host:
+        host_buf = torch.empty(n_host, dtype=torch.complex64, pin_memory=True)
     t0 = clock()
     for j in jobs:
         s = setups[j.setup]

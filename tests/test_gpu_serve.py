@@ -139,9 +139,10 @@ def test_autotuner_picks_a_candidate(gw):
     assert c.get("x") == res["tuning"]
 
 
-@pytest.mark.parametrize("use_graphs,bands", [(True, 0), (True, 4), (False, 0)],
-                         ids=["graphs", "graphs-readback", "plain"])
-def test_server_results_same_alone_and_in_the_mix(gw, use_graphs, bands):
+@pytest.mark.parametrize("use_graphs,bands,shared", [(True, 0, False), (True, 4, False),
+                                                     (False, 0, False), (True, 0, True)],
+                         ids=["graphs", "graphs-readback", "plain", "graphs-shared-staging"])
+def test_server_results_same_alone_and_in_the_mix(gw, use_graphs, bands, shared):
     from paper_2111_04141_gb300.serve import Server, build_stream, run_sequential
     max_vis = 60_000
     specs = syn.serving_setups(n_setups=4, max_vis=max_vis, grid_sizes=(256, 512))
@@ -153,9 +154,22 @@ def test_server_results_same_alone_and_in_the_mix(gw, use_graphs, bands):
                        + 1j * rng.normal(size=(s.npol, s.grid_n, s.grid_n))).astype(np.complex64)
               for s in setups}
     mixed = {}
+    staging = None
+    if shared:
+        # caller-provided pinned result staging (as servers that take turns share it)
+        n_host = max(max(s.npol * s.grid_n ** 2, -(-max_vis // s.nchan) * s.nchan * s.npol)
+                     for s in setups)
+        small_bufs = [torch.empty(n_host - 1, dtype=torch.complex64, pin_memory=True)] * 3
+        with pytest.raises(ValueError):
+            Server(setups, DEV, budget=8 << 30, n_slots=3, max_vis=max_vis,
+                   host_staging=small_bufs).warm(models)
+        staging = [torch.empty(n_host, dtype=torch.complex64, pin_memory=True) for _ in range(3)]
     srv = Server(setups, DEV, budget=8 << 30, n_slots=3, max_vis=max_vis, use_graphs=use_graphs,
-                 readback_bands=bands, on_result=lambda j, t: mixed.__setitem__(j.id, t.clone()))
+                 readback_bands=bands, on_result=lambda j, t: mixed.__setitem__(j.id, t.clone()),
+                 host_staging=staging)
     srv.warm(models)
+    if shared:
+        assert all(srv.slots[k]["host"] is staging[k] for k in range(3))
     done = srv.run(jobs)
     assert len(done) == len(jobs) and len(mixed) == len(jobs)
     assert all(j.t_done >= j.t_admit >= j.arrival for j in done)
@@ -166,7 +180,8 @@ def test_server_results_same_alone_and_in_the_mix(gw, use_graphs, bands):
     for j in jobs:
         j.arrival = 0.0
     run_sequential(setups, srv.plans, srv.models, srv.freqs, jobs, DEV,
-                   on_result=lambda j, t: alone.__setitem__(j.id, t.clone()))
+                   on_result=lambda j, t: alone.__setitem__(j.id, t.clone()),
+                   host_buf=staging[0] if shared else None)
     for j in jobs:
         assert rel(mixed[j.id], alone[j.id]) <= TOL, (j.id, j.kind, j.setup)
     srv.close()
@@ -216,3 +231,27 @@ def test_grid_readback_matches_devcount(gw, n_bands):
         assert rel(host2.to(DEV), ref_half) <= TOL
         with pytest.raises(gw.GwError):
             plan.grid_devcount_readback(uvw, freq, d_nrow, vis, g, host, n_bands=0)
+
+
+def test_hugepage_pinned_buffers(gw):
+    """Page-locked host buffers from hostmem: pinned, exact round trips
+    through the device, released on request; small ones use the ordinary
+    page-locked allocator."""
+    from paper_2111_04141_gb300 import hostmem
+    n = (hostmem.MIN_HUGE_BYTES // 8) * 2
+    before = hostmem.live_bytes()
+    t = hostmem.pinned_empty((n,), torch.complex64)
+    assert t.is_pinned() and tuple(t.shape) == (n,) and t.dtype == torch.complex64
+    src = torch.randn(n, dtype=torch.complex64, device=DEV)
+    t.copy_(src, non_blocking=True)
+    back = torch.empty_like(src)
+    back.copy_(t, non_blocking=True)
+    torch.cuda.synchronize()
+    assert torch.equal(back, src)
+    grew = hostmem.live_bytes() - before
+    assert grew in (0, n * 8)          # 0 where the host has no huge pages
+    hostmem.release(t)
+    assert hostmem.live_bytes() == before
+    small = hostmem.pinned_empty((1000, 3), torch.float64)
+    assert small.is_pinned() and tuple(small.shape) == (1000, 3)
+    assert hostmem.live_bytes() == before
