@@ -40,8 +40,8 @@ FFMA_PER_SM_PER_CLK = 128
 
 # DRAM traffic of the gridding kernel from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 of gw_grid_kernel.cuh); null otherwise.
-GRID_TRAFFIC = {"sha256": "143ed5e434f929e3248e0370557c3e0a5ad9ae36c845cf2d804a10612c9f912f",
-                "bytes_per_launch": 0.962756e9 + 0.263721e9,
+GRID_TRAFFIC = {"sha256": "1ee91684f8fa3ecd5a1cc714157b1691bdf3c0bbce0a8d1c95030106c9a3d36f",
+                "bytes_per_launch": 0.964303e9 + 0.264140e9,
                 "capture": "profiles/k_grid_wproj4096.md"}
 
 
