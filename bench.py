@@ -505,6 +505,7 @@ def measure_serving(args, dev):
     import numpy as np
     import torch
     import synthetic as syn
+    from paper_2111_04141_gb300 import hostmem
     from paper_2111_04141_gb300.serve import (Server, build_stream, latency_stats,
                                               run_sequential)
     from paper_2111_04141_gb300.tune import tune_plan
@@ -530,6 +531,12 @@ def measure_serving(args, dev):
         tuning[s.name] = res["tuning"]
         tune_ms[s.name] = res["ms"]
     plain = {s.name: Plan(**s.plan_kwargs) for s in setups}
+    # one page-locked arena of result staging (huge pages) for both servers
+    # and the sequential loop, which never run at the same time
+    n_host = max(max(s.npol * s.grid_n ** 2, -(-max_vis // s.nchan) * s.nchan * s.npol)
+                 for s in setups)
+    arena = hostmem.PinnedArena(hostmem.arena_bytes([(n_host, torch.complex64)] * n_slots))
+    staging = [arena.take(n_host, torch.complex64) for _ in range(n_slots)]
 
     def reset(js, arrivals):
         for j, t in zip(js, arrivals):
@@ -537,7 +544,7 @@ def measure_serving(args, dev):
 
     def seq(js, arrivals, srv):
         reset(js, arrivals)
-        run_sequential(setups, plain, srv.models, srv.freqs, js, dev)
+        run_sequential(setups, plain, srv.models, srv.freqs, js, dev, host_buf=staging[0])
         return latency_stats(js)
 
     def served(js, arrivals, srv):
@@ -546,14 +553,17 @@ def measure_serving(args, dev):
         return latency_stats(js)
 
     out = {"jobs": len(jobs), "setups": [s.name for s in setups], "slots": n_slots,
-           "graphs": True, "repeats": 3}
+           "graphs": True, "repeats": 3,
+           "host_staging": f"{n_slots} x {n_host * 8 / 2**30:.1f} GiB page-locked on huge pages "
+                           f"({'yes' if arena.huge else 'no'}), shared by both servers and the "
+                           "sequential loop; job pools likewise in one arena"}
     zeros = np.zeros(len(jobs))
     # both servers are built and warmed before any measurement; the modes
     # then alternate within each repeat, so slow drifts hit them alike
     srvs = {}
     for label, tun in (("default", None), ("autotuned", tuning)):
         srvs[label] = Server(setups, dev, budget=96 << 30, n_slots=n_slots, max_vis=max_vis,
-                             use_graphs=True, tuning=tun)
+                             use_graphs=True, tuning=tun, host_staging=staging)
         srvs[label].warm(models)
     s0 = srvs["default"]
     seq(jobs[:8], zeros[:8], s0)                           # warm-up of the plain path
@@ -573,6 +583,8 @@ def measure_serving(args, dev):
         srv.close()
     for p in plain.values():
         p.close()
+    torch.cuda.synchronize(dev)
+    arena.release()
     out["tuning"] = tuning
     out["tune_ms"] = tune_ms
     med = lambda runs, k: float(np.median([r[k] for r in runs]))

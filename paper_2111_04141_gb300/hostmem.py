@@ -1,19 +1,20 @@
-"""Page-locked host buffers on transparent huge pages.
+"""Page-locked host memory on transparent huge pages.
 
 The GPU reaches page-locked host memory through address translations, and
-their reach is limited.  On the Grace host of a GB300 (64 KiB base pages),
-device-to-host copies into ``cudaHostAlloc`` buffers ran at 15-110 GB/s
-instead of the link's 193 GB/s once about 20 GB of such buffers were in
-rotation (each buffer fast again only after a warm-up copy).  The same
-buffers on transparent huge pages (512 MiB on that host), mapped with
-``mmap`` + ``MADV_HUGEPAGE``, touched, and page-locked with
-``cudaHostRegister``, stayed at 193 GB/s in every pass.  Serving keeps
-several GB of result staging and job inputs in rotation, so its host buffers
-come from here.
+their reach is limited.  On the Grace host of a GB300 (64 KiB base pages,
+512 MiB transparent huge pages), device-to-host copies into 2 GiB
+``cudaHostAlloc`` buffers ran at 15-110 GB/s instead of the link's 193 GB/s
+once about 20 GB of such buffers were used in turn (each buffer fast again
+only after a warm-up copy), on a host whose free memory had been churned by
+earlier processes.  The same buffers on huge pages (``mmap`` +
+``MADV_HUGEPAGE``, touched, then page-locked with ``cudaHostRegister``)
+stayed at 193 GB/s (and 211 GB/s host-to-device) in every pass.  Huge pages
+only pay for whole pages, so many small buffers are carved from one
+``PinnedArena`` instead of being mapped one by one.
 
 Where huge pages are not available (no ``MADV_HUGEPAGE``, a failed
-registration) the buffer is an ordinary ``pin_memory`` tensor.  Buffers
-stay registered until ``release`` or process exit.
+registration) an arena is an ordinary ``pin_memory`` buffer.  Arenas stay
+registered until ``release`` or process exit.
 """
 import mmap
 import threading
@@ -24,58 +25,119 @@ import torch
 MIN_HUGE_BYTES = 64 << 20
 
 _lock = threading.Lock()
-_live = {}   # data_ptr -> (mmap, uint8 view, nbytes)
+_live = {}   # data_ptr of an arena's first byte -> arena
+
+
+def huge_page_bytes() -> int:
+    """The transparent huge page size of the host (2 MiB if unknown)."""
+    try:
+        with open("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size") as f:
+            return int(f.read().strip())
+    except (OSError, ValueError):
+        return 2 << 20
 
 
 def _itemsize(dtype) -> int:
     return torch.empty((), dtype=dtype).element_size()
 
 
+class PinnedArena:
+    """One page-locked host mapping on huge pages; ``take`` hands out
+    aligned, non-overlapping tensors from it."""
+
+    def __init__(self, nbytes: int):
+        self.nbytes = int(nbytes)
+        self.huge = False
+        self._mm = None
+        self._used = 0
+        hp = huge_page_bytes()
+        if self.nbytes >= MIN_HUGE_BYTES and hasattr(mmap, "MADV_HUGEPAGE"):
+            mm = None
+            try:
+                # one huge page extra, so the usable part can start on a
+                # huge-page boundary wherever the mapping lands
+                total = -(-self.nbytes // hp) * hp + hp
+                mm = mmap.mmap(-1, total, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+                mm.madvise(mmap.MADV_HUGEPAGE)
+                whole = torch.frombuffer(mm, dtype=torch.uint8)
+                start = (-whole.data_ptr()) % hp
+                raw = whole[start:start + self.nbytes]
+                raw.zero_()   # fault every page in now, as huge pages
+                err = torch.cuda.cudart().cudaHostRegister(raw.data_ptr(), self.nbytes, 0)
+                if int(err) == 0:
+                    self._mm, self._raw, self.huge = mm, raw, True
+            except (OSError, ValueError, BufferError, RuntimeError, AttributeError):
+                self.huge = False
+            if not self.huge and mm is not None:
+                raw = whole = None
+                try:
+                    mm.close()
+                except BufferError:
+                    pass
+        if not self.huge:
+            self._raw = torch.empty(max(self.nbytes, 1), dtype=torch.uint8, pin_memory=True)
+        with _lock:
+            _live[self._raw.data_ptr()] = self
+
+    def take(self, shape, dtype=torch.complex64, align: int = 4096) -> torch.Tensor:
+        shape = (shape,) if isinstance(shape, int) else tuple(int(s) for s in shape)
+        n = 1
+        for s in shape:
+            n *= s
+        nbytes = n * _itemsize(dtype)
+        off = -(-self._used // align) * align
+        if off + nbytes > self.nbytes:
+            raise ValueError(f"arena of {self.nbytes} bytes cannot hold {nbytes} more bytes "
+                             f"after {self._used}")
+        self._used = off + nbytes
+        return self._raw[off:off + nbytes].view(dtype).view(shape)
+
+    def release(self) -> None:
+        """Unregister and unmap (the caller guarantees no pending copy and no
+        further use of the tensors taken from the arena)."""
+        with _lock:
+            _live.pop(self._raw.data_ptr(), None)
+        if self.huge:
+            torch.cuda.cudart().cudaHostUnregister(self._raw.data_ptr())
+            self.huge = False
+        self._raw = torch.empty(0, dtype=torch.uint8)
+        if self._mm is not None:
+            try:
+                self._mm.close()
+            except BufferError:
+                pass   # tensors still view the mapping: it lives until they go
+            self._mm = None
+
+
+def arena_bytes(specs, align: int = 4096) -> int:
+    """Bytes an arena needs for tensors of the given (shape, dtype) pairs."""
+    total = 0
+    for shape, dtype in specs:
+        shape = (shape,) if isinstance(shape, int) else tuple(shape)
+        n = 1
+        for s in shape:
+            n *= int(s)
+        total = -(-total // align) * align + n * _itemsize(dtype)
+    return total
+
+
 def pinned_empty(shape, dtype=torch.complex64) -> torch.Tensor:
     """An uninitialised page-locked host tensor, on huge pages when it is at
-    least MIN_HUGE_BYTES and the host allows it."""
-    shape = (shape,) if isinstance(shape, int) else tuple(int(s) for s in shape)
-    n = 1
-    for s in shape:
-        n *= s
-    nbytes = n * _itemsize(dtype)
-    if nbytes < MIN_HUGE_BYTES or not hasattr(mmap, "MADV_HUGEPAGE"):
-        return torch.empty(shape, dtype=dtype, pin_memory=True)
-    try:
-        mm = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
-        mm.madvise(mmap.MADV_HUGEPAGE)
-    except (OSError, ValueError):
-        return torch.empty(shape, dtype=dtype, pin_memory=True)
-    raw = torch.frombuffer(mm, dtype=torch.uint8)
-    raw.zero_()   # fault every page in now, as huge pages
-    err = torch.cuda.cudart().cudaHostRegister(raw.data_ptr(), nbytes, 0)
-    if int(err) != 0:
-        del raw
-        mm.close()
-        return torch.empty(shape, dtype=dtype, pin_memory=True)
-    with _lock:
-        _live[raw.data_ptr()] = (mm, raw, nbytes)
-    return raw.view(dtype).view(shape)
+    least MIN_HUGE_BYTES and the host allows it (an arena of its own)."""
+    arena = PinnedArena(arena_bytes([(shape, dtype)]))
+    t = arena.take(shape, dtype)
+    t._gw_arena = arena   # the arena lives as long as the tensor object
+    return t
 
 
 def release(t: torch.Tensor) -> None:
-    """Unregister and unmap a tensor from ``pinned_empty`` (no-op for any
-    other tensor).  The caller guarantees that no copy into or out of it is
-    pending and that no view of it is used afterwards."""
-    with _lock:
-        ent = _live.pop(t.data_ptr(), None)
-    if ent is None:
-        return
-    mm, raw, _ = ent
-    torch.cuda.cudart().cudaHostUnregister(raw.data_ptr())
-    del raw
-    try:
-        mm.close()
-    except BufferError:
-        pass   # views still export the buffer: the mapping lives until they go
+    """Release the arena of a tensor from ``pinned_empty`` (no-op otherwise)."""
+    arena = getattr(t, "_gw_arena", None)
+    if arena is not None:
+        arena.release()
 
 
 def live_bytes() -> int:
-    """Bytes currently held by ``pinned_empty`` huge-page buffers."""
+    """Bytes held by registered huge-page arenas."""
     with _lock:
-        return sum(e[2] for e in _live.values())
+        return sum(a.nbytes for a in _live.values() if a.huge)

@@ -262,8 +262,9 @@ class Server:
                 host_tensor None and its reason in job.error
     host_staging  optional list of n_slots pinned complex64 host tensors used as
                 the slots' result staging instead of allocating new ones (for
-                servers that never run at the same time, or buffers on huge
-                pages from ``hostmem.pinned_empty``)
+                servers that never run at the same time); by default the slots'
+                staging is one page-locked arena on huge pages
+                (``hostmem.PinnedArena``)
     """
 
     def __init__(self, setups: List[Setup], device, budget: int, n_slots: int = 4,
@@ -285,6 +286,7 @@ class Server:
         self.work_cap = work_cap
         self.readback_bands = int(readback_bands)
         self.host_staging = host_staging
+        self._arena = None
         self.plans: Dict[str, object] = {}
         self.models: Dict[str, object] = {}
         self.freqs: Dict[str, object] = {}
@@ -327,7 +329,12 @@ class Server:
             max_grid = max(max_grid, s.grid_bytes())
             max_vis_el = max(max_vis_el, rows * s.nchan * s.npol)
         n_host = max(max_grid // 8, max_vis_el)
-        if self.host_staging is not None:
+        if self.host_staging is None:
+            # the slots' result staging: one page-locked arena on huge pages
+            from . import hostmem
+            self._arena = hostmem.PinnedArena(
+                hostmem.arena_bytes([(n_host, torch.complex64)] * self.n_slots))
+        else:
             if len(self.host_staging) < self.n_slots or any(
                     h.numel() < n_host or not h.is_pinned() or h.dtype != torch.complex64
                     for h in self.host_staging[:self.n_slots]):
@@ -341,7 +348,7 @@ class Server:
                 "vis": torch.empty(max_vis_el, dtype=torch.complex64, device=self.device),
                 "grid": torch.empty(max_grid // 8, dtype=torch.complex64, device=self.device),
                 "host": (self.host_staging[k] if self.host_staging is not None else
-                         torch.empty(n_host, dtype=torch.complex64, pin_memory=True)),
+                         self._arena.take(n_host, torch.complex64)),
                 "event": torch.cuda.Event(),
             }
             resident += (max_rows * 24 + max_vis_el * 8 + max_grid)
@@ -372,6 +379,11 @@ class Server:
         for p in self.plans.values():
             p.close()
         self.plans.clear()
+        if self._arena is not None:
+            self.torch.cuda.synchronize(self.device)
+            self.slots = []
+            self._arena.release()
+            self._arena = None
 
     # ---- slot state -------------------------------------------------------
     def _state_bytes(self, setup: str) -> int:
@@ -618,8 +630,21 @@ def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, 
     n_host = max(max(setups[j.setup].npol * setups[j.setup].grid_n ** 2,
                      j.nrow * setups[j.setup].nchan * setups[j.setup].npol) for j in jobs) \
         if jobs else 1
-    if host_buf is None or host_buf.numel() < n_host:
-        host_buf = torch.empty(n_host, dtype=torch.complex64, pin_memory=True)
+    from . import hostmem
+    owned = host_buf is None or host_buf.numel() < n_host
+    if owned:
+        host_buf = hostmem.pinned_empty(n_host, torch.complex64)
+    try:
+        return _run_sequential(setups, plans, models, freqs, jobs, device, on_result, clock,
+                               host_buf, stream)
+    finally:
+        if owned:
+            stream.synchronize()
+            hostmem.release(host_buf)
+
+
+def _run_sequential(setups, plans, models, freqs, jobs, device, on_result, clock, host_buf,
+                    stream):
     t0 = clock()
     for j in jobs:
         s = setups[j.setup]
@@ -651,11 +676,13 @@ def run_sequential(setups: List[Setup], plans: dict, models: dict, freqs: dict, 
 def build_stream(setup_specs: List[dict], job_specs: List[dict], arrivals, max_vis: int,
                  vis_seed: int = 0):
     """Setups and Jobs from plain specs: per setup, pinned pools of sorted
-    and shuffled uvw rows and of visibilities (CN(0, 1), max_vis x npol);
-    every job is a view into its setup's pools."""
+    and shuffled uvw rows and of visibilities (CN(0, 1), max_vis x npol),
+    all in one page-locked arena on huge pages; every job is a view into its
+    setup's pools."""
     import torch
+    from . import hostmem
     gen = torch.Generator().manual_seed(vis_seed)
-    setups, pools = [], {}
+    setups, host = [], {}
     for d in setup_specs:
         st = Setup(d["name"], dict(d["plan_kwargs"]), np.asarray(d["freq_hz"]))
         setups.append(st)
@@ -663,11 +690,19 @@ def build_stream(setup_specs: List[dict], job_specs: List[dict], arrivals, max_v
         rows = -(-max_vis // nchan)
         v = torch.randn((rows, nchan, npol, 2), generator=gen, dtype=torch.float32)
         v.mul_(float(np.sqrt(0.5)))
-        pools[st.name] = {
-            "sorted": torch.from_numpy(np.ascontiguousarray(d["uvw_sorted"])).pin_memory(),
-            "shuffled": torch.from_numpy(np.ascontiguousarray(d["uvw_shuffled"])).pin_memory(),
-            "vis": torch.view_as_complex(v).pin_memory(),
+        host[st.name] = {
+            "sorted": torch.from_numpy(np.ascontiguousarray(d["uvw_sorted"])),
+            "shuffled": torch.from_numpy(np.ascontiguousarray(d["uvw_shuffled"])),
+            "vis": torch.view_as_complex(v),
         }
+    arena = hostmem.PinnedArena(hostmem.arena_bytes(
+        [(t.shape, t.dtype) for h in host.values() for t in h.values()]))
+    pools = {}
+    for name, h in host.items():
+        pools[name] = {}
+        for k, t in h.items():
+            pools[name][k] = arena.take(t.shape, t.dtype)
+            pools[name][k].copy_(t)
     jobs = []
     for spec, t in zip(job_specs, arrivals):
         pool = pools[spec["setup"]]
