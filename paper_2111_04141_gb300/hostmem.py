@@ -25,7 +25,7 @@ import torch
 MIN_HUGE_BYTES = 64 << 20
 
 _lock = threading.Lock()
-_live = {}   # data_ptr of an arena's first byte -> arena
+_live = {}   # data_ptr of a registered arena's first byte -> arena
 
 
 def huge_page_bytes() -> int:
@@ -76,8 +76,11 @@ class PinnedArena:
                     pass
         if not self.huge:
             self._raw = torch.empty(max(self.nbytes, 1), dtype=torch.uint8, pin_memory=True)
-        with _lock:
-            _live[self._raw.data_ptr()] = self
+        else:
+            # a registered mapping must be unregistered before it is unmapped:
+            # the registry keeps it (and its views' memory) alive until release
+            with _lock:
+                _live[self._raw.data_ptr()] = self
 
     def take(self, shape, dtype=torch.complex64, align: int = 4096) -> torch.Tensor:
         shape = (shape,) if isinstance(shape, int) else tuple(int(s) for s in shape)
@@ -140,4 +143,4 @@ def release(t: torch.Tensor) -> None:
 def live_bytes() -> int:
     """Bytes held by registered huge-page arenas."""
     with _lock:
-        return sum(a.nbytes for a in _live.values() if a.huge)
+        return sum(a.nbytes for a in _live.values())
