@@ -53,7 +53,7 @@ typedef enum {
     GW_ENOMEM = -2,        /* a device or host allocation failed */
     GW_ECUDA = -3,         /* a CUDA runtime call failed (see gw_last_error) */
     GW_ETIMEDOUT = -4,     /* a bounded device-side wait gave up */
-    GW_EUNSUPPORTED = -5,  /* valid request this build does not implement */
+    GW_EUNSUPPORTED = -5,  /* valid request the library does not implement */
     GW_EDEVICE = -6,       /* called with a different current device than the plan's */
     GW_EBOUNDS = -7        /* a device-side bounds check of the debug build failed */
 } gw_status;
